@@ -1,0 +1,360 @@
+"""Benchmark of the solid-LBM hot path on GB300, one JSON line on stdout.
+
+A bench step is one complete solve of the workload: reset to the rest state,
+all time steps of the configuration (interior + boundary kernels each step),
+then the fields (u, v, sigma) on the device.  Throughput is giga lattice
+updates per second (GLUPS) over material nodes.
+
+Default workload: the suddenly loaded edge crack on a 2048 x 2048 lattice,
+crack length 512, 1500 steps, FP32 deviation storage.  Its working set
+(two 151 MB distribution buffers + 67 MB displacement) exceeds the 129 MB L2,
+so no L2 flush is needed between steps.  ``--workload plate`` runs the
+1024 x 512 plate with a hole (20000 steps; 46 MB, L2-resident).
+
+Arms:
+  (default)          the CUDA library through its C ABI (device-resident
+                     inputs), plus ``e2e`` through the same public API from
+                     host buffers, ``roofline`` of the interior kernel,
+                     ``cpu_baseline`` (the FP64 oracle on a bounded sample).
+  --impl reference   the FP64 oracle on the host cores (bounded sample per step).
+
+Multi-GPU (torchrun, one rank per GPU): every rank solves its own replica;
+no collective on the data path ("replicas only"), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS (giga lattice updates per second, whole job)"
+WORKLOADS = ("crack", "plate")
+
+
+def _workload(name):
+    from paper_2208_04088_gb300 import workloads as W
+    if name == "crack":
+        return W.CONFIG3
+    if name == "plate":
+        return W.CONFIG2
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _cpu_baseline(wl, seconds=12.0):
+    """The FP64 oracle, as it stands, on the host cores: run the first steps of
+    the same lattice until `seconds` have passed; GLUPS over material nodes."""
+    import oracle
+    nt, links = oracle.geometry(**wl.geometry_args())
+    o = oracle.Oracle(nt, links, wl.bcs, lam=wl.lam, mu=wl.mu, rho0=wl.rho0, tau=wl.tau)
+    nodes = int(nt.sum())
+    o.step(1)  # touch memory
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(2)
+        steps += 2
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= wl.steps:
+            break
+    o.close()
+    return {"value": nodes * steps / el / 1e9, "unit": "GLUPS", "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"first {steps} of {wl.steps} steps of the {wl.nx}x{wl.ny} {wl.name} "
+                      f"lattice ({nodes} material nodes), {el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    wl = _workload(args.workload)
+    if rank != 0:
+        return 0
+    import oracle
+    nt, links = oracle.geometry(**wl.geometry_args())
+    nodes = int(nt.sum())
+    per_step = max(2, int(args.ref_steps_per_step))
+    o = oracle.Oracle(nt, links, wl.bcs, lam=wl.lam, mu=wl.mu, rho0=wl.rho0, tau=wl.tau)
+    for _ in range(args.warmup):
+        o.step(per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(per_step)
+    el = time.perf_counter() - t0
+    o.close()
+    value = nodes * per_step * args.steps / el / 1e9
+    sample = (f"{per_step} time steps per bench step of the {wl.nx}x{wl.ny} {wl.name} lattice "
+              f"({nodes} material nodes)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "steps": wl.steps,
+                   "storage": "f64 absolute", "l2": "host run"},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": oracle.threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2208_04088_gb300 import _native as N
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N.load(build_if_missing=False)
+    wl = _workload(args.workload)
+    stream = torch.cuda.Stream(device=dev)
+
+    wall_node = args.wall_values == "node"
+    desc = N.desc_from_workload(wl, storage=args.storage, wall_node=wall_node)
+    nodes = int(desc.node_type.sum())
+    solver = N.Solver(desc, stream=stream, device=dev)
+    info0 = solver.info()
+    fields = {"u": torch.empty((2, wl.ny, wl.nx), device=dev),
+              "v": torch.empty((2, wl.ny, wl.nx), device=dev),
+              "s": torch.empty((3, wl.ny, wl.nx), device=dev)}
+
+    def solve():
+        solver.reset()
+        solver.step(wl.steps)
+        N.lbm_get_fields(solver.h, fields["u"].data_ptr(), fields["v"].data_ptr(),
+                         fields["s"].data_ptr(), on_device=True)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        solve()
+    solver.sync()
+    barrier()
+
+    # timed region: kernels timed with events on the launching stream
+    solver.set_timing(True)
+    solver.timing()  # clear
+    launches0 = solver.info()["kernel_launches"]
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        start.record(stream)
+        for _ in range(args.steps):
+            solve()
+        stop.record(stream)
+        barrier()
+    solver.sync()
+    elapsed_ms = start.elapsed_time(stop)
+    launches = solver.info()["kernel_launches"] - launches0
+    tim = solver.timing()
+    solver.set_timing(False)
+    t = torch.tensor([elapsed_ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    total_lu = nodes * wl.steps * args.steps * world
+    value = total_lu / (elapsed_ms * 1e-3) / 1e9
+
+    # roofline of the interior kernel: algorithmic bytes per launch / mean launch time
+    bpu = info0["bytes_per_update"]
+    interior = info0["interior_nodes"]
+    mean_interior_ms = tim["interior_ms"] / max(1, tim["steps"])
+    achieved_gbs = interior * bpu / (mean_interior_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+
+    # end to end through the public API from host buffers: create (host tables
+    # -> device), all steps, fields -> pinned host buffers, destroy
+    e2e = None
+    if not args.no_e2e:
+        host_u = torch.empty((2, wl.ny, wl.nx), pin_memory=True)
+        host_v = torch.empty((2, wl.ny, wl.nx), pin_memory=True)
+        host_s = torch.empty((3, wl.ny, wl.nx), pin_memory=True)
+        h2d = None
+
+        def e2e_solve():
+            nonlocal h2d
+            d = N.desc_from_workload(wl, storage=args.storage, wall_node=wall_node)
+            h = N.lbm_create(d, stream.cuda_stream, 0, 0)
+            inf = N.lbm_get_info(h)
+            h2d = (inf["pitch"] * wl.ny + 16 * inf["boundary_nodes"] +
+                   128 * inf["boundary_nodes"] + 24 * len(wl.bcs))
+            N.lbm_step(h, wl.steps)
+            N.lbm_get_fields(h, host_u.data_ptr(), host_v.data_ptr(), host_s.data_ptr(),
+                             on_device=False)
+            N.lbm_destroy(h)
+
+        e2e_solve()
+        barrier()
+        n_e2e = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_solve()
+        barrier()
+        el = time.perf_counter() - t0
+        te = torch.tensor([el], device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        el = float(te.item())
+        e2e = {"value": nodes * wl.steps * n_e2e * world / el / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(7 * 4 * wl.nx * wl.ny),
+               "steps": n_e2e,
+               "includes": "lbm_create from host tables (classification, device allocation, "
+                           "H2D), lbm_step, lbm_get_fields to pinned host, lbm_destroy"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(wl, seconds=args.cpu_seconds)
+
+    solver.close()
+    if rank == 0:
+        esz = 4 if args.storage == "f32" else 2
+        line = {
+            "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+            "data": "synthetic",
+            "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "time_steps": wl.steps,
+                       "material_nodes": nodes, "storage": args.storage + " deviations",
+                       "wall_values": args.wall_values,
+                       "parallelism": f"replicas x{world}",
+                       "l2": ("inputs larger than L2 (working set "
+                              f"{(2 * 9 * esz + 16) * wl.nx * wl.ny / 1e6:.0f} MB)"
+                              if (2 * 9 * esz + 16) * wl.nx * wl.ny > 129e6 else
+                              "working set fits in L2; no flush inside a solve")},
+            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak,
+                         "unit": "GB/s", "frac": achieved_gbs / peak,
+                         "traffic": args.traffic, "kernel": "k_interior",
+                         "bytes_per_update": bpu, "updates_per_launch": interior,
+                         "mean_launch_ms": mean_interior_ms, "peak_kind": peak_kind,
+                         "boundary_kernel_ms_per_step": tim["boundary_ms"] / max(1, tim["steps"])},
+            "clocks": clocks.summary(),
+            "gpu_launches": int(launches),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="crack", choices=WORKLOADS)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--wall-values", default="node", choices=["extrapolate", "node"],
+                    help="Neumann wall values: the boundary node's own (default) or the "
+                         "paper's extrapolation along the link, whose density mode grows "
+                         "after ~700 steps of the crack and dominates the fields by 1500")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-steps-per-step", type=int, default=4)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per interior launch, if measured for this kernel")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,234 @@
+/*
+ * lbm.h -- C ABI of a GB300 (sm_103a) solver for the solid lattice Boltzmann
+ * method with local Dirichlet and Neumann boundary rules (Faust, Schlueter,
+ * Mueller, Mueller 2022, arXiv 2208.04088).
+ *
+ * What one time step computes (lattice units dx = dt = 1, c_s^2 = 1/3):
+ *   streaming of the nine D2Q9 populations (Sec. 3, Eq. stream, pull form),
+ *   the moments rho, j, P (Eq. moments) with the source S = F +
+ *   (mu - lambda)/rho grad rho (Eq. sourceterm), the equilibrium of Eq. (fieq),
+ *   BGK collision with source (Eq. coll), the boundary rules of Sec. 4
+ *   (Eqs. bbcon, abbcon, bbnoncon, abbnoncon) for the populations that would
+ *   stream in from across a wall, and u += j/rho for the displacement.
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *   - D2Q9 directions 0 rest, 1 +x, 2 +y, 3 -x, 4 -y, 5 (+x,+y), 6 (-x,+y),
+ *     7 (-x,-y), 8 (+x,-y); weights 4/9, 1/9, 1/36.
+ *   - nodes sit at integer (x, y), 0 <= x < nx, 0 <= y < ny, row-major index
+ *     y*nx + x; the box is [-1/2, nx - 1/2] x [-1/2, ny - 1/2].
+ *   - Dirichlet data j* = rho0 d(u*)/dt; Neumann data sigma* from the traction
+ *     in the boundary frame with sigma_tt extrapolated along the link like
+ *     rho^bd (Sec. 2.2, Eqs. trafocauchy, bcchainneum, approxdiv).
+ *   - boundary values are taken at the time of the post-collision populations
+ *     they act on; a step load is on from the first step.
+ *   - a corner link (wall point at the corner of two edges) is Dirichlet if
+ *     either edge is; otherwise sigma* takes xx from the x-normal edge, yy from
+ *     the y-normal edge and the mean of both shears.
+ *   - if the node upstream of a cut link (x - c_i) is void or itself across a
+ *     wall, the link uses the lattice-conforming rule with rho^bd = rho(x).
+ *   - grad rho: central differences, one-sided next to a wall, zero between two.
+ *
+ * Errors: every call returns an lbm_status; the library never aborts.  The
+ * text of the last error of the calling thread is lbm_last_error().
+ * Threading: a handle may be used by one host thread at a time.
+ * All calls that launch device work are asynchronous on the handle's stream
+ * unless stated otherwise.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_solver *lbm_handle;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,      /* invalid argument or inconsistent tables */
+    LBM_ERR_NOMEM = 2,    /* device memory or workspace too small */
+    LBM_ERR_CUDA = 3,     /* a CUDA runtime call failed (see lbm_last_error) */
+    LBM_ERR_UNSTABLE = 4, /* a non-finite moment was produced (Sec. 6: the
+                             scheme is not unconditionally stable) */
+    LBM_ERR_TIMEOUT = 5   /* a bounded wait expired */
+} lbm_status;
+
+/* Storage of the distribution functions.  All arithmetic is FP32; the 16-bit
+ * forms store f - f_rest scaled by a power of two and round to nearest. */
+typedef enum { LBM_F32 = 0, LBM_F16_DEV = 1, LBM_BF16_DEV = 2 } lbm_storage;
+
+/* Where the Neumann rules take the wall density rho^bd and the wall stress
+ * used for sigma_tt.  LBM_WALL_EXTRAPOLATE is the rule of Sec. 4 (linear
+ * extrapolation along the link, (3 a(x) - a(x - c_i))/2 at a mid-link wall).
+ * LBM_WALL_NODE takes both at the boundary node itself; it is not the paper's
+ * rule.  On lattices with lambda = mu the density is otherwise undamped and the
+ * extrapolation feeds it back at traction edges: runs of more than about a
+ * thousand steps grow a density mode there, which LBM_WALL_NODE removes on
+ * straight edges. */
+typedef enum { LBM_WALL_EXTRAPOLATE = 0, LBM_WALL_NODE = 1 } lbm_wall_values;
+
+/* Boundary-condition kinds (Sec. 2, Eqs. bcdir and bcneu). */
+typedef enum {
+    LBM_BC_DIRICHLET = 0, /* value[0..1] = d(u*)/dt  (velocity of the wall)  */
+    LBM_BC_TRACTION = 1,  /* value[0..1] = t*                                  */
+    LBM_BC_PRESSURE = 2,  /* value[0] = p, t* = -p n  (n outward normal)       */
+    LBM_BC_STRESS = 3     /* value = (s_xx, s_yy, s_xy), t* = s n              */
+} lbm_bc_kind;
+
+typedef enum {
+    LBM_PROFILE_STEP = 0, /* Heaviside: full value from t = 0 */
+    LBM_PROFILE_RAMP = 1  /* linear from 0 at t = 0 to full at t_ramp, then held */
+} lbm_profile;
+
+/* One boundary condition, in the physical units of lbm_desc. 40 bytes. */
+typedef struct {
+    int32_t kind;    /* lbm_bc_kind */
+    int32_t profile; /* lbm_profile */
+    double value[3];
+    double t_ramp;   /* ramp duration (time units); used by LBM_PROFILE_RAMP */
+} lbm_bc;
+
+/* One cut link: the link from material node `node` towards node + c_dir
+ * crosses the wall at distance s = q * |c_dir| (Fig. boundnoncon).  40 bytes. */
+typedef struct {
+    int32_t node; /* y*nx + x of a material node */
+    int32_t dir;  /* 1..8 */
+    int32_t bc;   /* index into lbm_desc.bcs (the x-normal edge of a corner link) */
+    int32_t bc2;  /* -1, or the y-normal edge of a corner link */
+    double q;     /* s/l in (0, 1]; 0.5 is a lattice-conforming (mid-link) wall */
+    double n[2];  /* outward unit normal of the material at the wall point; for
+                     a corner link the signs (+-1, +-1) of the two edge normals */
+} lbm_link;
+
+/* Analytic geometry: a box, optionally with a circular hole or an edge crack.
+ * Box edges cut links at mid-link.  A node is void iff strictly inside the
+ * hole; a link is cut by the hole iff its end node is void, with q the first
+ * crossing of the circle.  The edge crack runs from the left edge along
+ * y = ny/2 - 1/2 (ny even) to its tip at x = crack_len - 1/2. */
+typedef struct {
+    int32_t nx, ny;
+    int32_t edge_bc[4]; /* bc index of the left, right, bottom, top edge */
+    double hole_cx, hole_cy, hole_r; /* hole_r <= 0: no hole */
+    int32_t hole_bc;
+    int32_t crack_len; /* <= 0: no crack */
+    int32_t crack_bc;  /* both crack faces */
+    int32_t reserved;  /* must be 0 */
+} lbm_geom;
+
+/* Problem description.  Physical units: the lattice spacing dx and the time
+ * step dt must satisfy the isotropy condition dx/(sqrt(3) dt) = sqrt(mu/rho0)
+ * of Sec. 5.1 to a relative 1e-3; the scheme then runs in lattice units with
+ * mu_lattice = rho0/3 and lambda_lattice = (lambda/mu) rho0/3. */
+typedef struct {
+    int32_t nx, ny;          /* lattice size, 1..65535 each */
+    double lambda, mu, rho0; /* Lame parameters and reference density */
+    double dx, dt;           /* lattice spacing, time step */
+    double tau;              /* relaxation time tau_bar/dt of Eq. (coll), > 0.5 */
+    double force[2];         /* constant body force density F (Eq. sourceterm) */
+    const uint8_t *node_type; /* host, nx*ny row-major: 0 void, 1 material */
+    const lbm_link *links;    /* host, nlinks cut links, any order, each
+                                 (node, dir) at most once */
+    int64_t nlinks;
+    const lbm_bc *bcs; /* host, nbcs entries */
+    int32_t nbcs;      /* 1..65535 */
+    int32_t storage;   /* lbm_storage */
+    int32_t wall_values; /* lbm_wall_values */
+    int32_t reserved;    /* must be 0 */
+} lbm_desc;
+
+/* Read-only information about a handle. */
+typedef struct {
+    int32_t nx, ny, pitch, storage;
+    int64_t time;           /* completed time steps */
+    int64_t boundary_nodes; /* nodes with at least one cut link */
+    int64_t interior_nodes; /* material nodes without cut links */
+    uint64_t workspace_bytes;
+    float storage_scale;    /* power-of-two scale of the 16-bit forms, 1 for FP32 */
+    float bytes_per_update; /* algorithmic HBM bytes per interior lattice update */
+    int64_t kernel_launches; /* kernels this handle has launched so far */
+} lbm_info;
+
+/* Accumulated kernel times of timing mode (see lbm_set_timing). */
+typedef struct {
+    double interior_ms; /* sum over steps of the interior (bulk) kernel */
+    double boundary_ms; /* sum over steps of the boundary-list kernel */
+    int64_t steps;      /* steps timed */
+} lbm_timing;
+
+/* Build the node mask and cut-link table of an analytic geometry on the host.
+ * node_type: nx*ny bytes written.  links: capacity `cap`, may be NULL to only
+ * count; *nlinks receives the number of cut links.  Links come in canonical
+ * order (node row-major, then direction).  q and n are computed in double
+ * precision with a fixed operation order: dx = x - cx, dy = y - cy,
+ * b = c.(dx, dy), c0 = dx*dx + dy*dy - R*R, a = |c|^2,
+ * q = (-b - sqrt(b*b - a*c0))/a, n = ((cx - (x + q c_x))/R, (cy - (y + q c_y))/R).
+ * Returns LBM_ERR_ARG for a bad geometry, LBM_ERR_NOMEM if cap is too small. */
+lbm_status lbm_geom_build(const lbm_geom *geom, uint8_t *node_type, lbm_link *links,
+                          int64_t cap, int64_t *nlinks);
+
+/* Device bytes a handle for `desc` needs (distributions, displacement,
+ * tables, field staging).  Host tables are validated as in lbm_create. */
+lbm_status lbm_workspace_size(const lbm_desc *desc, uint64_t *bytes);
+
+/* Create a solver: validates and classifies the tables on the host, copies
+ * them to the device and sets the zero-stress rest state at t = 0 (footnote
+ * to Eq. poissonstress).  `stream` is a cudaStream_t (NULL: the legacy default
+ * stream).  If `workspace` is non-NULL it must be device memory of at least
+ * lbm_workspace_size() bytes, 256-byte aligned, owned by the caller and kept
+ * alive until lbm_destroy; otherwise the library allocates with cudaMalloc.
+ * The caller keeps ownership of every host array; none is referenced after
+ * return.  Synchronises the stream before returning. */
+lbm_status lbm_create(const lbm_desc *desc, void *stream, void *workspace,
+                      uint64_t workspace_bytes, lbm_handle *out);
+
+/* Advance nsteps >= 0 time steps (asynchronous).  Long runs replay CUDA
+ * graphs of a fixed number of steps.  Returns LBM_ERR_UNSTABLE if an earlier
+ * step, already completed on the device, produced a non-finite moment. */
+lbm_status lbm_step(lbm_handle h, int64_t nsteps);
+
+/* Fields at the current time t, dense row-major planes, physical units:
+ *   u     [2][ny][nx]  displacement (x plane, then y plane)
+ *   v     [2][ny][nx]  velocity j/rho
+ *   sigma [3][ny][nx]  Cauchy stress xx, yy, xy: sigma = -P + (lambda - mu)
+ *                      (rho0 - rho)/rho0 I (Eqs. poissonstress, approxdiv)
+ * Void nodes are 0.  Any pointer may be NULL.  on_device = 1: device pointers,
+ * asynchronous; on_device = 0: host pointers, returns after the copy. */
+lbm_status lbm_get_fields(lbm_handle h, float *u, float *v, float *sigma, int32_t on_device);
+
+/* Fields at `count` nodes (host indices y*nx + x) into host `out`
+ * [count][7] = (u_x, u_y, v_x, v_y, s_xx, s_yy, s_xy).  Synchronous. */
+lbm_status lbm_probe(lbm_handle h, const int32_t *nodes, int32_t count, float *out);
+
+/* Replace boundary condition `index` (takes effect from the next step). */
+lbm_status lbm_set_bc(lbm_handle h, int32_t index, const lbm_bc *bc);
+
+/* Back to the rest state at t = 0 (asynchronous). */
+lbm_status lbm_reset(lbm_handle h);
+
+/* Wait for the handle's stream; LBM_ERR_UNSTABLE if a non-finite moment was
+ * produced since creation or the last reset. */
+lbm_status lbm_sync(lbm_handle h);
+
+lbm_status lbm_get_info(lbm_handle h, lbm_info *info);
+
+/* Timing mode for profiling.  While enabled, lbm_step launches the kernels of
+ * each step directly (no graphs; the boundary kernel on a private stream beside
+ * the interior kernel, joined before the next step, as inside the graphs) and
+ * records CUDA events around both on their streams.
+ * lbm_get_timing synchronises, returns the accumulated times and clears them. */
+lbm_status lbm_set_timing(lbm_handle h, int32_t enable);
+lbm_status lbm_get_timing(lbm_handle h, lbm_timing *out);
+
+/* Release the handle and any memory the library allocated (synchronises). */
+lbm_status lbm_destroy(lbm_handle h);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -85,7 +85,7 @@ def _load():
     lib.ora_geometry.restype = i64
     lib.ora_create.argtypes = [i32, i32, d, d, d, d, d, d, i32, i32,
                                C.POINTER(C.c_uint8), C.POINTER(Link), i64,
-                               C.POINTER(BC), i32]
+                               C.POINTER(BC), i32, i32]
     lib.ora_create.restype = p
     lib.ora_destroy.argtypes = [p]
     lib.ora_destroy.restype = None
@@ -184,7 +184,9 @@ class Oracle:
     """One FP64 solver instance (lattice units: dx = dt = 1, c_s^2 = 1/3)."""
 
     def __init__(self, node_type, links, bcs, lam, mu, rho0=1.0, tau=0.55,
-                 force=(0.0, 0.0), periodic=(False, False)):
+                 force=(0.0, 0.0), periodic=(False, False), wall_node=False):
+        """wall_node=True takes rho^bd and sigma^bd at the boundary node instead of
+        extrapolating them along the link (an option, not the paper's rule)."""
         self._lib = _load()
         node_type = np.ascontiguousarray(node_type, dtype=np.uint8)
         self.ny, self.nx = node_type.shape
@@ -196,7 +198,7 @@ class Oracle:
             float(force[0]), float(force[1]), int(periodic[0]), int(periodic[1]),
             node_type.ctypes.data_as(C.POINTER(C.c_uint8)),
             self._links.ctypes.data_as(C.POINTER(Link)), len(self._links),
-            self._bcs, len(bcs))
+            self._bcs, len(bcs), int(bool(wall_node)))
         if not self._h:
             raise RuntimeError("ora_create failed")
 

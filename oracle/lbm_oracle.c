@@ -40,6 +40,9 @@
  *     from the y-normal edge, xy the mean of both), no extrapolation.
  *   - if the upstream node x - c_i is void or across a cut link, the
  *     lattice-conforming form is used with rho^bd = rho(x), sigma^bd = sigma(x).
+ *   - option wall_node (not the paper's rule, off by default): rho^bd and
+ *     sigma^bd are the boundary node's own values instead of the extrapolation
+ *     along the link; the kappa terms of the curved rules are unchanged.
  *   - geometry: nodes at integer (i, j); the box is [-1/2, nx-1/2] x
  *     [-1/2, ny-1/2]; a node is void iff strictly inside the hole circle; a
  *     link is cut by the hole iff its end node is void, with s/l the smaller
@@ -289,6 +292,7 @@ typedef struct {
     int64_t nlinks;
     ora_bc *bcs;
     int32_t nbcs;
+    int32_t wall_node; /* 1: rho^bd, sigma^bd taken at the boundary node */
 } ora_solver;
 
 static int64_t neighbour(const ora_solver *s, int64_t k, int i) {
@@ -324,8 +328,10 @@ static void traction(const ora_bc *b, double n0, double n1, double t, double *ts
 
 void *ora_create(int32_t nx, int32_t ny, double lambda, double mu, double rho0, double tau,
                  double Fx, double Fy, int32_t per_x, int32_t per_y, const uint8_t *node_type,
-                 const ora_link *links, int64_t nlinks, const ora_bc *bcs, int32_t nbcs) {
+                 const ora_link *links, int64_t nlinks, const ora_bc *bcs, int32_t nbcs,
+                 int32_t wall_node) {
     ora_solver *s = (ora_solver *)calloc(1, sizeof *s);
+    s->wall_node = wall_node;
     s->nx = nx;
     s->ny = ny;
     s->per_x = per_x;
@@ -479,7 +485,8 @@ static double boundary_rule(const ora_solver *s, int64_t k, int i, const ora_lin
     double sx[2][2], su[2][2], sbd[2][2];
     cauchy(s, s->rho[k], s->pm + k * 3, sx);
     double rbd;
-    if (ku < 0) {
+    if (ku < 0 || s->wall_node) {
+        /* no usable upstream node, or wall values taken at the boundary node */
         rbd = s->rho[k];
         memcpy(sbd, sx, sizeof sx);
     } else {

@@ -1,0 +1,546 @@
+// lbm_capi.cu -- the C ABI of include/lbm.h: handle life cycle, device memory
+// layout, stepping (direct launches or replayed CUDA graphs), fields and probes.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+struct lbm_solver {
+    Tables tab;
+    Units units;
+    Lattice L;
+    DevState S;
+    int storage = LBM_F32;
+    cudaStream_t stream = nullptr;  // caller's stream
+    cudaStream_t cap_main = nullptr, cap_side = nullptr;  // private capture streams
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t gfork = nullptr, gjoin = nullptr;         // events used inside graphs
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};        // chunk starting in buffer 0/1
+    int cur = 0;
+    int64_t time = 0;
+    void *owned = nullptr;  // cudaMalloc'ed workspace, if the library allocated it
+    void *base = nullptr;
+    uint64_t bytes = 0;
+    int32_t *h_probe_idx = nullptr;  // pinned host staging for probes
+    float *h_probe_out = nullptr;
+    uint32_t *h_status = nullptr;    // pinned copy of the status word
+    cudaEvent_t status_ready = nullptr;
+    bool status_pending = false;
+    int64_t launches = 0;            // kernels launched by this handle
+    // timing mode: events around every interior and boundary kernel
+    bool timing = false;
+    std::vector<StepEvents> ev_pool;
+    size_t ev_used = 0;
+};
+
+namespace {
+
+constexpr int kGraphChunk = 32;  // steps per replayed graph (even: parity preserved)
+
+lbm_status cuda_fail(cudaError_t e, const char *where) {
+    set_error(std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return LBM_ERR_CUDA;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct Layout {
+    size_t f0, f1, ucomp, cls, bnodes, blinks, bcs, rho, status, time, stage, probe, probe_idx,
+        total;
+};
+
+Layout layout(const Tables &t, int storage, bool grad) {
+    const size_t plane = (size_t)t.pitch * t.ny;
+    const size_t esz = storage == LBM_F32 ? 4 : 2;
+    const size_t N = (size_t)t.nx * t.ny;
+    Layout l;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    l.f0 = take(9 * plane * esz);
+    l.f1 = take(9 * plane * esz);
+    l.ucomp = take(plane * sizeof(float4));
+    l.cls = take(plane);
+    l.bnodes = take(std::max<size_t>(1, t.bnodes.size()) * sizeof(BNode));
+    l.blinks = take(std::max<size_t>(1, t.blinks.size()) * sizeof(BLink));
+    l.bcs = take(t.bcs.size() * sizeof(BCDev));
+    l.rho = grad ? take(plane * sizeof(float)) : 0;
+    l.status = take(sizeof(uint32_t));
+    l.time = take(sizeof(int64_t));
+    l.stage = take(7 * N * sizeof(float));
+    l.probe = take(7 * (size_t)kMaxProbe * sizeof(float));
+    l.probe_idx = take((size_t)kMaxProbe * sizeof(int32_t));
+    l.total = o;
+    (void)grad;
+    return l;
+}
+
+Lattice make_lattice(const Tables &t, const Units &u, int storage) {
+    Lattice L;
+    std::memset(&L, 0, sizeof L);
+    L.nx = t.nx;
+    L.ny = t.ny;
+    L.pitch = t.pitch;
+    L.nb = (int32_t)t.bnodes.size();
+    L.plane = (int64_t)t.pitch * t.ny;
+    L.omega = (float)(1.0 / u.tau);
+    L.src = (float)(1.0 - 1.0 / (2.0 * u.tau));
+    L.fx = (float)u.fx;
+    L.fy = (float)u.fy;
+    L.mu_m_lam = (float)(u.mu - u.lam);
+    L.lam_m_mu_r0 = (float)((u.lam - u.mu) / u.rho0);
+    L.rho0 = (float)u.rho0;
+    L.inv_rho0 = (float)(1.0 / u.rho0);
+    // 16-bit storage: a power-of-two scale that maps the largest boundary value
+    // to about 8, leaving a factor 8000 below the FP16 maximum for stress
+    // concentrations (crack tips) and the normal range down to 1e-5 of the load
+    float scale = 1.0f;
+    if (storage != LBM_F32) {
+        const double a = t.max_load > 0.0f ? (double)t.max_load : 1e-3;
+        const int e = (int)std::floor(std::log2(8.0 / a));
+        scale = std::ldexp(1.0f, std::max(-30, std::min(60, e)));
+    }
+    L.scale = scale;
+    L.inv_scale = 1.0f / scale;
+    L.out_u = (float)u.dx;
+    L.out_v = (float)u.U;
+    L.out_s = (float)(u.U * u.U);
+    L.grad = (u.lam != u.mu) ? 1 : 0;
+    return L;
+}
+
+lbm_status prepare(const lbm_desc *desc, Tables *t, Units *u) {
+    if (!desc) {
+        set_error("NULL descriptor");
+        return LBM_ERR_ARG;
+    }
+    lbm_status st = make_units(*desc, u);
+    if (st != LBM_OK) return st;
+    return classify(*desc, *u, t);
+}
+
+void destroy_graphs(lbm_solver *h) {
+    for (auto &g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Capture kGraphChunk steps starting in buffer `start`, with the boundary
+// kernel on a side branch that runs beside the interior kernel.
+lbm_status build_graph(lbm_solver *h, int start) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_main, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_step: begin capture");
+    int cur = start;
+    for (int s = 0; s < kGraphChunk && e == cudaSuccess; ++s) {
+        e = launch_step(h->storage, h->L, h->S, cur, s, h->cap_main, h->cap_side, h->gfork,
+                        h->gjoin, nullptr);
+        cur ^= 1;
+    }
+    if (e == cudaSuccess) e = launch_advance(h->S, kGraphChunk, h->cap_main);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_main, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e != cudaSuccess ? e : e2, "lbm_step: capture");
+    }
+    e = cudaGraphInstantiate(&h->graph[start], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_step: instantiate");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_workspace_size(const lbm_desc *desc, uint64_t *bytes) {
+    set_error("");
+    if (!bytes) {
+        set_error("lbm_workspace_size: NULL output");
+        return LBM_ERR_ARG;
+    }
+    Tables t;
+    Units u;
+    lbm_status st = prepare(desc, &t, &u);
+    if (st != LBM_OK) return st;
+    *bytes = layout(t, desc->storage, u.lam != u.mu).total;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *workspace,
+                                 uint64_t workspace_bytes, lbm_handle *out) {
+    set_error("");
+    if (!out) {
+        set_error("lbm_create: NULL output handle");
+        return LBM_ERR_ARG;
+    }
+    *out = nullptr;
+    lbm_solver *h = new lbm_solver();
+    lbm_status st = prepare(desc, &h->tab, &h->units);
+    if (st != LBM_OK) {
+        delete h;
+        return st;
+    }
+    h->storage = desc->storage;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->L = make_lattice(h->tab, h->units, h->storage);
+    h->L.wall_node = desc->wall_values == LBM_WALL_NODE ? 1 : 0;
+    const Layout lay = layout(h->tab, h->storage, h->L.grad != 0);
+    h->bytes = lay.total;
+    cudaError_t e = cudaSuccess;
+    if (workspace) {
+        if (workspace_bytes < lay.total || (reinterpret_cast<uintptr_t>(workspace) & 255u)) {
+            set_error("lbm_create: workspace smaller than lbm_workspace_size() or not 256-byte aligned");
+            delete h;
+            return LBM_ERR_NOMEM;
+        }
+        h->base = workspace;
+    } else {
+        size_t free_b = 0, total_b = 0;
+        e = cudaMemGetInfo(&free_b, &total_b);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "lbm_create: cudaMemGetInfo");
+        }
+        if (lay.total > free_b) {
+            set_error("lbm_create: needs " + std::to_string(lay.total) + " device bytes, " +
+                      std::to_string(free_b) + " free");
+            delete h;
+            return LBM_ERR_NOMEM;
+        }
+        e = cudaMalloc(&h->owned, lay.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            set_error("lbm_create: cudaMalloc failed");
+            return LBM_ERR_NOMEM;
+        }
+        h->base = h->owned;
+    }
+    char *b = static_cast<char *>(h->base);
+    DevState &S = h->S;
+    S.f[0] = b + lay.f0;
+    S.f[1] = b + lay.f1;
+    S.ucomp = reinterpret_cast<float4 *>(b + lay.ucomp);
+    S.cls = reinterpret_cast<uint8_t *>(b + lay.cls);
+    S.bnodes = reinterpret_cast<BNode *>(b + lay.bnodes);
+    S.blinks = reinterpret_cast<BLink *>(b + lay.blinks);
+    S.bcs = reinterpret_cast<BCDev *>(b + lay.bcs);
+    S.rho = h->L.grad ? reinterpret_cast<float *>(b + lay.rho) : nullptr;
+    S.status = reinterpret_cast<uint32_t *>(b + lay.status);
+    S.time = reinterpret_cast<int64_t *>(b + lay.time);
+    S.stage = reinterpret_cast<float *>(b + lay.stage);
+    S.probe = reinterpret_cast<float *>(b + lay.probe);
+    S.probe_idx = reinterpret_cast<int32_t *>(b + lay.probe_idx);
+
+    auto fail = [&](cudaError_t err, const char *where) {
+        lbm_status s = cuda_fail(err, where);
+        lbm_destroy(h);
+        return s;
+    };
+    const Tables &t = h->tab;
+    e = cudaMemcpyAsync(S.cls, t.cls.data(), t.cls.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !t.bnodes.empty())
+        e = cudaMemcpyAsync(S.bnodes, t.bnodes.data(), t.bnodes.size() * sizeof(BNode),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !t.blinks.empty())
+        e = cudaMemcpyAsync(S.blinks, t.blinks.data(), t.blinks.size() * sizeof(BLink),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S.bcs, t.bcs.data(), t.bcs.size() * sizeof(BCDev),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_reset(h->storage, h->L, S, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(e, "lbm_create: upload");
+    e = cudaStreamCreateWithFlags(&h->cap_main, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gjoin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_probe_idx, kMaxProbe * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_probe_out, 7 * kMaxProbe * sizeof(float));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_status, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->status_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) *h->h_status = 0;
+    if (e != cudaSuccess) return fail(e, "lbm_create: streams/events");
+    *out = h;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
+    set_error("");
+    if (!h || nsteps < 0) {
+        set_error("lbm_step: bad handle or negative step count");
+        return LBM_ERR_ARG;
+    }
+    // status of work queued by an earlier call, if the device has finished it
+    if (h->status_pending) {
+        const cudaError_t q = cudaEventQuery(h->status_ready);
+        if (q == cudaSuccess) {
+            h->status_pending = false;
+            if (*h->h_status & 1u) {
+                set_error("lbm_step: a non-finite moment was produced (unstable run)");
+                return LBM_ERR_UNSTABLE;
+            }
+        } else if (q == cudaErrorNotReady) {
+            cudaGetLastError();  // clear the not-ready code so later launch checks see only real errors
+        } else {
+            return cuda_fail(q, "lbm_step: status query");
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    int64_t done = 0;
+    const int per_step = kernels_per_step(h->L);
+    if (h->timing) {
+        // kernels one by one, interior and boundary bracketed by events
+        for (int64_t s = 0; s < nsteps; ++s) {
+            if (h->ev_used == h->ev_pool.size()) {
+                StepEvents ev{};
+                e = cudaEventCreate(&ev.before_interior);
+                if (e == cudaSuccess) e = cudaEventCreate(&ev.after_interior);
+                if (e == cudaSuccess) e = cudaEventCreate(&ev.before_boundary);
+                if (e == cudaSuccess) e = cudaEventCreate(&ev.after_boundary);
+                if (e != cudaSuccess) return cuda_fail(e, "lbm_step: timing events");
+                h->ev_pool.push_back(ev);
+            }
+            e = launch_step(h->storage, h->L, h->S, h->cur, (int)s, h->stream, h->cap_side,
+                            h->fork, h->join, &h->ev_pool[h->ev_used++]);
+            if (e != cudaSuccess) return cuda_fail(e, "lbm_step: launch");
+            h->cur ^= 1;
+        }
+        h->launches += nsteps * per_step;
+        done = nsteps;
+    }
+    if (nsteps - done >= kGraphChunk) {
+        // the graph runs on the caller's stream
+        for (; done + kGraphChunk <= nsteps; done += kGraphChunk) {
+            if (!h->graph[h->cur]) {
+                lbm_status st = build_graph(h, h->cur);
+                if (st != LBM_OK) return st;
+            }
+            e = cudaGraphLaunch(h->graph[h->cur], h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "lbm_step: graph launch");
+            h->launches += kGraphChunk * per_step + 1;
+        }
+    }
+    const int64_t rest = nsteps - done;
+    for (int64_t s = 0; s < rest; ++s) {
+        e = launch_step(h->storage, h->L, h->S, h->cur, (int)s, h->stream, nullptr, nullptr,
+                        nullptr, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_step: launch");
+        h->cur ^= 1;
+    }
+    h->launches += rest * per_step;
+    const int64_t direct = rest + (h->timing ? nsteps : 0);
+    if (direct > 0) {
+        e = launch_advance(h->S, direct, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_step: advance");
+        h->launches += 1;
+    }
+    h->time += nsteps;
+    if (nsteps > 0 && !h->status_pending) {
+        e = cudaMemcpyAsync(h->h_status, h->S.status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                            h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->status_ready, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_step: status copy");
+        h->status_pending = true;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_fields(lbm_handle h, float *u, float *v, float *sigma,
+                                     int32_t on_device) {
+    set_error("");
+    if (!h) {
+        set_error("lbm_get_fields: NULL handle");
+        return LBM_ERR_ARG;
+    }
+    cudaError_t e = launch_fields(h->storage, h->L, h->S, h->cur, u, v, sigma, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_get_fields");
+    h->launches += kernels_per_fields(h->L);
+    if (!on_device) {
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_get_fields: sync");
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_probe(lbm_handle h, const int32_t *nodes, int32_t count, float *out) {
+    set_error("");
+    if (!h || count < 0 || count > kMaxProbe || (count > 0 && (!nodes || !out))) {
+        set_error("lbm_probe: bad arguments (at most 4096 nodes)");
+        return LBM_ERR_ARG;
+    }
+    if (count == 0) return LBM_OK;
+    const int64_t N = (int64_t)h->L.nx * h->L.ny;
+    for (int32_t p = 0; p < count; ++p) {
+        if (nodes[p] < 0 || nodes[p] >= N) {
+            set_error("lbm_probe: node index out of range");
+            return LBM_ERR_ARG;
+        }
+        h->h_probe_idx[p] = nodes[p];
+    }
+    cudaError_t e = cudaMemcpyAsync(h->S.probe_idx, h->h_probe_idx, count * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = launch_fields(h->storage, h->L, h->S, h->cur, nullptr, nullptr, nullptr, h->stream);
+    if (e == cudaSuccess) e = launch_gather_probe(h->L, h->S, count, h->stream);
+    h->launches += kernels_per_fields(h->L) + 1;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->h_probe_out, h->S.probe, 7 * (size_t)count * sizeof(float),
+                            cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_probe");
+    std::memcpy(out, h->h_probe_out, 7 * (size_t)count * sizeof(float));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_bc(lbm_handle h, int32_t index, const lbm_bc *bc) {
+    set_error("");
+    if (!h || !bc || index < 0 || index >= (int32_t)h->tab.bcs.size()) {
+        set_error("lbm_set_bc: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    if (bc->kind != h->tab.bcs[index].kind) {
+        // the bounce-back / anti-bounce-back choice is baked into the link tables
+        set_error("lbm_set_bc: the kind of a boundary condition cannot change");
+        return LBM_ERR_ARG;
+    }
+    if ((bc->profile != LBM_PROFILE_STEP && bc->profile != LBM_PROFILE_RAMP) ||
+        !std::isfinite(bc->value[0]) || !std::isfinite(bc->value[1]) ||
+        !std::isfinite(bc->value[2]) || (bc->profile == LBM_PROFILE_RAMP && !(bc->t_ramp > 0.0))) {
+        set_error("lbm_set_bc: bad boundary condition");
+        return LBM_ERR_ARG;
+    }
+    h->tab.bcs[index] = to_lattice(*bc, h->units);
+    // bounded by the table size; stream-ordered with the steps
+    cudaError_t e = cudaMemcpyAsync(h->S.bcs + index, &h->tab.bcs[index], sizeof(BCDev),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_set_bc");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_reset(lbm_handle h) {
+    set_error("");
+    if (!h) {
+        set_error("lbm_reset: NULL handle");
+        return LBM_ERR_ARG;
+    }
+    cudaError_t e = launch_reset(h->storage, h->L, h->S, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_reset");
+    h->cur = 0;
+    h->time = 0;
+    h->launches += 0;  // the reset is memsets, not kernels
+    if (h->status_pending) cudaEventSynchronize(h->status_ready);
+    h->status_pending = false;
+    *h->h_status = 0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_sync(lbm_handle h) {
+    set_error("");
+    if (!h) {
+        set_error("lbm_sync: NULL handle");
+        return LBM_ERR_ARG;
+    }
+    uint32_t status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, h->S.status, sizeof status, cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_sync");
+    if (status & 1u) {
+        set_error("lbm_sync: a non-finite moment was produced (unstable run)");
+        return LBM_ERR_UNSTABLE;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_info(lbm_handle h, lbm_info *info) {
+    set_error("");
+    if (!h || !info) {
+        set_error("lbm_get_info: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    info->nx = h->L.nx;
+    info->ny = h->L.ny;
+    info->pitch = h->L.pitch;
+    info->storage = h->storage;
+    info->time = h->time;
+    info->boundary_nodes = h->L.nb;
+    info->interior_nodes = h->tab.interior;
+    info->workspace_bytes = h->bytes;
+    info->storage_scale = h->L.scale;
+    const float esz = h->storage == LBM_F32 ? 4.0f : 2.0f;
+    info->bytes_per_update = 2.0f * 9.0f * esz + 32.0f;  // f read + write, u and compensation R+W
+    info->kernel_launches = h->launches;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_timing(lbm_handle h, int32_t enable) {
+    set_error("");
+    if (!h) {
+        set_error("lbm_set_timing: NULL handle");
+        return LBM_ERR_ARG;
+    }
+    h->timing = enable != 0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_timing(lbm_handle h, lbm_timing *out) {
+    set_error("");
+    if (!h || !out) {
+        set_error("lbm_get_timing: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    std::memset(out, 0, sizeof *out);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_get_timing: sync");
+    for (size_t k = 0; k < h->ev_used; ++k) {
+        float a = 0.0f, b = 0.0f;
+        e = cudaEventElapsedTime(&a, h->ev_pool[k].before_interior, h->ev_pool[k].after_interior);
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&b, h->ev_pool[k].before_boundary, h->ev_pool[k].after_boundary);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_get_timing: elapsed");
+        out->interior_ms += a;
+        out->boundary_ms += b;
+    }
+    out->steps = (int64_t)h->ev_used;
+    h->ev_used = 0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_destroy(lbm_handle h) {
+    if (!h) return LBM_OK;
+    if (h->stream || h->owned) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    if (h->cap_main) cudaStreamDestroy(h->cap_main);
+    if (h->cap_side) cudaStreamDestroy(h->cap_side);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
+    if (h->gfork) cudaEventDestroy(h->gfork);
+    if (h->gjoin) cudaEventDestroy(h->gjoin);
+    if (h->h_probe_idx) cudaFreeHost(h->h_probe_idx);
+    if (h->h_probe_out) cudaFreeHost(h->h_probe_out);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->status_ready) cudaEventDestroy(h->status_ready);
+    for (auto &ev : h->ev_pool) {
+        cudaEventDestroy(ev.before_interior);
+        cudaEventDestroy(ev.after_interior);
+        cudaEventDestroy(ev.before_boundary);
+        cudaEventDestroy(ev.after_boundary);
+    }
+    if (h->owned) cudaFree(h->owned);
+    delete h;
+    return LBM_OK;
+}

@@ -1,0 +1,137 @@
+// lbm_internal.h -- layouts shared by the host classifier, the kernels and the
+// C ABI of the GB300 solid-LBM library.  Not part of the public interface
+// (include/lbm.h is).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// D2Q9 numbering (0 rest, 1 +x, 2 +y, 3 -x, 4 -y, 5 (+,+), 6 (-,+), 7 (-,-),
+// 8 (+,-)) -- the same numbering the public header states.
+constexpr int kQ = 9;
+constexpr int kCx[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+constexpr int kCy[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+constexpr int kOpp[kQ] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+// Node classes in the per-node class array.
+enum : uint8_t { kVoid = 0, kInterior = 1, kBoundary = 2 };
+
+// One boundary node of the compacted list.  Bit i (1..8) of each mask refers
+// to the link from the node towards node + c_i.
+struct BNode {
+    int32_t x, y;
+    uint16_t cut;     // link i crosses a wall
+    uint16_t dirich;  // cut link i takes the bounce-back rule (Dirichlet)
+    uint16_t corner;  // cut link i is a Neumann corner link
+    uint16_t miss;    // upstream node x - c_i of cut link i is unusable
+};
+static_assert(sizeof(BNode) == 16, "BNode layout");
+
+// Per (boundary node, direction 1..8) slot; meaningful where the cut bit is set.
+struct BLink {
+    float q;        // s/l
+    float n0, n1;   // outward unit normal (corner: the two edge-normal signs)
+    uint16_t bc;    // Dirichlet: first Dirichlet edge; Neumann: x-normal edge
+    uint16_t bc2;   // Dirichlet: second Dirichlet edge (or bc); corner: y-normal edge
+};
+static_assert(sizeof(BLink) == 16, "BLink layout");
+
+// Boundary condition in lattice units.
+struct BCDev {
+    int32_t kind, profile;
+    float v0, v1, v2;
+    float t_ramp;  // steps
+};
+static_assert(sizeof(BCDev) == 24, "BCDev layout");
+
+// Scalar parameters of one lattice, passed by value to every kernel.
+struct Lattice {
+    int32_t nx, ny, pitch, nb;  // nb: number of boundary nodes
+    int64_t plane;              // elements per population plane (pitch * ny)
+    float omega;                // 1/tau
+    float src;                  // 1 - 1/(2 tau), Eq. (coll)
+    float fx, fy;               // body force, lattice units
+    float mu_m_lam;             // mu - lambda (lattice units), Eq. (sourceterm)
+    float lam_m_mu_r0;          // (lambda - mu)/rho0, Eqs. (poissonstress), (approxdiv)
+    float rho0, inv_rho0;
+    float scale, inv_scale;     // 16-bit storage scale (1 for FP32)
+    float out_u, out_v, out_s;  // lattice -> physical units for the fields
+    int32_t grad;               // lambda != mu: the source needs grad rho
+    int32_t wall_node;          // Neumann wall values at the boundary node (no extrapolation)
+};
+
+// Host-side result of validating and classifying an lbm_desc.
+struct Tables {
+    int32_t nx = 0, ny = 0, pitch = 0;
+    std::vector<uint8_t> cls;    // [ny][pitch]
+    std::vector<BNode> bnodes;   // canonical order (row-major)
+    std::vector<BLink> blinks;   // [nb][8]
+    std::vector<BCDev> bcs;
+    int64_t interior = 0;
+    float max_load = 0.0f;       // largest boundary-value magnitude (lattice units)
+};
+
+// Unit conversion from lbm_desc to lattice units.
+struct Units {
+    double U = 1.0;       // dx/dt
+    double dx = 1.0, dt = 1.0;
+    double lam = 0.0, mu = 0.0, rho0 = 1.0, tau = 0.55;
+    double fx = 0.0, fy = 0.0;
+};
+
+// Thread-local error text for lbm_last_error().
+void set_error(const std::string &msg);
+
+lbm_status make_units(const lbm_desc &d, Units *u);
+BCDev to_lattice(const lbm_bc &b, const Units &u);
+lbm_status classify(const lbm_desc &d, const Units &u, Tables *t);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (lbm_kernels.cu).  `cur` holds f^col(t-1), `nxt` receives
+// f^col(t).  d_time holds the number of completed steps; a launch with offset
+// `toff` computes f at time t = *d_time + toff.
+struct DevState {
+    void *f[2] = {nullptr, nullptr};  // two distribution buffers (9 planes each)
+    float4 *ucomp = nullptr;          // (u_x, u_y, kahan_x, kahan_y) per node
+    uint8_t *cls = nullptr;
+    BNode *bnodes = nullptr;
+    BLink *blinks = nullptr;
+    BCDev *bcs = nullptr;
+    float *rho = nullptr;             // density deviation at the current time (lambda != mu)
+    uint32_t *status = nullptr;       // bit 0: non-finite moment seen
+    int64_t *time = nullptr;
+    float *stage = nullptr;           // field staging [7][ny][nx]
+    float *probe = nullptr;           // probe staging [7][max_probe]
+    int32_t *probe_idx = nullptr;
+};
+
+constexpr int kMaxProbe = 4096;
+
+// Events recorded around the interior and boundary kernels of one step (timing
+// mode).  With a side stream the boundary kernel runs beside the interior one,
+// as in the replayed graphs.
+struct StepEvents {
+    cudaEvent_t before_interior, after_interior;  // on the main stream
+    cudaEvent_t before_boundary, after_boundary;  // on the stream of the boundary kernel
+};
+
+cudaError_t launch_step(int storage, const Lattice &L, const DevState &S, int cur, int toff,
+                        cudaStream_t s_main, cudaStream_t s_side, cudaEvent_t fork,
+                        cudaEvent_t join, const StepEvents *ev);
+int kernels_per_step(const Lattice &L);
+int kernels_per_fields(const Lattice &L);
+cudaError_t launch_advance(const DevState &S, int64_t n, cudaStream_t s);
+cudaError_t launch_fields(int storage, const Lattice &L, const DevState &S, int cur,
+                          float *u, float *v, float *sigma, cudaStream_t s);
+cudaError_t launch_gather_probe(const Lattice &L, const DevState &S, int count,
+                                cudaStream_t s);
+cudaError_t launch_reset(int storage, const Lattice &L, const DevState &S, cudaStream_t s);
+
+}  // namespace lbm

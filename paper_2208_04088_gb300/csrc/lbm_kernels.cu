@@ -1,0 +1,632 @@
+// lbm_kernels.cu -- sm_103a kernels of the solid lattice Boltzmann method
+// (arXiv 2208.04088): one time step is
+//   [density pass, lambda != mu only]  rho(t) at every material node
+//   interior kernel   pull-stream + moments + BGK with source + store + u
+//   boundary kernel   the same for the compacted list of boundary nodes, with
+//                     the populations arriving across a wall replaced by the
+//                     rules of Sec. 4
+// Distributions are stored as deviations from the zero-stress rest state,
+// delta f = f - f^eq(rho0, 0, 0), in structure-of-arrays planes
+// [9][ny][pitch].  The buffer holds f^col(t-1); a step pulls f_i(x, t) =
+// f_i^col(x - c_i, t-1) (Eq. stream), collides (Eq. coll) and writes f^col(x, t).
+// All arithmetic is FP32.  The rest state is a fixed point of every rule, so
+// each rule acts on the deviations with the same coefficients it has for f.
+#include <cstdint>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Storage of one population value (FP32, or 16-bit scaled deviations).
+template <class T>
+struct Store;
+
+template <>
+struct Store<float> {
+    static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
+};
+
+template <>
+struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half *p, float inv_scale) {
+        return __half2float(__ldg(p)) * inv_scale;
+    }
+    static __device__ __forceinline__ void st(__half *p, float v, float scale) {
+        *p = __float2half_rn(v * scale);
+    }
+};
+
+template <>
+struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float inv_scale) {
+        return __bfloat162float(__ldg(p)) * inv_scale;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float scale) {
+        *p = __float2bfloat16_rn(v * scale);
+    }
+};
+
+// D2Q9 velocity components and opposite directions as constant expressions.
+__host__ __device__ constexpr int c_cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ constexpr int c_cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5);
+}
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2 && opp(5) == 7 &&
+                  opp(6) == 8 && opp(7) == 5 && opp(8) == 6,
+              "opposite directions");
+
+// ---------------------------------------------------------------------------
+// Raw moments m_pq = sum_i f_i c_ix^p c_iy^q (p, q in 0..2) of the nine
+// populations.  D2Q9 is the tensor product of {-1, 0, 1} in x and y, so the
+// transform is two passes of the 1-D map (a-, a0, a+) -> (a- + a0 + a+,
+// a+ - a-, a+ + a-), whose inverse has only the coefficients 1 and 1/2: the
+// round trip adds nothing but additions to the rounding.
+struct Raw {
+    float m00, m10, m01, m20, m02, m11, m21, m12, m22;
+};
+
+__device__ __forceinline__ Raw raw_moments(const float f[9]) {
+    // rows c_y = -1: (f7, f4, f8); c_y = 0: (f3, f0, f1); c_y = +1: (f6, f2, f5)
+    const float a0 = (f[7] + f[4]) + f[8], a1 = f[8] - f[7], a2 = f[8] + f[7];
+    const float b0 = (f[3] + f[0]) + f[1], b1 = f[1] - f[3], b2 = f[1] + f[3];
+    const float c0 = (f[6] + f[2]) + f[5], c1 = f[5] - f[6], c2 = f[5] + f[6];
+    Raw m;
+    m.m00 = (a0 + b0) + c0;
+    m.m01 = c0 - a0;
+    m.m02 = c0 + a0;
+    m.m10 = (a1 + b1) + c1;
+    m.m11 = c1 - a1;
+    m.m12 = c1 + a1;
+    m.m20 = (a2 + b2) + c2;
+    m.m21 = c2 - a2;
+    m.m22 = c2 + a2;
+    return m;
+}
+
+__device__ __forceinline__ void populations(const Raw &m, float f[9]) {
+    // inverse in y for each x-order p, then inverse in x for each row
+    const float a0 = 0.5f * (m.m02 - m.m01), b0 = m.m00 - m.m02, c0 = 0.5f * (m.m02 + m.m01);
+    const float a1 = 0.5f * (m.m12 - m.m11), b1 = m.m10 - m.m12, c1 = 0.5f * (m.m12 + m.m11);
+    const float a2 = 0.5f * (m.m22 - m.m21), b2 = m.m20 - m.m22, c2 = 0.5f * (m.m22 + m.m21);
+    f[7] = 0.5f * (a2 - a1);
+    f[4] = a0 - a2;
+    f[8] = 0.5f * (a2 + a1);
+    f[3] = 0.5f * (b2 - b1);
+    f[0] = b0 - b2;
+    f[1] = 0.5f * (b2 + b1);
+    f[6] = 0.5f * (c2 - c1);
+    f[2] = c0 - c2;
+    f[5] = 0.5f * (c2 + c1);
+}
+
+// Moments of Eq. (moments) in deviation form: drho, m = sum f c (without S/2), P.
+struct Mom {
+    float dr, mx, my, pxx, pyy, pxy;
+};
+
+__device__ __forceinline__ Mom moments(const float f[9]) {
+    const Raw r = raw_moments(f);
+    return Mom{r.m00, r.m10, r.m01, r.m20, r.m02, r.m11};
+}
+
+// BGK collision with source (Eq. coll) carried out on the raw moments.  The
+// map f -> f + omega (f^eq - f) + (1 - 1/(2 tau)) psi is the same linear map in
+// any basis; in this one the raw moments of f^eq (Eq. fieq, c_s^2 = 1/3) are
+//   rho, j, P                     (the moments the equilibrium reproduces)
+//   m_xxy = j_y/3, m_xyy = j_x/3  (third moment c_s^2 (j d + j d + j d))
+//   m_xxyy = (P_xx + P_yy)/3 - rho/9,
+// and those of psi_i = 3 w_i c_i.S are S in the first and S/3 in the third
+// moments.  rho and P pass through untouched and j gains exactly S, so the
+// collision invariants are not disturbed by the rounding of 1/3 and 1/9.
+// On return f holds f^col, jx/jy the momentum j = m + S/2, dr the density deviation.
+__device__ __forceinline__ void collide(float f[9], float sx, float sy, const Lattice &L,
+                                        float &dr_out, float &jx_out, float &jy_out) {
+    Raw m = raw_moments(f);
+    const float jx = m.m10 + 0.5f * sx, jy = m.m01 + 0.5f * sy;
+    const float w = L.omega;
+    const float s3 = L.src * (1.0f / 3.0f);
+    m.m10 += sx;
+    m.m01 += sy;
+    m.m21 += w * (jy * (1.0f / 3.0f) - m.m21) + s3 * sy;
+    m.m12 += w * (jx * (1.0f / 3.0f) - m.m12) + s3 * sx;
+    m.m22 += w * ((m.m20 + m.m02) * (1.0f / 3.0f) - m.m00 * (1.0f / 9.0f) - m.m22);
+    dr_out = m.m00;
+    jx_out = jx;
+    jy_out = jy;
+    populations(m, f);
+}
+
+// u(t+1) = u(t) + j/rho with Kahan compensation per component.
+__device__ __forceinline__ void integrate_u(float4 *uc, float jx, float jy, float rho) {
+    float4 w = *uc;
+    const float vx = jx / rho, vy = jy / rho;
+    float y = vx - w.z;
+    float t = w.x + y;
+    w.z = (t - w.x) - y;
+    w.x = t;
+    y = vy - w.w;
+    t = w.y + y;
+    w.w = (t - w.y) - y;
+    w.y = t;
+    *uc = w;
+}
+
+__device__ __forceinline__ void flag_nonfinite(uint32_t *status, float a, float b, float c) {
+    if (!isfinite(a + b + c)) atomicOr(status, 1u);
+}
+
+// Amplitude of a boundary value at (lattice) time t: step or ramp-then-hold.
+__device__ __forceinline__ float amplitude(const BCDev &b, float t) {
+    if (t < 0.0f) return 0.0f;
+    if (b.profile == LBM_PROFILE_RAMP) return fminf(t / b.t_ramp, 1.0f);
+    return 1.0f;
+}
+
+// Traction t*(t) of a Neumann condition on a wall with outward normal n.
+__device__ __forceinline__ void traction(const BCDev &b, float n0, float n1, float t, float &tx,
+                                         float &ty) {
+    const float a = amplitude(b, t);
+    if (b.kind == LBM_BC_PRESSURE) {
+        tx = -b.v0 * n0 * a;
+        ty = -b.v0 * n1 * a;
+    } else if (b.kind == LBM_BC_STRESS) {
+        tx = (b.v0 * n0 + b.v2 * n1) * a;
+        ty = (b.v2 * n0 + b.v1 * n1) * a;
+    } else {
+        tx = b.v0 * a;
+        ty = b.v1 * a;
+    }
+}
+
+// Interior pull: f_i(x, t) = f_i^col(x - c_i, t - 1).
+template <class T>
+__device__ __forceinline__ void pull_interior(const T *__restrict__ src, int64_t k, int pitch,
+                                              int64_t plane, float inv_scale, float f[9]) {
+    f[0] = Store<T>::ld(src + k, inv_scale);
+    f[1] = Store<T>::ld(src + plane + k - 1, inv_scale);
+    f[2] = Store<T>::ld(src + 2 * plane + k - pitch, inv_scale);
+    f[3] = Store<T>::ld(src + 3 * plane + k + 1, inv_scale);
+    f[4] = Store<T>::ld(src + 4 * plane + k + pitch, inv_scale);
+    f[5] = Store<T>::ld(src + 5 * plane + k - pitch - 1, inv_scale);
+    f[6] = Store<T>::ld(src + 6 * plane + k - pitch + 1, inv_scale);
+    f[7] = Store<T>::ld(src + 7 * plane + k + pitch + 1, inv_scale);
+    f[8] = Store<T>::ld(src + 8 * plane + k + pitch - 1, inv_scale);
+}
+
+// Populations f(x, t) of a boundary node: pulled where the link is intact,
+// otherwise given by Eqs. (bbnoncon)/(abbnoncon) (which reduce to Eqs. bbcon/
+// abbcon at s = l/2) from f^col(., t-1), rho(., t-1), sigma(., t-1) and the
+// boundary data at t-1.  rho and P are collision invariants, so their values
+// at t-1 are the moments of the stored post-collision populations.
+template <class T>
+__device__ void pull_boundary(const T *__restrict__ src, const BNode &b,
+                              const BLink *__restrict__ links, const BCDev *__restrict__ bcs,
+                              float tb, const Lattice &L, float f[9]) {
+    const int64_t k = (int64_t)b.y * L.pitch + b.x;
+    const int64_t P = L.plane;
+    float gx[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) gx[i] = Store<T>::ld(src + i * P + k, L.inv_scale);
+    const Mom mx = moments(gx);
+    // Cauchy stress at x (Eq. poissonstress with Eq. approxdiv), deviation form
+    const float dvx = -L.lam_m_mu_r0 * mx.dr;
+    const float sxx_x = -mx.pxx + dvx, syy_x = -mx.pyy + dvx, sxy_x = -mx.pxy;
+
+    f[0] = gx[0];
+#pragma unroll
+    for (int kk = 1; kk < 9; ++kk) {
+        // population kk arrives through the link i = opp(kk), from x + c_i
+        const int i = opp(kk);
+        const uint32_t bit = 1u << i;
+        if (!(b.cut & bit)) {
+            const int64_t src_k = k - (int64_t)c_cy(kk) * L.pitch - c_cx(kk);
+            f[kk] = Store<T>::ld(src + kk * P + src_k, L.inv_scale);
+            continue;
+        }
+        const BLink lk = links[i - 1];
+        const bool miss = (b.miss & bit) != 0;
+        const float q = miss ? 0.5f : lk.q;
+        const float kap = (1.0f - 2.0f * q) / (1.0f + 2.0f * q);
+        const float fac = 2.0f / (1.0f + 2.0f * q);  // 1 + kappa = 2 l/(l + 2 s)
+        const float w = (i <= 4) ? (1.0f / 9.0f) : (1.0f / 36.0f);
+        const float cix = (float)c_cx(i), ciy = (float)c_cy(i);
+        // upstream node x - c_i
+        float gy_i = 0.0f, gy[9];
+        const int64_t ku = k - (int64_t)c_cy(i) * L.pitch - c_cx(i);
+        if (b.dirich & bit) {
+            if (!miss) gy_i = Store<T>::ld(src + i * P + ku, L.inv_scale);
+            const BCDev ba = bcs[lk.bc], bb = bcs[lk.bc2];
+            const float aa = amplitude(ba, tb), ab = amplitude(bb, tb);
+            // j* = rho0 d(u*)/dt (Eq. bcchaindir); corners: mean of the Dirichlet edges
+            const float jsx = L.rho0 * 0.5f * (ba.v0 * aa + bb.v0 * ab);
+            const float jsy = L.rho0 * 0.5f * (ba.v1 * aa + bb.v1 * ab);
+            const float cj = cix * jsx + ciy * jsy;
+            // Eq. (bbnoncon); kappa = 0 and 1 + kappa = 1 give Eq. (bbcon)
+            f[kk] = gx[i] + kap * (gy_i - gx[kk]) - fac * (6.0f * w) * cj;
+            continue;
+        }
+        // Neumann: density and stress at the wall by extrapolation along the link
+        // (or the node's own values with the wall-node option)
+        float drb = mx.dr, sbxx = sxx_x, sbyy = syy_x, sbxy = sxy_x;
+        if (!miss && L.wall_node) {
+            gy_i = Store<T>::ld(src + i * P + ku, L.inv_scale);
+        } else if (!miss) {
+#pragma unroll
+            for (int m = 0; m < 9; ++m) gy[m] = Store<T>::ld(src + m * P + ku, L.inv_scale);
+            gy_i = gy[i];
+            const Mom my = moments(gy);
+            const float dvy = -L.lam_m_mu_r0 * my.dr;
+            const float a1 = 1.0f + q;
+            drb = a1 * mx.dr - q * my.dr;
+            sbxx = a1 * sxx_x - q * (-my.pxx + dvy);
+            sbyy = a1 * syy_x - q * (-my.pyy + dvy);
+            sbxy = a1 * sxy_x - q * (-my.pxy);
+        }
+        float sxx, syy, sxy;  // sigma* (Eq. trafocauchy)
+        if (b.corner & bit) {
+            float tax, tay, tbx, tby;
+            traction(bcs[lk.bc], lk.n0, 0.0f, tb, tax, tay);
+            traction(bcs[lk.bc2], 0.0f, lk.n1, tb, tbx, tby);
+            sxx = tax * lk.n0;
+            syy = tby * lk.n1;
+            sxy = 0.5f * (tay * lk.n0 + tbx * lk.n1);
+        } else {
+            const float n0 = lk.n0, n1 = lk.n1, t0 = -n1, t1 = n0;  // e^n, e^t
+            float tx, ty;
+            traction(bcs[lk.bc], n0, n1, tb, tx, ty);
+            const float tn = tx * n0 + ty * n1, tt = tx * t0 + ty * t1;
+            const float stt = t0 * t0 * sbxx + 2.0f * t0 * t1 * sbxy + t1 * t1 * sbyy;
+            sxx = tn * n0 * n0 + 2.0f * tt * n0 * t0 + stt * t0 * t0;
+            syy = tn * n1 * n1 + 2.0f * tt * n1 * t1 + stt * t1 * t1;
+            sxy = tn * n0 * n1 + tt * (n0 * t1 + t0 * n1) + stt * t0 * t1;
+        }
+        // P* = -sigma* + (lambda - mu) div u I, div u = (rho0 - rho^bd)/rho0 (Eq. bcchainneum)
+        const float dv = -L.lam_m_mu_r0 * drb;
+        const float pxx = -sxx + dv, pyy = -syy + dv, pxy = -sxy;
+        const float axx = pxx - drb * (1.0f / 3.0f), ayy = pyy - drb * (1.0f / 3.0f);
+        const float con = 4.5f * (cix * cix * axx + 2.0f * cix * ciy * pxy + ciy * ciy * ayy -
+                                  (axx + ayy) * (1.0f / 3.0f));
+        const float eq = 2.0f * w * (drb + con);
+        // Eq. (abbnoncon); kappa = 0 and 1 + kappa = 1 give Eq. (abbcon)
+        f[kk] = -gx[i] - kap * (gy_i + gx[kk]) + fac * eq;
+    }
+}
+
+// Source S = F + (mu - lambda)/rho grad rho at an interior node (central
+// differences).  `drho` holds density deviations rho - rho0, so the differences
+// do not cancel against rho0.
+__device__ __forceinline__ void source_interior(const float *__restrict__ drho, int64_t k, int pitch,
+                                                float drho_k, const Lattice &L, float &sx,
+                                                float &sy) {
+    sx = L.fx;
+    sy = L.fy;
+    if (L.grad) {
+        const float gx = 0.5f * (__ldg(drho + k + 1) - __ldg(drho + k - 1));
+        const float gy = 0.5f * (__ldg(drho + k + pitch) - __ldg(drho + k - pitch));
+        const float c = L.mu_m_lam / (L.rho0 + drho_k);
+        sx += c * gx;
+        sy += c * gy;
+    }
+}
+
+// Same at a boundary node: one-sided where a neighbour is across a wall.
+__device__ __forceinline__ void source_boundary(const float *__restrict__ rho, const BNode &b,
+                                                int64_t k, float drho_k, const Lattice &L,
+                                                float &sx, float &sy) {
+    sx = L.fx;
+    sy = L.fy;
+    if (!L.grad) return;
+    const bool xp = !(b.cut & (1u << 1)), xm = !(b.cut & (1u << 3));
+    const bool yp = !(b.cut & (1u << 2)), ym = !(b.cut & (1u << 4));
+    const float r0 = rho[k];
+    float gx = 0.0f, gy = 0.0f;
+    if (xp && xm) gx = 0.5f * (rho[k + 1] - rho[k - 1]);
+    else if (xp) gx = rho[k + 1] - r0;
+    else if (xm) gx = r0 - rho[k - 1];
+    if (yp && ym) gy = 0.5f * (rho[k + L.pitch] - rho[k - L.pitch]);
+    else if (yp) gy = rho[k + L.pitch] - r0;
+    else if (ym) gy = r0 - rho[k - L.pitch];
+    const float c = L.mu_m_lam / (L.rho0 + drho_k);
+    sx += c * gx;
+    sy += c * gy;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels.
+constexpr int kBX = 32, kBY = 8;
+
+template <class T>
+__global__ void __launch_bounds__(kBX *kBY) k_interior(const T *__restrict__ src, T *__restrict__ dst,
+                                                       float4 *__restrict__ uc,
+                                                       const uint8_t *__restrict__ cls,
+                                                       const float *__restrict__ rho, Lattice L,
+                                                       uint32_t *__restrict__ status) {
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    const int y = blockIdx.y * kBY + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const int64_t k = (int64_t)y * L.pitch + x;
+    if (cls[k] != kInterior) return;
+    float f[9];
+    pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
+    float sx = L.fx, sy = L.fy;
+    if (L.grad) {
+        const float rk = rho[k];
+        source_interior(rho, k, L.pitch, rk, L, sx, sy);
+    }
+    float dr, jx, jy;
+    collide(f, sx, sy, L, dr, jx, jy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.plane + k, f[i], L.scale);
+    integrate_u(uc + k, jx, jy, L.rho0 + dr);
+    flag_nonfinite(status, dr, jx, jy);
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_boundary(const T *__restrict__ src, T *__restrict__ dst,
+                                                  float4 *__restrict__ uc,
+                                                  const BNode *__restrict__ bnodes,
+                                                  const BLink *__restrict__ blinks,
+                                                  const BCDev *__restrict__ bcs,
+                                                  const float *__restrict__ rho, Lattice L,
+                                                  const int64_t *__restrict__ time, int toff,
+                                                  uint32_t *__restrict__ status) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= L.nb) return;
+    const BNode b = bnodes[m];
+    const float tb = (float)(*time + toff - 1);  // boundary data at the time of f^col
+    float f[9];
+    pull_boundary(src, b, blinks + (int64_t)m * 8, bcs, tb, L, f);
+    const int64_t k = (int64_t)b.y * L.pitch + b.x;
+    float sx = L.fx, sy = L.fy;
+    if (L.grad) source_boundary(rho, b, k, rho[k], L, sx, sy);
+    float dr, jx, jy;
+    collide(f, sx, sy, L, dr, jx, jy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.plane + k, f[i], L.scale);
+    integrate_u(uc + k, jx, jy, L.rho0 + dr);
+    flag_nonfinite(status, dr, jx, jy);
+}
+
+// Density at time t of every material node (lambda != mu): pull, with the
+// boundary rules at boundary nodes.  Writes the deviation rho - rho0 into a
+// dense [ny][pitch] array.
+template <class T>
+__global__ void __launch_bounds__(kBX *kBY) k_density_interior(const T *__restrict__ src,
+                                                               const uint8_t *__restrict__ cls,
+                                                               float *__restrict__ rho, Lattice L) {
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    const int y = blockIdx.y * kBY + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const int64_t k = (int64_t)y * L.pitch + x;
+    if (cls[k] != kInterior) return;
+    float f[9];
+    pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
+    rho[k] = moments(f).dr;
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_density_boundary(const T *__restrict__ src,
+                                                          const BNode *__restrict__ bnodes,
+                                                          const BLink *__restrict__ blinks,
+                                                          const BCDev *__restrict__ bcs,
+                                                          float *__restrict__ rho, Lattice L,
+                                                          const int64_t *__restrict__ time,
+                                                          int toff) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= L.nb) return;
+    const BNode b = bnodes[m];
+    const float tb = (float)(*time + toff - 1);
+    float f[9];
+    pull_boundary(src, b, blinks + (int64_t)m * 8, bcs, tb, L, f);
+    rho[(int64_t)b.y * L.pitch + b.x] = moments(f).dr;
+}
+
+// Fields at the current time t (Eqs. moments, poissonstress, approxdiv).
+__device__ __forceinline__ void write_fields(float *__restrict__ out, int64_t N, int64_t o,
+                                             const float f[9], float sx, float sy, float4 w,
+                                             const Lattice &L) {
+    const Mom m = moments(f);
+    const float jx = m.mx + 0.5f * sx, jy = m.my + 0.5f * sy;
+    const float rho = L.rho0 + m.dr;
+    const float dv = -L.lam_m_mu_r0 * m.dr;
+    out[o] = (w.x - w.z) * L.out_u;
+    out[N + o] = (w.y - w.w) * L.out_u;
+    out[2 * N + o] = jx / rho * L.out_v;
+    out[3 * N + o] = jy / rho * L.out_v;
+    out[4 * N + o] = (-m.pxx + dv) * L.out_s;
+    out[5 * N + o] = (-m.pyy + dv) * L.out_s;
+    out[6 * N + o] = (-m.pxy) * L.out_s;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBX *kBY) k_fields_interior(const T *__restrict__ src,
+                                                              const float4 *__restrict__ uc,
+                                                              const uint8_t *__restrict__ cls,
+                                                              const float *__restrict__ rho,
+                                                              Lattice L, float *__restrict__ out) {
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    const int y = blockIdx.y * kBY + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const int64_t k = (int64_t)y * L.pitch + x;
+    const int64_t N = (int64_t)L.nx * L.ny, o = (int64_t)y * L.nx + x;
+    const uint8_t c = cls[k];
+    if (c == kBoundary) return;
+    if (c == kVoid) {
+#pragma unroll
+        for (int a = 0; a < 7; ++a) out[a * N + o] = 0.0f;
+        return;
+    }
+    float f[9];
+    pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
+    float sx = L.fx, sy = L.fy;
+    if (L.grad) source_interior(rho, k, L.pitch, rho[k], L, sx, sy);
+    write_fields(out, N, o, f, sx, sy, uc[k], L);
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_fields_boundary(const T *__restrict__ src,
+                                                         const float4 *__restrict__ uc,
+                                                         const BNode *__restrict__ bnodes,
+                                                         const BLink *__restrict__ blinks,
+                                                         const BCDev *__restrict__ bcs,
+                                                         const float *__restrict__ rho, Lattice L,
+                                                         const int64_t *__restrict__ time,
+                                                         float *__restrict__ out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= L.nb) return;
+    const BNode b = bnodes[m];
+    const float tb = (float)(*time - 1);
+    float f[9];
+    pull_boundary(src, b, blinks + (int64_t)m * 8, bcs, tb, L, f);
+    const int64_t k = (int64_t)b.y * L.pitch + b.x;
+    float sx = L.fx, sy = L.fy;
+    if (L.grad) source_boundary(rho, b, k, rho[k], L, sx, sy);
+    const int64_t N = (int64_t)L.nx * L.ny, o = (int64_t)b.y * L.nx + b.x;
+    write_fields(out, N, o, f, sx, sy, uc[k], L);
+}
+
+__global__ void k_advance(int64_t *time, int64_t n) { *time += n; }
+
+__global__ void k_gather_probe(const float *__restrict__ stage, const int32_t *__restrict__ idx,
+                               int count, int64_t N, float *__restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= count) return;
+    const int64_t o = idx[p];
+#pragma unroll
+    for (int a = 0; a < 7; ++a) out[(int64_t)p * 7 + a] = stage[a * N + o];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+template <class T>
+static cudaError_t step_t(const Lattice &L, const DevState &S, int cur, int toff,
+                          cudaStream_t s_main, cudaStream_t s_side, cudaEvent_t fork,
+                          cudaEvent_t join, const StepEvents *ev) {
+    const T *src = static_cast<const T *>(S.f[cur]);
+    T *dst = static_cast<T *>(S.f[cur ^ 1]);
+    const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
+    const int nbb = (L.nb + 127) / 128;
+    if (L.grad) {
+        k_density_interior<T><<<grd, blk, 0, s_main>>>(src, S.cls, S.rho, L);
+        if (L.nb > 0)
+            k_density_boundary<T><<<nbb, 128, 0, s_main>>>(src, S.bnodes, S.blinks, S.bcs, S.rho,
+                                                           L, S.time, toff);
+    }
+    const bool split = s_side && fork && join && L.nb > 0;
+    cudaStream_t s_b = split ? s_side : s_main;
+    if (split) {
+        cudaEventRecord(fork, s_main);
+        cudaStreamWaitEvent(s_side, fork, 0);
+        if (ev) cudaEventRecord(ev->before_boundary, s_side);
+        k_boundary<T><<<nbb, 128, 0, s_side>>>(src, dst, S.ucomp, S.bnodes, S.blinks, S.bcs,
+                                               S.rho, L, S.time, toff, S.status);
+        if (ev) cudaEventRecord(ev->after_boundary, s_side);
+        cudaEventRecord(join, s_side);
+    }
+    if (ev) cudaEventRecord(ev->before_interior, s_main);
+    k_interior<T><<<grd, blk, 0, s_main>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status);
+    if (ev) cudaEventRecord(ev->after_interior, s_main);
+    if (split) {
+        cudaStreamWaitEvent(s_main, join, 0);
+    } else {
+        if (ev) cudaEventRecord(ev->before_boundary, s_b);
+        if (L.nb > 0)
+            k_boundary<T><<<nbb, 128, 0, s_b>>>(src, dst, S.ucomp, S.bnodes, S.blinks, S.bcs,
+                                                S.rho, L, S.time, toff, S.status);
+        if (ev) cudaEventRecord(ev->after_boundary, s_b);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(int storage, const Lattice &L, const DevState &S, int cur, int toff,
+                        cudaStream_t s_main, cudaStream_t s_side, cudaEvent_t fork,
+                        cudaEvent_t join, const StepEvents *ev) {
+    switch (storage) {
+        case LBM_F16_DEV:
+            return step_t<__half>(L, S, cur, toff, s_main, s_side, fork, join, ev);
+        case LBM_BF16_DEV:
+            return step_t<__nv_bfloat16>(L, S, cur, toff, s_main, s_side, fork, join, ev);
+        default:
+            return step_t<float>(L, S, cur, toff, s_main, s_side, fork, join, ev);
+    }
+}
+
+int kernels_per_step(const Lattice &L) { return (L.grad ? (L.nb > 0 ? 2 : 1) : 0) + 1 + (L.nb > 0 ? 1 : 0); }
+int kernels_per_fields(const Lattice &L) { return kernels_per_step(L); }
+
+cudaError_t launch_advance(const DevState &S, int64_t n, cudaStream_t s) {
+    k_advance<<<1, 1, 0, s>>>(S.time, n);
+    return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t fields_t(const Lattice &L, const DevState &S, int cur, cudaStream_t s) {
+    const T *src = static_cast<const T *>(S.f[cur]);
+    const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
+    const int nbb = (L.nb + 127) / 128;
+    if (L.grad) {
+        k_density_interior<T><<<grd, blk, 0, s>>>(src, S.cls, S.rho, L);
+        if (L.nb > 0)
+            k_density_boundary<T><<<nbb, 128, 0, s>>>(src, S.bnodes, S.blinks, S.bcs, S.rho, L,
+                                                      S.time, 0);
+    }
+    k_fields_interior<T><<<grd, blk, 0, s>>>(src, S.ucomp, S.cls, S.rho, L, S.stage);
+    if (L.nb > 0)
+        k_fields_boundary<T><<<nbb, 128, 0, s>>>(src, S.ucomp, S.bnodes, S.blinks, S.bcs, S.rho,
+                                                 L, S.time, S.stage);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields(int storage, const Lattice &L, const DevState &S, int cur, float *u,
+                          float *v, float *sigma, cudaStream_t s) {
+    cudaError_t e;
+    switch (storage) {
+        case LBM_F16_DEV:
+            e = fields_t<__half>(L, S, cur, s);
+            break;
+        case LBM_BF16_DEV:
+            e = fields_t<__nv_bfloat16>(L, S, cur, s);
+            break;
+        default:
+            e = fields_t<float>(L, S, cur, s);
+    }
+    if (e != cudaSuccess) return e;
+    const int64_t N = (int64_t)L.nx * L.ny;
+    if (u) e = cudaMemcpyAsync(u, S.stage, 2 * N * sizeof(float), cudaMemcpyDefault, s);
+    if (e == cudaSuccess && v)
+        e = cudaMemcpyAsync(v, S.stage + 2 * N, 2 * N * sizeof(float), cudaMemcpyDefault, s);
+    if (e == cudaSuccess && sigma)
+        e = cudaMemcpyAsync(sigma, S.stage + 4 * N, 3 * N * sizeof(float), cudaMemcpyDefault, s);
+    return e;
+}
+
+cudaError_t launch_gather_probe(const Lattice &L, const DevState &S, int count, cudaStream_t s) {
+    const int64_t N = (int64_t)L.nx * L.ny;
+    k_gather_probe<<<(count + 127) / 128, 128, 0, s>>>(S.stage, S.probe_idx, count, N, S.probe);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset(int storage, const Lattice &L, const DevState &S, cudaStream_t s) {
+    const size_t esz = storage == LBM_F32 ? 4 : 2;
+    const size_t fbytes = (size_t)9 * L.plane * esz;
+    cudaError_t e = cudaMemsetAsync(S.f[0], 0, fbytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.f[1], 0, fbytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.ucomp, 0, (size_t)L.plane * sizeof(float4), s);
+    if (e == cudaSuccess && S.rho) e = cudaMemsetAsync(S.rho, 0, (size_t)L.plane * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.status, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.time, 0, sizeof(int64_t), s);
+    return e;
+}
+
+}  // namespace lbm

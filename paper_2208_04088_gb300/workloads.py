@@ -43,6 +43,9 @@ class Workload:
     crack: Optional[Tuple[int, int]] = None  # (length, bc)
     bcs: List[dict] = dataclasses.field(default_factory=list)
     tau: float = TAU
+    # Neumann wall values at the boundary node instead of the extrapolation of
+    # Sec. 4 (an option of the library and the oracle, off = the paper's rule)
+    wall_node: bool = False
 
     @property
     def lam(self) -> float:

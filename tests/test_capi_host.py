@@ -1,0 +1,104 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+* liblbm.so loads and exports every function include/lbm.h declares.
+* The library's geometry builder (its own code) produces node masks and
+  cut-link tables bit-identical to the oracle's independent classifier.
+* Descriptor validation rejects inconsistent tables with LBM_ERR_ARG.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2208_04088_gb300 import _native as N
+from paper_2208_04088_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = N.load()
+    declared = _declared_functions()
+    assert len(declared) >= 12
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert name in N.SIGNATURES, name
+
+
+@pytest.mark.parametrize("wl", [W.square_plate(64, 0), W.hole_plate(256, 128, 16.0, 0),
+                                W.hole_plate(1024, 512, 64.0, 0), W.hole_plate(101, 77, 12.5, 0),
+                                W.edge_crack(128, 40, 0), W.edge_crack(64, 64, 0, ny=32)],
+                         ids=lambda w: w.name)
+def test_geometry_tables_bit_exact_with_oracle(oracle_mod, wl):
+    nt_o, lk_o = oracle_mod.geometry(**wl.geometry_args())
+    nt_l, lk_l = N.lbm_geom_build(**wl.geometry_args())
+    assert np.array_equal(nt_o, nt_l)
+    assert len(lk_o) == len(lk_l)
+    for f in ("node", "dir", "bc", "bc2"):
+        assert np.array_equal(lk_o[f], lk_l[f]), f
+    for f in ("q", "n0", "n1"):
+        assert np.array_equal(lk_o[f].view(np.uint64), lk_l[f].view(np.uint64)), f
+
+
+def _desc(wl, **kw):
+    return N.desc_from_workload(wl, **kw)
+
+
+def test_workspace_size_accounts_for_storage():
+    wl = W.hole_plate(256, 128, 16.0, 0)
+    b32 = N.lbm_workspace_size(_desc(wl, storage="f32"))
+    b16 = N.lbm_workspace_size(_desc(wl, storage="f16"))
+    plane = 256 * 128
+    assert b32 - b16 >= 2 * 9 * plane * 2   # two buffers, 2 bytes less per value
+    assert b32 > 2 * 9 * plane * 4 + 16 * plane
+
+
+def test_validation_rejects_bad_tables():
+    wl = W.square_plate(16, 0)
+    nt, links = N.lbm_geom_build(**wl.geometry_args())
+    # a missing cut link leaves a node linked to the outside
+    d = N.Desc(nt, links[1:], wl.bcs, wl.lam, wl.mu)
+    with pytest.raises(N.LbmError) as e:
+        N.lbm_workspace_size(d)
+    assert e.value.status == N.LBM_ERR_ARG
+    # duplicate link
+    d = N.Desc(nt, np.concatenate([links, links[:1]]), wl.bcs, wl.lam, wl.mu)
+    with pytest.raises(N.LbmError):
+        N.lbm_workspace_size(d)
+    # bad wall distance
+    bad = links.copy()
+    bad["q"][0] = 0.0
+    with pytest.raises(N.LbmError):
+        N.lbm_workspace_size(N.Desc(nt, bad, wl.bcs, wl.lam, wl.mu))
+    # isotropy condition dx/(sqrt(3) dt) = sqrt(mu/rho0) violated
+    with pytest.raises(N.LbmError):
+        N.lbm_workspace_size(N.Desc(nt, links, wl.bcs, wl.lam, wl.mu, dx=1.0, dt=0.5))
+    # tau must exceed 1/2
+    with pytest.raises(N.LbmError):
+        N.lbm_workspace_size(N.Desc(nt, links, wl.bcs, wl.lam, wl.mu, tau=0.5))
+    # out-of-range bc index
+    bad = links.copy()
+    bad["bc"][0] = 99
+    with pytest.raises(N.LbmError):
+        N.lbm_workspace_size(N.Desc(nt, bad, wl.bcs, wl.lam, wl.mu))
+    assert "bad cut link" in N.lbm_last_error()
+
+
+def test_physical_units_are_accepted():
+    # the plate of Sec. 5.1 in its own units: l = 1, dx = 0.0125 l, mu = 1, rho = 1,
+    # c_s = 1, dt = dx/(sqrt(3) c_s)
+    wl = W.square_plate(80, 0)
+    nt, links = N.lbm_geom_build(**wl.geometry_args())
+    dx = 0.0125
+    d = N.Desc(nt, links, wl.bcs, lam=1.0, mu=1.0, rho0=1.0, dx=dx, dt=dx / np.sqrt(3.0))
+    assert N.lbm_workspace_size(d) > 0
+    # the paper's printed, rounded time step 7.217e-3 l/c_s is within the tolerance
+    d = N.Desc(nt, links, wl.bcs, lam=1.0, mu=1.0, rho0=1.0, dx=dx, dt=7.217e-3)
+    assert N.lbm_workspace_size(d) > 0

@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle,
+element by element on every material node.
+
+Tolerance: relative L2 error <= 1e-5 per field (u, v, sigma) at FP32 storage of
+the deviations from the rest state.  The 16-bit storage forms carry a stated,
+looser bound: their rounding is 2^-11 (FP16) or 2^-8 (BF16) of each stored
+deviation every step.
+
+Run lengths: the boundary rules of Sec. 4 grow a density mode at traction
+walls after roughly a thousand steps (the oracle diverges as well, see
+tests/test_oracle_stability.py); parity is checked on runs that stay bounded
+in the oracle, and on the wall-node option for long runs.
+"""
+import numpy as np
+import pytest
+
+from paper_2208_04088_gb300 import workloads as W
+
+from helpers import compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _assert_parity(gpu, ora, tol=TOL):
+    err = compare(gpu, ora)
+    assert all(e <= tol for e in err.values()), err
+    # void nodes are exactly zero
+    for k in ("u", "v", "sigma"):
+        assert np.all(gpu[k][..., ~ora["mask"]] == 0.0)
+    return err
+
+
+@pytest.mark.parametrize("wall_node", [False, True])
+def test_config1_square_plate(oracle_mod, wall_node):
+    wl = W.square_plate(64, 500)
+    wl.wall_node = wall_node
+    _assert_parity(run_gpu(wl, wl.steps), run_oracle(oracle_mod, wl, wl.steps))
+
+
+@pytest.mark.parametrize("wall_node,steps", [(False, 500), (True, 700)])
+def test_config2_downscale_hole_plate(oracle_mod, wall_node, steps):
+    wl = W.hole_plate(256, 128, 16.0, steps)
+    wl.wall_node = wall_node
+    _assert_parity(run_gpu(wl, steps), run_oracle(oracle_mod, wl, steps))
+
+
+def test_crack_small(oracle_mod):
+    wl = W.edge_crack(256, 64, 500)
+    _assert_parity(run_gpu(wl, wl.steps), run_oracle(oracle_mod, wl, wl.steps))
+
+
+@pytest.mark.parametrize("lam_over_mu", [W.PLATE_NONPOISSON_LAM_OVER_MU,
+                                         W.CRACK_PAPER_LAM_OVER_MU])
+def test_non_poisson_source_term(oracle_mod, lam_over_mu):
+    wl = W.hole_plate(160, 96, 12.0, 500, lam_over_mu=lam_over_mu)
+    _assert_parity(run_gpu(wl, wl.steps), run_oracle(oracle_mod, wl, wl.steps))
+
+
+def test_non_poisson_crack(oracle_mod):
+    wl = W.edge_crack(192, 50, 300, lam_over_mu=W.CRACK_PAPER_LAM_OVER_MU)
+    _assert_parity(run_gpu(wl, wl.steps), run_oracle(oracle_mod, wl, wl.steps))
+
+
+def test_every_rule_kind_ragged_lattice(oracle_mod):
+    """Ragged size (not a multiple of the tile), a rigid circular inclusion
+    (curved Dirichlet), a moving clamped edge, stress, pressure and traction
+    edges, corner links of every pairing and ramp profiles."""
+    wl = W.hole_plate(77, 45, 9.5, 400)
+    wl.bcs = [W.bc(W.DIRICHLET, (2e-4, -1e-4)),                    # left: moving wall
+              W.bc(W.DIRICHLET, (0.0, 0.0)),                       # hole: rigid inclusion
+              W.bc(W.STRESS, (1e-3, -5e-4, 3e-4)),                 # right
+              W.bc(W.PRESSURE, (-4e-4,), W.RAMP, 60.0),            # bottom
+              W.bc(W.TRACTION, (2e-4, 6e-4), W.RAMP, 25.0)]        # top
+    wl.edge_bc = (0, 2, 3, 4)
+    wl.hole = (wl.hole[0], wl.hole[1], wl.hole[2], 1)
+    _assert_parity(run_gpu(wl, wl.steps), run_oracle(oracle_mod, wl, wl.steps))
+
+
+def test_curved_neumann_hole_with_shear_stress(oracle_mod):
+    wl = W.hole_plate(96, 80, 13.0, 500)
+    wl.bcs = [W.bc(W.STRESS, (6e-4, -2e-4, 4e-4)), W.bc(W.PRESSURE, (3e-4,))]
+    _assert_parity(run_gpu(wl, wl.steps), run_oracle(oracle_mod, wl, wl.steps))
+
+
+def test_tiny_lattices(oracle_mod):
+    # no interior node at all, a single interior node, a ragged 5 x 5
+    for n, steps in ((2, 40), (3, 40), (5, 60)):
+        wl = W.square_plate(n, steps)
+        _assert_parity(run_gpu(wl, steps), run_oracle(oracle_mod, wl, steps))
+
+
+def test_long_run_with_wall_node_values(oracle_mod):
+    wl = W.square_plate(64, 3000)
+    wl.wall_node = True
+    _assert_parity(run_gpu(wl, wl.steps), run_oracle(oracle_mod, wl, wl.steps))
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 3e-3), ("bf16", 3e-2)])
+def test_16bit_deviation_storage_error_bound(oracle_mod, storage, tol):
+    wl = W.edge_crack(256, 64, 500)
+    err = compare(run_gpu(wl, wl.steps, storage=storage), run_oracle(oracle_mod, wl, wl.steps))
+    assert all(e <= tol for e in err.values()), err
+
+
+def test_rest_state_is_exactly_zero():
+    wl = W.hole_plate(128, 64, 10.0, 300)
+    wl.bcs = [W.bc(W.TRACTION, (0.0, 0.0)), W.bc(W.TRACTION, (0.0, 0.0))]
+    F = run_gpu(wl, wl.steps)
+    for k in ("u", "v", "sigma"):
+        assert np.all(F[k] == 0.0)
+
+
+def test_graph_replay_equals_direct_launches_and_is_deterministic():
+    wl = W.hole_plate(200, 120, 14.0, 0)
+    a = run_gpu(wl, 0, chunks=[96])            # three replayed 32-step graphs
+    b = run_gpu(wl, 0, chunks=[1] * 96)        # 96 direct launches
+    c = run_gpu(wl, 0, chunks=[7, 64, 25])     # mixed, odd parity before a graph
+    for k in ("u", "v", "sigma"):
+        assert np.array_equal(a[k], b[k]) and np.array_equal(a[k], c[k])
+
+
+def test_timing_mode_gives_identical_results():
+    from paper_2208_04088_gb300 import _native as N
+    wl = W.edge_crack(256, 64, 0)
+    outs = []
+    for timing in (False, True):
+        s = N.Solver(N.desc_from_workload(wl))
+        s.set_timing(timing)
+        s.step(100)
+        outs.append(s.fields_host())
+        if timing:
+            t = s.timing()
+            assert t["steps"] == 100 and t["interior_ms"] > 0 and t["boundary_ms"] > 0
+        s.close()
+    for k in ("u", "v", "sigma"):
+        assert np.array_equal(outs[0][k], outs[1][k])
+
+
+def test_reset_restarts_bitwise():
+    from paper_2208_04088_gb300 import _native as N
+    wl = W.hole_plate(128, 96, 10.0, 0)
+    s = N.Solver(N.desc_from_workload(wl))
+    s.step(150)
+    first = s.fields_host()
+    s.reset()
+    assert s.info()["time"] == 0
+    s.step(150)
+    second = s.fields_host()
+    s.close()
+    for k in ("u", "v", "sigma"):
+        assert np.array_equal(first[k], second[k])
+
+
+def test_probe_matches_fields():
+    from paper_2208_04088_gb300 import _native as N
+    wl = W.edge_crack(128, 32, 0)
+    s = N.Solver(N.desc_from_workload(wl))
+    s.step(80)
+    F = s.fields_host()
+    nodes = np.array([0, 5, 64 * 128 + 33, 128 * 128 - 1, 63 * 128 + 10], dtype=np.int32)
+    P = s.probe(nodes)
+    s.close()
+    for p, n in enumerate(nodes):
+        y, x = divmod(int(n), 128)
+        expect = [F["u"][0, y, x], F["u"][1, y, x], F["v"][0, y, x], F["v"][1, y, x],
+                  F["sigma"][0, y, x], F["sigma"][1, y, x], F["sigma"][2, y, x]]
+        assert np.array_equal(P[p], np.array(expect, dtype=np.float32))
+
+
+def test_unstable_run_is_reported_not_hidden():
+    """tau = 1 with the extrapolated wall values overflows FP32 within a few
+    thousand steps; the status word turns that into LBM_ERR_UNSTABLE."""
+    import torch
+
+    from paper_2208_04088_gb300 import _native as N
+    wl = W.square_plate(64, 0)
+    wl.tau = 1.0
+    s = N.Solver(N.desc_from_workload(wl))
+    s.step(6000)
+    with pytest.raises(N.LbmError) as e:
+        s.sync()
+    assert e.value.status == N.LBM_ERR_UNSTABLE
+    torch.cuda.synchronize()
+    with pytest.raises(N.LbmError) as e:   # the next asynchronous call reports it too
+        s.step(1)
+        s.step(1)
+    assert e.value.status == N.LBM_ERR_UNSTABLE
+    s.close()
