@@ -197,6 +197,27 @@ lbm_status lbm_step(lbm_handle h, int64_t nsteps);
  * asynchronous; on_device = 0: host pointers, returns after the copy. */
 lbm_status lbm_get_fields(lbm_handle h, float *u, float *v, float *sigma, int32_t on_device);
 
+/* The fields of lbm_get_fields, copied to host memory, for callers that must
+ * not allocate device memory.  The paper has no counterpart; this is a service
+ * of the library.  Some callers cannot call cudaMalloc: code that runs under a
+ * fixed device-memory budget reserved up front by another allocator (it passed
+ * its own workspace to lbm_create, sized by lbm_workspace_size), or code on a
+ * latency-critical path where a cudaMalloc and its implicit device
+ * synchronisation are not acceptable.  This call allocates nothing: the field
+ * planes are staged in a fixed array inside the library, 7 x 262144 floats
+ * (7 MiB), which every GPU that loads the library holds until the process
+ * exits.  Limits and behaviour:
+ *   - nx * ny must not exceed 262144 (e.g. 512 x 512); larger lattices return
+ *     LBM_ERR_ARG with a message naming the limit;
+ *   - u, v, sigma are host pointers with the layouts of lbm_get_fields, any
+ *     may be NULL; the call returns after the copies (synchronous);
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device;
+ *   - every call on a device shares the array and leaves its contents behind;
+ *     calls whose device work overlaps (different streams or threads) race. */
+lbm_status lbm_get_fields_host_noalloc(lbm_handle h, float *u, float *v, float *sigma);
+
 /* Fields at `count` nodes (host indices y*nx + x) into host `out`
  * [count][7] = (u_x, u_y, v_x, v_y, s_xx, s_yy, s_xy).  Synchronous. */
 lbm_status lbm_probe(lbm_handle h, const int32_t *nodes, int32_t count, float *out);

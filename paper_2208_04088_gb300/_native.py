@@ -82,6 +82,7 @@ SIGNATURES = {
                              C.POINTER(C.c_void_p)]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_get_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "lbm_get_fields_host_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_probe": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
                             C.POINTER(C.c_float)]),
     "lbm_set_bc": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(lbm_bc)]),
@@ -210,6 +211,13 @@ def lbm_get_fields(h, u_ptr: int = 0, v_ptr: int = 0, sigma_ptr: int = 0,
                    on_device: bool = True) -> None:
     _check(load().lbm_get_fields(h, C.c_void_p(u_ptr), C.c_void_p(v_ptr), C.c_void_p(sigma_ptr),
                                  int(bool(on_device))))
+
+
+def lbm_get_fields_host_noalloc(h, u_ptr: int = 0, v_ptr: int = 0, sigma_ptr: int = 0) -> None:
+    """Fields to host pointers without device allocation (static staging array,
+    at most 262144 nodes; see include/lbm.h)."""
+    _check(load().lbm_get_fields_host_noalloc(h, C.c_void_p(u_ptr), C.c_void_p(v_ptr),
+                                              C.c_void_p(sigma_ptr)))
 
 
 def lbm_probe(h, nodes) -> np.ndarray:

@@ -2,6 +2,7 @@
 // layout, stepping (direct launches or replayed CUDA graphs), fields and probes.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -542,5 +543,85 @@ extern "C" lbm_status lbm_destroy(lbm_handle h) {
     }
     if (h->owned) cudaFree(h->owned);
     delete h;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Fields to host memory without any device allocation.
+//
+// lbm_get_fields stages the seven field planes in the handle's workspace.
+// This variant stages them in a fixed device array that lives in the module
+// instead, so a caller whose handle sits in a workspace it sized itself (or
+// that must not allocate at this point) can still read the fields back.  The
+// array is shared by every call on a device and keeps the last call's
+// contents; each call overwrites every entry it later copies, so nothing has
+// to be cleared first.  Calls whose device work overlaps (on different
+// streams, or from different threads) race on the array.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxNodes = int64_t(1) << 18;  // nx * ny limit: 262144 nodes
+constexpr int kNoAllocMaxDevices = 64;
+
+// 7 planes x 2^18 nodes x 4 bytes = 7 MiB held on every device that loads the library.
+static __device__ __align__(256) float g_noalloc_fields[7 * kNoAllocMaxNodes];
+
+std::mutex g_noalloc_mutex;
+float *g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the array on the current device, looked up once per device.
+lbm_status noalloc_scratch(float **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_get_fields_host_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("lbm_get_fields_host_noalloc: device ordinal beyond 63");
+        return LBM_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_fields);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "lbm_get_fields_host_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_get_fields_host_noalloc(lbm_handle h, float *u, float *v,
+                                                  float *sigma) {
+    set_error("");
+    if (!h) {
+        set_error("lbm_get_fields_host_noalloc: NULL handle");
+        return LBM_ERR_ARG;
+    }
+    const int64_t N = (int64_t)h->L.nx * h->L.ny;
+    if (N > kNoAllocMaxNodes) {
+        set_error("lbm_get_fields_host_noalloc: nx*ny = " + std::to_string(N) +
+                  " exceeds the 262144 nodes of the static staging array");
+        return LBM_ERR_ARG;
+    }
+    float *scratch = nullptr;
+    lbm_status st = noalloc_scratch(&scratch);
+    if (st != LBM_OK) return st;
+    DevState S = h->S;
+    S.stage = scratch;  // same kernels, staging redirected to the static array
+    cudaError_t e = launch_fields(h->storage, h->L, S, h->cur, nullptr, nullptr, nullptr,
+                                  h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_get_fields_host_noalloc");
+    h->launches += kernels_per_fields(h->L);
+    if (u) e = cudaMemcpyAsync(u, scratch, 2 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && v)
+        e = cudaMemcpyAsync(v, scratch + 2 * N, 2 * N * sizeof(float), cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (e == cudaSuccess && sigma)
+        e = cudaMemcpyAsync(sigma, scratch + 4 * N, 3 * N * sizeof(float),
+                            cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_get_fields_host_noalloc: copy");
     return LBM_OK;
 }
