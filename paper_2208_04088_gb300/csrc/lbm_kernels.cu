@@ -12,6 +12,7 @@
 // All arithmetic is FP32.  The rest state is a fixed point of every rule, so
 // each rule acts on the deviations with the same coefficients it has for f.
 #include <cstdint>
+#include <cstring>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -147,7 +148,20 @@ __device__ __forceinline__ void collide(float f[9], float sx, float sy, const La
     populations(m, f);
 }
 
-// u(t+1) = u(t) + j/rho with Kahan compensation per component.
+// u(t+1) = u(t) + j/rho with Kahan compensation per component; w holds
+// (u_x, u_y, compensation_x, compensation_y).
+__device__ __forceinline__ void integrate_u_value(float4 &w, float jx, float jy, float rho) {
+    const float vx = jx / rho, vy = jy / rho;
+    float y = vx - w.z;
+    float t = w.x + y;
+    w.z = (t - w.x) - y;
+    w.x = t;
+    y = vy - w.w;
+    t = w.y + y;
+    w.w = (t - w.y) - y;
+    w.y = t;
+}
+
 __device__ __forceinline__ void integrate_u(float4 *uc, float jx, float jy, float rho) {
     float4 w = *uc;
     const float vx = jx / rho, vy = jy / rho;
@@ -210,14 +224,29 @@ __device__ __forceinline__ void pull_interior(const T *__restrict__ src, int64_t
 // boundary data at t-1.  rho and P are collision invariants, so their values
 // at t-1 are the moments of the stored post-collision populations.
 template <class T>
-__device__ void pull_boundary(const T *__restrict__ src, const BNode &b,
-                              const BLink *__restrict__ links, const BCDev *__restrict__ bcs,
-                              float tb, const Lattice &L, float f[9]) {
+__device__ __forceinline__ void pull_boundary(const T *__restrict__ src, const BNode &b,
+                                              const BLink *__restrict__ links,
+                                              const BCDev *__restrict__ bcs, float tb,
+                                              const Lattice &L, float f[9]) {
     const int64_t k = (int64_t)b.y * L.pitch + b.x;
     const int64_t P = L.plane;
-    float gx[9];
+    // Phase 1: every load that depends only on the node record, issued before
+    // any arithmetic so their latencies overlap.  Cut directions read the
+    // node itself (a valid address whose value is not used).
+    float gx[9], pl[9], gy1[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) gx[i] = Store<T>::ld(src + i * P + k, L.inv_scale);
+#pragma unroll
+    for (int kk = 1; kk < 9; ++kk) {
+        const int i = opp(kk);
+        const bool cut = (b.cut >> i) & 1u;
+        const int64_t sk = cut ? k : k - (int64_t)c_cy(kk) * L.pitch - c_cx(kk);
+        pl[kk] = Store<T>::ld(src + kk * P + sk, L.inv_scale);
+        // f_i^col at the upstream node x - c_i of the cut link i (kappa term)
+        const bool up = cut && !((b.miss >> i) & 1u);
+        const int64_t ku = up ? k - (int64_t)c_cy(i) * L.pitch - c_cx(i) : k;
+        gy1[i] = Store<T>::ld(src + i * P + ku, L.inv_scale);
+    }
     const Mom mx = moments(gx);
     // Cauchy stress at x (Eq. poissonstress with Eq. approxdiv), deviation form
     const float dvx = -L.lam_m_mu_r0 * mx.dr;
@@ -230,8 +259,7 @@ __device__ void pull_boundary(const T *__restrict__ src, const BNode &b,
         const int i = opp(kk);
         const uint32_t bit = 1u << i;
         if (!(b.cut & bit)) {
-            const int64_t src_k = k - (int64_t)c_cy(kk) * L.pitch - c_cx(kk);
-            f[kk] = Store<T>::ld(src + kk * P + src_k, L.inv_scale);
+            f[kk] = pl[kk];
             continue;
         }
         const BLink lk = links[i - 1];
@@ -241,11 +269,8 @@ __device__ void pull_boundary(const T *__restrict__ src, const BNode &b,
         const float fac = 2.0f / (1.0f + 2.0f * q);  // 1 + kappa = 2 l/(l + 2 s)
         const float w = (i <= 4) ? (1.0f / 9.0f) : (1.0f / 36.0f);
         const float cix = (float)c_cx(i), ciy = (float)c_cy(i);
-        // upstream node x - c_i
-        float gy_i = 0.0f, gy[9];
-        const int64_t ku = k - (int64_t)c_cy(i) * L.pitch - c_cx(i);
+        const float gy_i = miss ? 0.0f : gy1[i];
         if (b.dirich & bit) {
-            if (!miss) gy_i = Store<T>::ld(src + i * P + ku, L.inv_scale);
             const BCDev ba = bcs[lk.bc], bb = bcs[lk.bc2];
             const float aa = amplitude(ba, tb), ab = amplitude(bb, tb);
             // j* = rho0 d(u*)/dt (Eq. bcchaindir); corners: mean of the Dirichlet edges
@@ -259,12 +284,11 @@ __device__ void pull_boundary(const T *__restrict__ src, const BNode &b,
         // Neumann: density and stress at the wall by extrapolation along the link
         // (or the node's own values with the wall-node option)
         float drb = mx.dr, sbxx = sxx_x, sbyy = syy_x, sbxy = sxy_x;
-        if (!miss && L.wall_node) {
-            gy_i = Store<T>::ld(src + i * P + ku, L.inv_scale);
-        } else if (!miss) {
+        if (!miss && !L.wall_node) {
+            const int64_t ku = k - (int64_t)c_cy(i) * L.pitch - c_cx(i);
+            float gy[9];
 #pragma unroll
             for (int m = 0; m < 9; ++m) gy[m] = Store<T>::ld(src + m * P + ku, L.inv_scale);
-            gy_i = gy[i];
             const Mom my = moments(gy);
             const float dvy = -L.lam_m_mu_r0 * my.dr;
             const float a1 = 1.0f + q;
@@ -301,6 +325,140 @@ __device__ void pull_boundary(const T *__restrict__ src, const BNode &b,
         // Eq. (abbnoncon); kappa = 0 and 1 + kappa = 1 give Eq. (abbcon)
         f[kk] = -gx[i] - kap * (gy_i + gx[kk]) + fac * eq;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Cooperative boundary update: eight lanes per boundary node.  Lane j owns the
+// population k = j + 1 and the link i = opp(k) through which it arrives; lane
+// 0 also carries the rest population.  Moments are formed with butterfly
+// shuffles inside the 8-lane group (every lane ends with bit-identical sums,
+// since each pairwise addition is commutative), so a node's loads are issued
+// by eight lanes at once and its serial chain is an eighth of the single-thread
+// form above.
+__device__ __forceinline__ float grp8_sum(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+__device__ __forceinline__ int lane_cx(int k) {
+    return (k == 1 || k == 5 || k == 8) ? 1 : (k == 3 || k == 6 || k == 7) ? -1 : 0;
+}
+__device__ __forceinline__ int lane_cy(int k) {
+    return (k == 2 || k == 5 || k == 6) ? 1 : (k == 4 || k == 7 || k == 8) ? -1 : 0;
+}
+
+// Raw moments of a node's populations held one per lane (+ f0 on lane 0).
+__device__ __forceinline__ Raw grp8_raw(float fk, float f0, int cx, int cy, bool lane0) {
+    const float cxx = (float)(cx * cx), cyy = (float)(cy * cy);
+    Raw m;
+    m.m00 = grp8_sum(fk + (lane0 ? f0 : 0.0f));
+    m.m10 = grp8_sum(cx * fk);
+    m.m01 = grp8_sum(cy * fk);
+    m.m20 = grp8_sum(cxx * fk);
+    m.m02 = grp8_sum(cyy * fk);
+    m.m11 = grp8_sum((float)(cx * cy) * fk);
+    m.m21 = grp8_sum(cxx * cy * fk);
+    m.m12 = grp8_sum(cx * cyy * fk);
+    m.m22 = grp8_sum(cxx * cyy * fk);
+    return m;
+}
+
+// f_k(x, t) for lane k of a boundary node (and f_0 on lane 0): pulled where
+// link opp(k) is intact, otherwise Eqs. (bbnoncon)/(abbnoncon).  Same rules
+// and data as pull_boundary.
+template <class T>
+__device__ __forceinline__ float pull_boundary8(const T *__restrict__ src, const BNode &b, int k,
+                                                const BLink *__restrict__ links,
+                                                const BCDev *__restrict__ bcs, float tb,
+                                                const Lattice &L, bool lane0, float &f0) {
+    const int64_t kn = (int64_t)b.y * L.pitch + b.x;
+    const int64_t P = L.plane;
+    const int i = k <= 4 ? (k + 1) % 4 + 1 : (k - 3) % 4 + 5;  // opp(k)
+    const int cxk = lane_cx(k), cyk = lane_cy(k);
+    const int cxi = -cxk, cyi = -cyk;
+    const uint32_t bit = 1u << i;
+    const bool cut = (b.cut & bit) != 0;
+    const bool miss = (b.miss & bit) != 0;
+    // loads, all independent
+    const float gk = Store<T>::ld(src + k * P + kn, L.inv_scale);      // f_k^col(x)
+    const float gi = Store<T>::ld(src + i * P + kn, L.inv_scale);      // f_i^col(x)
+    f0 = lane0 ? Store<T>::ld(src + kn, L.inv_scale) : 0.0f;           // f_0^col(x)
+    const int64_t kpull = cut ? kn : kn - (int64_t)cyk * L.pitch - cxk;
+    const float pulled = Store<T>::ld(src + k * P + kpull, L.inv_scale);
+    const int64_t ku = (cut && !miss) ? kn - (int64_t)cyi * L.pitch - cxi : kn;
+    const float gy_i = (cut && !miss) ? Store<T>::ld(src + i * P + ku, L.inv_scale) : 0.0f;
+    const bool neu_ex = cut && !miss && !L.wall_node && !(b.dirich & bit);
+    float my_dr = 0.0f, my_xx = 0.0f, my_yy = 0.0f, my_xy = 0.0f;
+    if (neu_ex) {
+        float gy[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) gy[m] = Store<T>::ld(src + m * P + ku, L.inv_scale);
+        const Mom my = moments(gy);
+        my_dr = my.dr;
+        my_xx = my.pxx;
+        my_yy = my.pyy;
+        my_xy = my.pxy;
+    }
+    BLink lk;
+    if (cut) lk = links[i - 1];
+    // moments of f^col(x, t-1) (rho and P are collision invariants)
+    const float cxf = (float)cxk, cyf = (float)cyk;
+    const float dr_x = grp8_sum(gk + f0);
+    const float pxx_x = grp8_sum(cxf * cxf * gk);
+    const float pyy_x = grp8_sum(cyf * cyf * gk);
+    const float pxy_x = grp8_sum(cxf * cyf * gk);
+    if (!cut) return pulled;
+    const float q = miss ? 0.5f : lk.q;
+    const float kap = (1.0f - 2.0f * q) / (1.0f + 2.0f * q);
+    const float fac = 2.0f / (1.0f + 2.0f * q);
+    const float w = (i <= 4) ? (1.0f / 9.0f) : (1.0f / 36.0f);
+    const float cix = (float)cxi, ciy = (float)cyi;
+    if (b.dirich & bit) {
+        const BCDev ba = bcs[lk.bc], bb = bcs[lk.bc2];
+        const float aa = amplitude(ba, tb), ab = amplitude(bb, tb);
+        const float jsx = L.rho0 * 0.5f * (ba.v0 * aa + bb.v0 * ab);
+        const float jsy = L.rho0 * 0.5f * (ba.v1 * aa + bb.v1 * ab);
+        const float cj = cix * jsx + ciy * jsy;
+        return gi + kap * (gy_i - gk) - fac * (6.0f * w) * cj;
+    }
+    const float dvx = -L.lam_m_mu_r0 * dr_x;
+    const float sxx_x = -pxx_x + dvx, syy_x = -pyy_x + dvx, sxy_x = -pxy_x;
+    float drb = dr_x, sbxx = sxx_x, sbyy = syy_x, sbxy = sxy_x;
+    if (neu_ex) {
+        const float dvy = -L.lam_m_mu_r0 * my_dr;
+        const float a1 = 1.0f + q;
+        drb = a1 * dr_x - q * my_dr;
+        sbxx = a1 * sxx_x - q * (-my_xx + dvy);
+        sbyy = a1 * syy_x - q * (-my_yy + dvy);
+        sbxy = a1 * sxy_x - q * (-my_xy);
+    }
+    float sxx, syy, sxy;
+    if (b.corner & bit) {
+        float tax, tay, tbx, tby;
+        traction(bcs[lk.bc], lk.n0, 0.0f, tb, tax, tay);
+        traction(bcs[lk.bc2], 0.0f, lk.n1, tb, tbx, tby);
+        sxx = tax * lk.n0;
+        syy = tby * lk.n1;
+        sxy = 0.5f * (tay * lk.n0 + tbx * lk.n1);
+    } else {
+        const float n0 = lk.n0, n1 = lk.n1, t0 = -n1, t1 = n0;
+        float tx, ty;
+        traction(bcs[lk.bc], n0, n1, tb, tx, ty);
+        const float tn = tx * n0 + ty * n1, tt = tx * t0 + ty * t1;
+        const float stt = t0 * t0 * sbxx + 2.0f * t0 * t1 * sbxy + t1 * t1 * sbyy;
+        sxx = tn * n0 * n0 + 2.0f * tt * n0 * t0 + stt * t0 * t0;
+        syy = tn * n1 * n1 + 2.0f * tt * n1 * t1 + stt * t1 * t1;
+        sxy = tn * n0 * n1 + tt * (n0 * t1 + t0 * n1) + stt * t0 * t1;
+    }
+    const float dv = -L.lam_m_mu_r0 * drb;
+    const float pxx = -sxx + dv, pyy = -syy + dv, pxy = -sxy;
+    const float axx = pxx - drb * (1.0f / 3.0f), ayy = pyy - drb * (1.0f / 3.0f);
+    const float con = 4.5f * (cix * cix * axx + 2.0f * cix * ciy * pxy + ciy * ciy * ayy -
+                              (axx + ayy) * (1.0f / 3.0f));
+    const float eq = 2.0f * w * (drb + con);
+    return -gi - kap * (gy_i + gk) + fac * eq;
 }
 
 // Source S = F + (mu - lambda)/rho grad rho at an interior node (central
@@ -345,35 +503,54 @@ __device__ __forceinline__ void source_boundary(const float *__restrict__ rho, c
 // ---------------------------------------------------------------------------
 // Kernels.
 constexpr int kBX = 32, kBY = 8;
+constexpr int kBB = 64;  // threads per block of the boundary-list kernels
 
-template <class T>
+// Interior kernel: one node per thread (NR rows per thread, kBY rows apart).
+// Every load of a node -- the nine pulled populations and the displacement
+// record -- is issued before any arithmetic, so all of them are in flight
+// together.
+template <class T, int NR>
 __global__ void __launch_bounds__(kBX *kBY) k_interior(const T *__restrict__ src, T *__restrict__ dst,
                                                        float4 *__restrict__ uc,
                                                        const uint8_t *__restrict__ cls,
                                                        const float *__restrict__ rho, Lattice L,
                                                        uint32_t *__restrict__ status) {
     const int x = blockIdx.x * kBX + threadIdx.x;
-    const int y = blockIdx.y * kBY + threadIdx.y;
-    if (x >= L.nx || y >= L.ny) return;
-    const int64_t k = (int64_t)y * L.pitch + x;
-    if (cls[k] != kInterior) return;
-    float f[9];
-    pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
-    float sx = L.fx, sy = L.fy;
-    if (L.grad) {
-        const float rk = rho[k];
-        source_interior(rho, k, L.pitch, rk, L, sx, sy);
-    }
-    float dr, jx, jy;
-    collide(f, sx, sy, L, dr, jx, jy);
+    const int y0 = blockIdx.y * (kBY * NR) + threadIdx.y;
+    if (x >= L.nx) return;
+    bool live[NR];
+    int64_t k[NR];
+    float f[NR][9];
+    float4 w[NR];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.plane + k, f[i], L.scale);
-    integrate_u(uc + k, jx, jy, L.rho0 + dr);
-    flag_nonfinite(status, dr, jx, jy);
+    for (int r = 0; r < NR; ++r) {
+        const int y = y0 + r * kBY;
+        k[r] = (int64_t)y * L.pitch + x;
+        live[r] = y < L.ny && __ldg(cls + k[r]) == kInterior;
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+        if (live[r]) {
+            pull_interior(src, k[r], L.pitch, L.plane, L.inv_scale, f[r]);
+            w[r] = uc[k[r]];
+        }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        if (!live[r]) continue;
+        float sx = L.fx, sy = L.fy;
+        if (L.grad) source_interior(rho, k[r], L.pitch, rho[k[r]], L, sx, sy);
+        float dr, jx, jy;
+        collide(f[r], sx, sy, L, dr, jx, jy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.plane + k[r], f[r][i], L.scale);
+        integrate_u_value(w[r], jx, jy, L.rho0 + dr);
+        uc[k[r]] = w[r];
+        flag_nonfinite(status, dr, jx, jy);
+    }
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) k_boundary(const T *__restrict__ src, T *__restrict__ dst,
+__global__ void __launch_bounds__(kBB) k_boundary(const T *__restrict__ src, T *__restrict__ dst,
                                                   float4 *__restrict__ uc,
                                                   const BNode *__restrict__ bnodes,
                                                   const BLink *__restrict__ blinks,
@@ -398,6 +575,58 @@ __global__ void __launch_bounds__(128) k_boundary(const T *__restrict__ src, T *
     flag_nonfinite(status, dr, jx, jy);
 }
 
+constexpr int kB8 = 128;  // threads per block of the cooperative boundary kernel (16 nodes)
+
+template <class T>
+__global__ void __launch_bounds__(kB8) k_boundary8(const T *__restrict__ src, T *__restrict__ dst,
+                                                   float4 *__restrict__ uc,
+                                                   const BNode *__restrict__ bnodes,
+                                                   const BLink *__restrict__ blinks,
+                                                   const BCDev *__restrict__ bcs,
+                                                   const float *__restrict__ rho, Lattice L,
+                                                   const int64_t *__restrict__ time, int toff,
+                                                   uint32_t *__restrict__ status) {
+    const int g = (blockIdx.x * kB8 + threadIdx.x) >> 3;  // boundary node of this lane group
+    const int j = threadIdx.x & 7;
+    const bool lane0 = j == 0;
+    const bool live = g < L.nb;
+    // groups past the end compute on node 0 and store nothing: every lane
+    // takes part in the shuffles
+    const BNode b = bnodes[live ? g : 0];
+    const int kdir = j + 1;
+    const float tb = (float)(*time + toff - 1);
+    float f0;
+    const float fk = pull_boundary8(src, b, kdir, blinks + (int64_t)(live ? g : 0) * 8, bcs, tb,
+                                    L, lane0, f0);
+    const int64_t kn = (int64_t)b.y * L.pitch + b.x;
+    float sx = L.fx, sy = L.fy;
+    if (L.grad) source_boundary(rho, b, kn, rho[kn], L, sx, sy);
+    // collision on the raw moments (as collide())
+    const int cx = lane_cx(kdir), cy = lane_cy(kdir);
+    Raw m = grp8_raw(fk, f0, cx, cy, lane0);
+    const float jx = m.m10 + 0.5f * sx, jy = m.m01 + 0.5f * sy;
+    const float w = L.omega;
+    const float s3 = L.src * (1.0f / 3.0f);
+    m.m10 += sx;
+    m.m01 += sy;
+    m.m21 += w * (jy * (1.0f / 3.0f) - m.m21) + s3 * sy;
+    m.m12 += w * (jx * (1.0f / 3.0f) - m.m12) + s3 * sx;
+    m.m22 += w * ((m.m20 + m.m02) * (1.0f / 3.0f) - m.m00 * (1.0f / 9.0f) - m.m22);
+    float f[9];
+    populations(m, f);
+    float mine = f[1];
+#pragma unroll
+    for (int q = 2; q < 9; ++q)
+        if (kdir == q) mine = f[q];
+    if (!live) return;
+    Store<T>::st(dst + kdir * L.plane + kn, mine, L.scale);
+    if (lane0) {
+        Store<T>::st(dst + kn, f[0], L.scale);
+        integrate_u(uc + kn, jx, jy, L.rho0 + m.m00);
+        flag_nonfinite(status, m.m00, jx, jy);
+    }
+}
+
 // Density at time t of every material node (lambda != mu): pull, with the
 // boundary rules at boundary nodes.  Writes the deviation rho - rho0 into a
 // dense [ny][pitch] array.
@@ -416,7 +645,7 @@ __global__ void __launch_bounds__(kBX *kBY) k_density_interior(const T *__restri
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) k_density_boundary(const T *__restrict__ src,
+__global__ void __launch_bounds__(kBB) k_density_boundary(const T *__restrict__ src,
                                                           const BNode *__restrict__ bnodes,
                                                           const BLink *__restrict__ blinks,
                                                           const BCDev *__restrict__ bcs,
@@ -475,7 +704,7 @@ __global__ void __launch_bounds__(kBX *kBY) k_fields_interior(const T *__restric
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) k_fields_boundary(const T *__restrict__ src,
+__global__ void __launch_bounds__(kBB) k_fields_boundary(const T *__restrict__ src,
                                                          const float4 *__restrict__ uc,
                                                          const BNode *__restrict__ bnodes,
                                                          const BLink *__restrict__ blinks,
@@ -509,6 +738,52 @@ __global__ void k_gather_probe(const float *__restrict__ stage, const int32_t *_
 
 // ---------------------------------------------------------------------------
 // Launchers.
+
+// The boundary-list kernel runs beside the interior kernel; it is short and
+// latency-bound, so it is launched at the highest stream priority: its blocks
+// are placed before the interior kernel's pending blocks instead of waiting for
+// the interior grid to drain.
+static int high_priority() {
+    static const int p = [] {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return greatest;
+    }();
+    return p;
+}
+
+template <class T>
+static cudaError_t launch_boundary(const T *src, T *dst, const DevState &S, const Lattice &L,
+                                   int toff, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((L.nb + kB8 / 8 - 1) / (kB8 / 8));
+    cfg.blockDim = dim3(kB8);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = high_priority();
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_boundary8<T>, src, dst, S.ucomp,
+                              (const BNode *)S.bnodes, (const BLink *)S.blinks,
+                              (const BCDev *)S.bcs, (const float *)S.rho, L,
+                              (const int64_t *)S.time, toff, S.status);
+}
+
+template <class T>
+static void launch_interior(const T *src, T *dst, const DevState &S, const Lattice &L,
+                            cudaStream_t s) {
+    // one row per thread measured fastest for every storage (2 and 4 rows cost
+    // occupancy: 58+ registers)
+    constexpr int NR = 1;
+    const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY * NR - 1) / (kBY * NR));
+    k_interior<T, NR><<<grd, blk, 0, s>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status);
+}
+
 template <class T>
 static cudaError_t step_t(const Lattice &L, const DevState &S, int cur, int toff,
                           cudaStream_t s_main, cudaStream_t s_side, cudaEvent_t fork,
@@ -516,11 +791,11 @@ static cudaError_t step_t(const Lattice &L, const DevState &S, int cur, int toff
     const T *src = static_cast<const T *>(S.f[cur]);
     T *dst = static_cast<T *>(S.f[cur ^ 1]);
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
-    const int nbb = (L.nb + 127) / 128;
+    const int nbb = (L.nb + kBB - 1) / kBB;
     if (L.grad) {
         k_density_interior<T><<<grd, blk, 0, s_main>>>(src, S.cls, S.rho, L);
         if (L.nb > 0)
-            k_density_boundary<T><<<nbb, 128, 0, s_main>>>(src, S.bnodes, S.blinks, S.bcs, S.rho,
+            k_density_boundary<T><<<nbb, kBB, 0, s_main>>>(src, S.bnodes, S.blinks, S.bcs, S.rho,
                                                            L, S.time, toff);
     }
     const bool split = s_side && fork && join && L.nb > 0;
@@ -529,21 +804,18 @@ static cudaError_t step_t(const Lattice &L, const DevState &S, int cur, int toff
         cudaEventRecord(fork, s_main);
         cudaStreamWaitEvent(s_side, fork, 0);
         if (ev) cudaEventRecord(ev->before_boundary, s_side);
-        k_boundary<T><<<nbb, 128, 0, s_side>>>(src, dst, S.ucomp, S.bnodes, S.blinks, S.bcs,
-                                               S.rho, L, S.time, toff, S.status);
+        launch_boundary<T>(src, dst, S, L, toff, s_side);
         if (ev) cudaEventRecord(ev->after_boundary, s_side);
         cudaEventRecord(join, s_side);
     }
     if (ev) cudaEventRecord(ev->before_interior, s_main);
-    k_interior<T><<<grd, blk, 0, s_main>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status);
+    launch_interior<T>(src, dst, S, L, s_main);
     if (ev) cudaEventRecord(ev->after_interior, s_main);
     if (split) {
         cudaStreamWaitEvent(s_main, join, 0);
     } else {
         if (ev) cudaEventRecord(ev->before_boundary, s_b);
-        if (L.nb > 0)
-            k_boundary<T><<<nbb, 128, 0, s_b>>>(src, dst, S.ucomp, S.bnodes, S.blinks, S.bcs,
-                                                S.rho, L, S.time, toff, S.status);
+        if (L.nb > 0) launch_boundary<T>(src, dst, S, L, toff, s_b);
         if (ev) cudaEventRecord(ev->after_boundary, s_b);
     }
     return cudaGetLastError();
@@ -574,16 +846,16 @@ template <class T>
 static cudaError_t fields_t(const Lattice &L, const DevState &S, int cur, cudaStream_t s) {
     const T *src = static_cast<const T *>(S.f[cur]);
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
-    const int nbb = (L.nb + 127) / 128;
+    const int nbb = (L.nb + kBB - 1) / kBB;
     if (L.grad) {
         k_density_interior<T><<<grd, blk, 0, s>>>(src, S.cls, S.rho, L);
         if (L.nb > 0)
-            k_density_boundary<T><<<nbb, 128, 0, s>>>(src, S.bnodes, S.blinks, S.bcs, S.rho, L,
+            k_density_boundary<T><<<nbb, kBB, 0, s>>>(src, S.bnodes, S.blinks, S.bcs, S.rho, L,
                                                       S.time, 0);
     }
     k_fields_interior<T><<<grd, blk, 0, s>>>(src, S.ucomp, S.cls, S.rho, L, S.stage);
     if (L.nb > 0)
-        k_fields_boundary<T><<<nbb, 128, 0, s>>>(src, S.ucomp, S.bnodes, S.blinks, S.bcs, S.rho,
+        k_fields_boundary<T><<<nbb, kBB, 0, s>>>(src, S.ucomp, S.bnodes, S.blinks, S.bcs, S.rho,
                                                  L, S.time, S.stage);
     return cudaGetLastError();
 }
