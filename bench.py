@@ -182,6 +182,43 @@ def run_reference(args):
     return 0
 
 
+def _traffic(wl, storage):
+    """Measured DRAM bytes of one interior launch (profiles/traffic.json), or None
+    if the kernels have changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2208_04088_gb300", "csrc", "lbm_kernels.cu")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        if sha != t.get("kernels_sha256_16"):
+            return None
+        e = t[wl.name][storage]
+        return float(e["dram_read"] + e["dram_write"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def run_profile(args):
+    """A short run for ncu captures: --profile N direct-launch steps of the
+    workload (no graphs, no timing events), then exit."""
+    from paper_2208_04088_gb300 import _native as N
+    import torch
+    torch.cuda.set_device(0)
+    wl = _workload(args.workload)
+    s = N.Solver(N.desc_from_workload(wl, storage=args.storage,
+                                      wall_node=args.wall_values == "node"))
+    for _ in range(args.profile):
+        s.step(1)
+    s.sync()
+    s.close()
+    print(json.dumps({"profile_steps": args.profile, "workload": wl.name,
+                      "storage": args.storage}), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -330,7 +367,8 @@ def run_gpu(args):
                               "working set fits in L2; no flush inside a solve")},
             "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak,
                          "unit": "GB/s", "frac": achieved_gbs / peak,
-                         "traffic": args.traffic, "kernel": "k_interior",
+                         "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage),
+                         "kernel": "k_interior",
                          "bytes_per_update": bpu, "updates_per_launch": interior,
                          "mean_launch_ms": mean_interior_ms, "peak_kind": peak_kind,
                          "boundary_kernel_ms_per_step": tim["boundary_ms"] / max(1, tim["steps"]),
@@ -368,11 +406,15 @@ def main():
     ap.add_argument("--timing-solves", type=int, default=3,
                     help="solves of the second timed pass that times each kernel launch")
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
+    ap.add_argument("--profile", type=int, default=0,
+                    help="run this many direct-launch steps of the workload and exit (for ncu)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per interior launch, if measured for this kernel")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
     return run_gpu(args)
 
 
