@@ -248,6 +248,84 @@ lbm_status lbm_destroy(lbm_handle h);
 /* Text of the last error on the calling thread ("" if none). */
 const char *lbm_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Many instances, one launch per step.  The paper has one lattice per run;
+ * these entry points advance many independent lattices (Poisson solids,
+ * lambda = mu, one storage form) together.  A step is one persistent interior
+ * kernel over a table of (instance, tile) pairs and one persistent boundary
+ * kernel over a table of (instance, boundary node) pairs, running the same
+ * per-node code as lbm_step, so every instance's fields are bit-identical to
+ * the same instance stepped alone.  Steps replay a captured CUDA graph.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_engine *lbm_batch;
+typedef struct lbm_engine *lbm_server;
+
+/* Launch shape of the batched interior kernel: a tile of tile_x x tile_y
+ * threads (one node each; 32x4, 32x8, 32x16 or 64x4), a persistent grid of
+ * blocks_per_sm blocks per SM, tiles handed out statically (dynamic = 0,
+ * grid stride) or by an atomic counter (dynamic = 1). */
+typedef struct {
+    int32_t tile_x, tile_y, blocks_per_sm, dynamic;
+} lbm_launch_shape;
+
+typedef struct {
+    int32_t instances;
+    int32_t pad;
+    int64_t nodes;           /* material nodes over all instances */
+    int64_t steps;           /* steps run */
+    uint64_t device_bytes;   /* arena bytes in use */
+    int64_t kernel_launches;
+    lbm_launch_shape shape;
+} lbm_batch_stats;
+
+/* Create a batch of `count` instances (host descriptors as for lbm_create,
+ * every one with lambda = mu and the same storage), all at rest at t = 0.
+ * Device memory: one arena sized for all instances.  Synchronous. */
+lbm_status lbm_batch_create(const lbm_desc *descs, int32_t count, void *stream, lbm_batch *out);
+/* Advance every instance by nsteps (asynchronous). */
+lbm_status lbm_batch_step(lbm_batch b, int64_t nsteps);
+/* Fields of instance `index`, as lbm_get_fields. */
+lbm_status lbm_batch_get_fields(lbm_batch b, int32_t index, float *u, float *v, float *sigma,
+                                int32_t on_device);
+/* Autotuner: time each candidate launch shape on this batch for
+ * steps_per_trial steps (CUDA events), keep the fastest, then put every
+ * instance back to rest at t = 0.  `chosen` may be NULL.  Synchronous. */
+lbm_status lbm_batch_tune(lbm_batch b, int32_t steps_per_trial, lbm_launch_shape *chosen);
+lbm_status lbm_batch_set_shape(lbm_batch b, const lbm_launch_shape *shape);
+lbm_status lbm_batch_reset(lbm_batch b);
+/* Wait; LBM_ERR_UNSTABLE if any instance produced a non-finite moment. */
+lbm_status lbm_batch_sync(lbm_batch b);
+lbm_status lbm_batch_info(lbm_batch b, lbm_batch_stats *stats);
+lbm_status lbm_batch_destroy(lbm_batch b);
+
+/* Continuous-batching server.  Requests (a descriptor and a step count) are
+ * queued by lbm_server_submit; each lbm_server_tick admits queued requests in
+ * arrival order while their workspaces fit in the device budget, advances
+ * every admitted instance together by up to max_steps (never past the nearest
+ * completion), and retires the instances that reached their step count:
+ * their fields are copied to host memory and their device memory returns to
+ * the budget.  Requests that arrive while others run join at the next tick. */
+typedef struct {
+    int32_t active, queued;   /* after the tick */
+    int32_t admitted, finished; /* during the tick */
+    int64_t steps;            /* steps advanced by the tick */
+    int64_t active_nodes;
+    uint64_t device_bytes;
+    int64_t kernel_launches;  /* cumulative */
+} lbm_server_stats;
+
+lbm_status lbm_server_create(uint64_t hbm_budget_bytes, int32_t storage, void *stream,
+                             lbm_server *out);
+/* Queue a request; the descriptor's host arrays are copied. */
+lbm_status lbm_server_submit(lbm_server s, const lbm_desc *desc, int64_t nsteps, int64_t *id);
+lbm_status lbm_server_tick(lbm_server s, int32_t max_steps, lbm_server_stats *stats);
+/* *state: 0 queued, 1 running, 2 done (fields copied to the host arrays, any
+ * may be NULL, layouts of lbm_get_fields; the request is then forgotten).
+ * A failed request returns LBM_ERR_ARG with its error text. */
+lbm_status lbm_server_result(lbm_server s, int64_t id, int32_t *state, float *u, float *v,
+                             float *sigma);
+lbm_status lbm_server_destroy(lbm_server s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,23 @@ class lbm_info(C.Structure):
                 ("kernel_launches", C.c_int64)]
 
 
+class lbm_launch_shape(C.Structure):
+    _fields_ = [("tile_x", C.c_int32), ("tile_y", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("dynamic", C.c_int32)]
+
+
+class lbm_batch_stats(C.Structure):
+    _fields_ = [("instances", C.c_int32), ("pad", C.c_int32), ("nodes", C.c_int64),
+                ("steps", C.c_int64), ("device_bytes", C.c_uint64),
+                ("kernel_launches", C.c_int64), ("shape", lbm_launch_shape)]
+
+
+class lbm_server_stats(C.Structure):
+    _fields_ = [("active", C.c_int32), ("queued", C.c_int32), ("admitted", C.c_int32),
+                ("finished", C.c_int32), ("steps", C.c_int64), ("active_nodes", C.c_int64),
+                ("device_bytes", C.c_uint64), ("kernel_launches", C.c_int64)]
+
+
 class lbm_timing(C.Structure):
     _fields_ = [("interior_ms", C.c_double), ("boundary_ms", C.c_double), ("steps", C.c_int64)]
 
@@ -93,6 +110,24 @@ SIGNATURES = {
     "lbm_get_timing": (C.c_int, [C.c_void_p, C.POINTER(lbm_timing)]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, []),
+    "lbm_batch_create": (C.c_int, [C.POINTER(lbm_desc), C.c_int32, C.c_void_p,
+                                   C.POINTER(C.c_void_p)]),
+    "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_batch_get_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_int32]),
+    "lbm_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(lbm_launch_shape)]),
+    "lbm_batch_set_shape": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch_shape)]),
+    "lbm_batch_reset": (C.c_int, [C.c_void_p]),
+    "lbm_batch_sync": (C.c_int, [C.c_void_p]),
+    "lbm_batch_info": (C.c_int, [C.c_void_p, C.POINTER(lbm_batch_stats)]),
+    "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_server_create": (C.c_int, [C.c_uint64, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lbm_server_submit": (C.c_int, [C.c_void_p, C.POINTER(lbm_desc), C.c_int64,
+                                    C.POINTER(C.c_int64)]),
+    "lbm_server_tick": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(lbm_server_stats)]),
+    "lbm_server_result": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
+    "lbm_server_destroy": (C.c_int, [C.c_void_p]),
 }
 
 _lib = None
@@ -327,6 +362,127 @@ class Solver:
     def close(self) -> None:
         if getattr(self, "h", None) is not None and self.h.value:
             lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _shape_dict(sh):
+    return {"tile_x": sh.tile_x, "tile_y": sh.tile_y, "blocks_per_sm": sh.blocks_per_sm,
+            "dynamic": sh.dynamic}
+
+
+class Batch:
+    """Many lambda = mu instances advanced by one persistent launch per step
+    (lbm_batch_* of include/lbm.h).  Argument marshalling only."""
+
+    def __init__(self, descs, stream=None):
+        import torch
+        self.descs = list(descs)  # keeps the host arrays alive until create returns
+        arr = (lbm_desc * len(self.descs))()
+        for k, d in enumerate(self.descs):
+            arr[k] = d.c
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p(0)
+        _check(load().lbm_batch_create(arr, len(self.descs), C.c_void_p(self.stream.cuda_stream),
+                                       C.byref(h)))
+        self.h = h
+
+    def step(self, n):
+        _check(load().lbm_batch_step(self.h, C.c_int64(int(n))))
+
+    def fields_host(self, index):
+        d = self.descs[index]
+        u = np.empty((2, d.ny, d.nx), np.float32)
+        v = np.empty_like(u)
+        s = np.empty((3, d.ny, d.nx), np.float32)
+        _check(load().lbm_batch_get_fields(self.h, int(index), C.c_void_p(u.ctypes.data),
+                                           C.c_void_p(v.ctypes.data), C.c_void_p(s.ctypes.data), 0))
+        return {"u": u, "v": v, "sigma": s}
+
+    def tune(self, steps_per_trial=20):
+        sh = lbm_launch_shape()
+        _check(load().lbm_batch_tune(self.h, int(steps_per_trial), C.byref(sh)))
+        return _shape_dict(sh)
+
+    def set_shape(self, tile_x, tile_y, blocks_per_sm, dynamic):
+        sh = lbm_launch_shape(tile_x, tile_y, blocks_per_sm, dynamic)
+        _check(load().lbm_batch_set_shape(self.h, C.byref(sh)))
+
+    def reset(self):
+        _check(load().lbm_batch_reset(self.h))
+
+    def sync(self):
+        _check(load().lbm_batch_sync(self.h))
+
+    def info(self):
+        st = lbm_batch_stats()
+        _check(load().lbm_batch_info(self.h, C.byref(st)))
+        out = {k: getattr(st, k) for k, _ in lbm_batch_stats._fields_ if k not in ("pad", "shape")}
+        out["shape"] = _shape_dict(st.shape)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _check(load().lbm_batch_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server (lbm_server_* of include/lbm.h)."""
+
+    QUEUED, RUNNING, DONE = 0, 1, 2
+
+    def __init__(self, budget_bytes, storage="f32", stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p(0)
+        st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        _check(load().lbm_server_create(C.c_uint64(int(budget_bytes)), st,
+                                        C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+        self.shapes = {}
+
+    def submit(self, desc, nsteps):
+        rid = C.c_int64(0)
+        _check(load().lbm_server_submit(self.h, C.byref(desc.c), C.c_int64(int(nsteps)),
+                                        C.byref(rid)))
+        self.shapes[rid.value] = (desc.ny, desc.nx)
+        return rid.value
+
+    def tick(self, max_steps=64):
+        st = lbm_server_stats()
+        _check(load().lbm_server_tick(self.h, int(max_steps), C.byref(st)))
+        return {k: getattr(st, k) for k, _ in lbm_server_stats._fields_}
+
+    def result(self, rid):
+        """None while queued or running; the fields dict once done."""
+        ny, nx = self.shapes[rid]
+        u = np.empty((2, ny, nx), np.float32)
+        v = np.empty_like(u)
+        s = np.empty((3, ny, nx), np.float32)
+        state = C.c_int32(0)
+        _check(load().lbm_server_result(self.h, C.c_int64(rid), C.byref(state),
+                                        C.c_void_p(u.ctypes.data), C.c_void_p(v.ctypes.data),
+                                        C.c_void_p(s.ctypes.data)))
+        if state.value != self.DONE:
+            return None
+        del self.shapes[rid]
+        return {"u": u, "v": v, "sigma": s}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _check(load().lbm_server_destroy(self.h))
             self.h = None
 
     def __del__(self):

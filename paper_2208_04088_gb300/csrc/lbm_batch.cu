@@ -1,0 +1,832 @@
+// lbm_batch.cu -- many independent solver instances advanced by one persistent
+// launch per step: the lockstep batch (lbm_batch_*) and the continuous-batching
+// server (lbm_server_*) of include/lbm.h.
+//
+// Each instance is an ordinary lbm_solver whose workspace is carved from one
+// device arena.  Per step, a persistent interior kernel walks a table of
+// (instance, tile) pairs and a persistent cooperative boundary kernel walks a
+// table of (instance, boundary node) pairs; both run the per-node device code
+// of the single-solver kernels (lbm_device.cuh), so an instance computes
+// bit-identical fields alone and in a batch.  The table sizes and every
+// instance's clock live in device memory, so one captured CUDA graph stays
+// valid while instances come and go.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// Device descriptor of one instance.
+struct InstDev {
+    Lattice L;
+    void *f[2];
+    float4 *uc;
+    const uint8_t *cls;
+    const BNode *bn;
+    const BLink *bl;
+    const BCDev *bcs;
+    uint32_t *status;
+    int64_t *time;   // completed steps (the instance's own clock)
+    int64_t target;  // the instance stops stepping at this time
+    int32_t tiles_x, pad;
+};
+
+// Sizes of the work tables and the dynamic-schedule counters (device memory).
+struct BatchCounts {
+    int32_t ntiles, nbnodes, ninst, pad;
+    int32_t tile_counter, pad2[3];
+};
+
+namespace {
+
+constexpr int kChunk = 16;  // steps per replayed graph
+
+template <class T, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) k_batch_interior(const InstDev *__restrict__ insts,
+                                                           const int2 *__restrict__ tiles,
+                                                           BatchCounts *__restrict__ counts,
+                                                           int dynamic) {
+    const int ntiles = counts->ntiles;
+    __shared__ int s_tile;
+    int tile;
+    if (dynamic) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) s_tile = atomicAdd(&counts->tile_counter, 1);
+        __syncthreads();
+        tile = s_tile;
+    } else {
+        tile = blockIdx.x;
+    }
+    while (tile < ntiles) {
+        const int2 t = tiles[tile];
+        const InstDev &I = insts[t.x];
+        const int64_t time = *I.time;
+        if (time < I.target) {
+            const int tx = t.y % I.tiles_x, ty = t.y / I.tiles_x;
+            const int x = tx * TX + threadIdx.x, y = ty * TY + threadIdx.y;
+            if (x < I.L.nx && y < I.L.ny) {
+                const int cur = (int)(time & 1);
+                interior_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]),
+                                 I.uc, I.cls, nullptr, I.L, (int64_t)y * I.L.pitch + x, I.status);
+            }
+        }
+        if (dynamic) {
+            __syncthreads();
+            if (threadIdx.x == 0 && threadIdx.y == 0) s_tile = atomicAdd(&counts->tile_counter, 1);
+            __syncthreads();
+            tile = s_tile;
+        } else {
+            tile += gridDim.x;
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kB8) k_batch_boundary(const InstDev *__restrict__ insts,
+                                                        const int2 *__restrict__ bmap,
+                                                        const BatchCounts *__restrict__ counts) {
+    const int nb = counts->nbnodes;
+    constexpr int kGroups = kB8 / 8;
+    const int j = threadIdx.x & 7;
+    // the loop bound is uniform over the block, so all lanes reach the shuffles
+    for (int base = blockIdx.x * kGroups; base < nb; base += gridDim.x * kGroups) {
+        const int g = base + (threadIdx.x >> 3);
+        const bool in_list = g < nb;
+        const int2 m = bmap[in_list ? g : base];
+        const InstDev &I = insts[m.x];
+        const int64_t time = *I.time;
+        const bool live = in_list && time < I.target;
+        const int cur = (int)(time & 1);
+        boundary8_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]), I.uc,
+                          I.bn, I.bl, I.bcs, nullptr, I.L, m.y, live, j, (float)(time - 1),
+                          I.status);
+    }
+}
+
+__global__ void k_batch_advance(const InstDev *__restrict__ insts,
+                                BatchCounts *__restrict__ counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) counts->tile_counter = 0;
+    if (i < counts->ninst) {
+        int64_t *t = insts[i].time;
+        if (*t < insts[i].target) *t += 1;
+    }
+}
+
+lbm_status fail_cuda(cudaError_t e, const char *where) {
+    set_error(std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+              ")");
+    return LBM_ERR_CUDA;
+}
+
+// First-fit arena over one device allocation (256-byte granules).
+class Arena {
+   public:
+    lbm_status init(uint64_t bytes) {
+        bytes_ = (bytes + 255) / 256 * 256;
+        cudaError_t e = cudaMalloc(&base_, bytes_);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("arena: cudaMalloc of " + std::to_string(bytes_) + " bytes failed");
+            return LBM_ERR_NOMEM;
+        }
+        free_[0] = bytes_;
+        return LBM_OK;
+    }
+    ~Arena() {
+        if (base_) cudaFree(base_);
+    }
+    // returns offset or UINT64_MAX
+    uint64_t alloc(uint64_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second >= bytes) {
+                const uint64_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > bytes) free_[off + bytes] = len - bytes;
+                used_ += bytes;
+                return off;
+            }
+        return UINT64_MAX;
+    }
+    void release(uint64_t off, uint64_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    char *base() const { return static_cast<char *>(base_); }
+    uint64_t capacity() const { return bytes_; }
+    uint64_t used() const { return used_; }
+
+   private:
+    void *base_ = nullptr;
+    uint64_t bytes_ = 0, used_ = 0;
+    std::map<uint64_t, uint64_t> free_;
+};
+
+// Deep copy of an lbm_desc (the caller may free its arrays after submitting).
+struct DescCopy {
+    lbm_desc d;
+    std::vector<uint8_t> node_type;
+    std::vector<lbm_link> links;
+    std::vector<lbm_bc> bcs;
+    explicit DescCopy(const lbm_desc &src) : d(src) {
+        node_type.assign(src.node_type, src.node_type + (size_t)src.nx * src.ny);
+        links.assign(src.links, src.links + src.nlinks);
+        bcs.assign(src.bcs, src.bcs + src.nbcs);
+        d.node_type = node_type.data();
+        d.links = links.data();
+        d.bcs = bcs.data();
+    }
+};
+
+struct Instance {
+    int64_t id = -1;
+    lbm_solver *h = nullptr;
+    uint64_t off = 0, bytes = 0;
+    int64_t steps = 0;   // requested steps
+    int64_t done = 0;    // steps completed (host mirror)
+    int64_t nodes = 0;
+};
+
+struct Request {
+    int64_t id;
+    std::unique_ptr<DescCopy> desc;
+    int64_t steps;
+    int state = 0;  // 0 queued, 1 active, 2 done, 3 failed
+    std::vector<float> result;  // u(2N), v(2N), sigma(3N) when done
+    std::string error;
+};
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_engine {
+    int storage = LBM_F32;
+    bool server = false;
+    cudaStream_t stream = nullptr, cap_main = nullptr, cap_side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, ev0 = nullptr, ev1 = nullptr;
+    Arena arena;
+    std::vector<Instance> inst;          // active instances (table order)
+    std::map<int64_t, Request> requests; // server requests by id
+    std::vector<int64_t> queue;          // queued request ids (FIFO)
+    int64_t next_id = 0;
+    // device tables
+    InstDev *d_inst = nullptr;
+    int2 *d_tiles = nullptr, *d_bmap = nullptr;
+    BatchCounts *d_counts = nullptr;
+    int cap_inst = 0;
+    int64_t cap_tiles = 0, cap_bnodes = 0;
+    bool tables_dirty = true;
+    lbm_launch_shape shape{32, 8, 8, 0};
+    int sms = 0;
+    cudaGraphExec_t graph = nullptr;
+    int64_t launches = 0;
+    int64_t step_count = 0;  // steps run by the engine
+    ~lbm_engine();
+};
+
+namespace {
+
+lbm_status ensure_capacity(lbm_engine *E, int ninst, int64_t ntiles, int64_t nbnodes) {
+    bool realloc = false;
+    cudaError_t e = cudaSuccess;
+    if (ninst > E->cap_inst) {
+        if (E->d_inst) cudaFree(E->d_inst);
+        E->cap_inst = std::max(ninst, 2 * E->cap_inst);
+        e = cudaMalloc(&E->d_inst, sizeof(InstDev) * E->cap_inst);
+        realloc = true;
+    }
+    if (e == cudaSuccess && ntiles > E->cap_tiles) {
+        if (E->d_tiles) cudaFree(E->d_tiles);
+        E->cap_tiles = std::max<int64_t>(ntiles, 2 * E->cap_tiles);
+        e = cudaMalloc(&E->d_tiles, sizeof(int2) * E->cap_tiles);
+        realloc = true;
+    }
+    if (e == cudaSuccess && nbnodes > E->cap_bnodes) {
+        if (E->d_bmap) cudaFree(E->d_bmap);
+        E->cap_bnodes = std::max<int64_t>(std::max<int64_t>(nbnodes, 1), 2 * E->cap_bnodes);
+        e = cudaMalloc(&E->d_bmap, sizeof(int2) * E->cap_bnodes);
+        realloc = true;
+    }
+    if (e == cudaSuccess && !E->d_counts) {
+        e = cudaMalloc(&E->d_counts, sizeof(BatchCounts));
+        if (e == cudaSuccess) e = cudaMemset(E->d_counts, 0, sizeof(BatchCounts));
+        realloc = true;
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "batch: table allocation");
+    if (realloc && E->graph) {
+        cudaGraphExecDestroy(E->graph);
+        E->graph = nullptr;
+    }
+    return LBM_OK;
+}
+
+// Rebuild the instance, tile and boundary-node tables on the device.
+lbm_status rebuild_tables(lbm_engine *E) {
+    const int TX = E->shape.tile_x, TY = E->shape.tile_y;
+    std::vector<InstDev> hi(E->inst.size());
+    std::vector<int2> tiles, bmap;
+    for (size_t i = 0; i < E->inst.size(); ++i) {
+        const lbm_solver *h = E->inst[i].h;
+        InstDev &d = hi[i];
+        std::memset(&d, 0, sizeof d);
+        d.L = h->L;
+        d.f[0] = h->S.f[0];
+        d.f[1] = h->S.f[1];
+        d.uc = h->S.ucomp;
+        d.cls = h->S.cls;
+        d.bn = h->S.bnodes;
+        d.bl = h->S.blinks;
+        d.bcs = h->S.bcs;
+        d.status = h->S.status;
+        d.time = h->S.time;
+        d.target = E->server ? E->inst[i].steps : INT64_MAX;
+        d.tiles_x = (h->L.nx + TX - 1) / TX;
+        const int tiles_y = (h->L.ny + TY - 1) / TY;
+        for (int t = 0; t < d.tiles_x * tiles_y; ++t) tiles.push_back(make_int2((int)i, t));
+        for (int b = 0; b < h->L.nb; ++b) bmap.push_back(make_int2((int)i, b));
+    }
+    lbm_status st = ensure_capacity(E, (int)hi.size(), (int64_t)tiles.size(), (int64_t)bmap.size());
+    if (st != LBM_OK) return st;
+    BatchCounts c;
+    std::memset(&c, 0, sizeof c);
+    c.ntiles = (int32_t)tiles.size();
+    c.nbnodes = (int32_t)bmap.size();
+    c.ninst = (int32_t)hi.size();
+    cudaError_t e = cudaSuccess;
+    if (!hi.empty())
+        e = cudaMemcpyAsync(E->d_inst, hi.data(), sizeof(InstDev) * hi.size(),
+                            cudaMemcpyHostToDevice, E->stream);
+    if (e == cudaSuccess && !tiles.empty())
+        e = cudaMemcpyAsync(E->d_tiles, tiles.data(), sizeof(int2) * tiles.size(),
+                            cudaMemcpyHostToDevice, E->stream);
+    if (e == cudaSuccess && !bmap.empty())
+        e = cudaMemcpyAsync(E->d_bmap, bmap.data(), sizeof(int2) * bmap.size(),
+                            cudaMemcpyHostToDevice, E->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(E->d_counts, &c, sizeof c, cudaMemcpyHostToDevice, E->stream);
+    // the host vectors die here: wait for the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "batch: table upload");
+    E->tables_dirty = false;
+    return LBM_OK;
+}
+
+int high_priority_value() {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return greatest;
+}
+
+template <class T, int TX, int TY>
+cudaError_t launch_interior_shape(lbm_engine *E, cudaStream_t s) {
+    const dim3 blk(TX, TY), grd(E->shape.blocks_per_sm * E->sms);
+    k_batch_interior<T, TX, TY><<<grd, blk, 0, s>>>(E->d_inst, E->d_tiles, E->d_counts,
+                                                     E->shape.dynamic);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_batch_step_t(lbm_engine *E, cudaStream_t s_main, cudaStream_t s_side) {
+    // boundary nodes beside the interior tiles, at the highest priority
+    cudaEventRecord(E->fork, s_main);
+    cudaStreamWaitEvent(s_side, E->fork, 0);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * E->sms);
+    cfg.blockDim = dim3(kB8);
+    cfg.stream = s_side;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = high_priority_value();
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch_boundary<T>, (const InstDev *)E->d_inst,
+                                       (const int2 *)E->d_bmap,
+                                       (const BatchCounts *)E->d_counts);
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(E->join, s_side);
+    const int TX = E->shape.tile_x, TY = E->shape.tile_y;
+    if (TX == 32 && TY == 8)
+        e = launch_interior_shape<T, 32, 8>(E, s_main);
+    else if (TX == 32 && TY == 4)
+        e = launch_interior_shape<T, 32, 4>(E, s_main);
+    else if (TX == 64 && TY == 4)
+        e = launch_interior_shape<T, 64, 4>(E, s_main);
+    else
+        e = launch_interior_shape<T, 32, 16>(E, s_main);
+    if (e != cudaSuccess) return e;
+    cudaStreamWaitEvent(s_main, E->join, 0);
+    k_batch_advance<<<(std::max(1, E->cap_inst) + 255) / 256, 256, 0, s_main>>>(E->d_inst,
+                                                                               E->d_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_step(lbm_engine *E, cudaStream_t s_main, cudaStream_t s_side) {
+    switch (E->storage) {
+        case LBM_F16_DEV:
+            return launch_batch_step_t<__half>(E, s_main, s_side);
+        case LBM_BF16_DEV:
+            return launch_batch_step_t<__nv_bfloat16>(E, s_main, s_side);
+        default:
+            return launch_batch_step_t<float>(E, s_main, s_side);
+    }
+}
+
+lbm_status build_batch_graph(lbm_engine *E) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(E->cap_main, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail_cuda(e, "batch: begin capture");
+    for (int s = 0; s < kChunk && e == cudaSuccess; ++s)
+        e = launch_batch_step(E, E->cap_main, E->cap_side);
+    cudaError_t e2 = cudaStreamEndCapture(E->cap_main, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail_cuda(e != cudaSuccess ? e : e2, "batch: capture");
+    }
+    e = cudaGraphInstantiate(&E->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail_cuda(e, "batch: instantiate");
+    return LBM_OK;
+}
+
+// Advance every active instance by nsteps (instances past their target idle).
+lbm_status engine_steps(lbm_engine *E, int64_t nsteps) {
+    if (E->tables_dirty) {
+        lbm_status st = rebuild_tables(E);
+        if (st != LBM_OK) return st;
+    }
+    if (E->inst.empty() || nsteps <= 0) return LBM_OK;
+    cudaError_t e = cudaSuccess;
+    int64_t done = 0;
+    if (nsteps >= kChunk) {
+        if (!E->graph) {
+            lbm_status st = build_batch_graph(E);
+            if (st != LBM_OK) return st;
+        }
+        for (; done + kChunk <= nsteps; done += kChunk) {
+            e = cudaGraphLaunch(E->graph, E->stream);
+            if (e != cudaSuccess) return fail_cuda(e, "batch: graph launch");
+        }
+    }
+    for (; done < nsteps; ++done) {
+        e = launch_batch_step(E, E->stream, E->cap_side);
+        if (e != cudaSuccess) return fail_cuda(e, "batch: launch");
+    }
+    E->launches += 3 * nsteps;
+    E->step_count += nsteps;
+    for (auto &I : E->inst) {
+        I.done = E->server ? std::min(I.steps, I.done + nsteps) : I.done + nsteps;
+        I.h->time = I.done;
+        I.h->cur = (int)(I.done & 1);
+    }
+    return LBM_OK;
+}
+
+lbm_status engine_init(lbm_engine *E, int storage, void *stream) {
+    E->storage = storage;
+    E->stream = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&E->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&E->cap_main, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&E->cap_side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&E->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&E->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&E->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&E->ev1);
+    if (e != cudaSuccess) return fail_cuda(e, "engine: init");
+    return LBM_OK;
+}
+
+// Admit one instance into the arena; LBM_ERR_NOMEM if it does not fit now.
+lbm_status admit(lbm_engine *E, const lbm_desc &d, int64_t id, int64_t steps) {
+    uint64_t bytes = 0;
+    lbm_status st = lbm_workspace_size(&d, &bytes);
+    if (st != LBM_OK) return st;
+    {
+        // the batched kernels implement the lambda = mu path (no density pass)
+        Units u;
+        if (make_units(d, &u) != LBM_OK) return LBM_ERR_ARG;
+        if (u.lam != u.mu) {
+            set_error("batch/server: instances must have lambda = mu (the density pass of the "
+                      "lambda != mu source is single-solver only)");
+            return LBM_ERR_ARG;
+        }
+        if (d.storage != E->storage) {
+            set_error("batch/server: every instance must use the engine's storage");
+            return LBM_ERR_ARG;
+        }
+    }
+    const uint64_t off = E->arena.alloc(bytes);
+    if (off == UINT64_MAX) {
+        set_error("batch/server: not enough room in the device budget");
+        return LBM_ERR_NOMEM;
+    }
+    lbm_handle h = nullptr;
+    st = lbm_create(&d, E->stream, E->arena.base() + off, bytes, &h);
+    if (st != LBM_OK) {
+        E->arena.release(off, bytes);
+        return st;
+    }
+    Instance I;
+    I.id = id;
+    I.h = h;
+    I.off = off;
+    I.bytes = bytes;
+    I.steps = steps;
+    I.nodes = h->tab.interior + h->L.nb;
+    E->inst.push_back(I);
+    E->tables_dirty = true;
+    return LBM_OK;
+}
+
+void retire(lbm_engine *E, size_t k) {
+    Instance &I = E->inst[k];
+    lbm_destroy(I.h);
+    E->arena.release(I.off, I.bytes);
+    E->inst.erase(E->inst.begin() + (long)k);
+    E->tables_dirty = true;
+}
+
+}  // namespace
+
+lbm_engine::~lbm_engine() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto &I : inst) lbm_destroy(I.h);
+    inst.clear();
+    if (graph) cudaGraphExecDestroy(graph);
+    if (d_inst) cudaFree(d_inst);
+    if (d_tiles) cudaFree(d_tiles);
+    if (d_bmap) cudaFree(d_bmap);
+    if (d_counts) cudaFree(d_counts);
+    if (cap_main) cudaStreamDestroy(cap_main);
+    if (cap_side) cudaStreamDestroy(cap_side);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+}
+
+// ---------------------------------------------------------------------------
+// Lockstep batch.
+
+extern "C" lbm_status lbm_batch_create(const lbm_desc *descs, int32_t count, void *stream,
+                                       lbm_batch *out) {
+    set_error("");
+    if (!descs || count < 1 || !out) {
+        set_error("lbm_batch_create: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    *out = nullptr;
+    std::unique_ptr<lbm_engine> E(new lbm_engine());
+    lbm_status st = engine_init(E.get(), descs[0].storage, stream);
+    if (st != LBM_OK) return st;
+    uint64_t total = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        uint64_t b = 0;
+        st = lbm_workspace_size(&descs[i], &b);
+        if (st != LBM_OK) return st;
+        total += (b + 255) / 256 * 256;
+    }
+    st = E->arena.init(total);
+    if (st != LBM_OK) return st;
+    for (int32_t i = 0; i < count; ++i) {
+        st = admit(E.get(), descs[i], i, INT64_MAX);
+        if (st != LBM_OK) return st;
+    }
+    st = rebuild_tables(E.get());
+    if (st != LBM_OK) return st;
+    *out = E.release();
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_step(lbm_batch b, int64_t nsteps) {
+    set_error("");
+    if (!b || nsteps < 0) {
+        set_error("lbm_batch_step: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    return engine_steps(b, nsteps);
+}
+
+extern "C" lbm_status lbm_batch_get_fields(lbm_batch b, int32_t index, float *u, float *v,
+                                           float *sigma, int32_t on_device) {
+    set_error("");
+    if (!b || index < 0 || index >= (int32_t)b->inst.size()) {
+        set_error("lbm_batch_get_fields: bad instance index");
+        return LBM_ERR_ARG;
+    }
+    return lbm_get_fields(b->inst[index].h, u, v, sigma, on_device);
+}
+
+extern "C" lbm_status lbm_batch_set_shape(lbm_batch b, const lbm_launch_shape *shape) {
+    set_error("");
+    if (!b || !shape) {
+        set_error("lbm_batch_set_shape: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    const bool ok_tile = (shape->tile_x == 32 && (shape->tile_y == 4 || shape->tile_y == 8 ||
+                                                  shape->tile_y == 16)) ||
+                         (shape->tile_x == 64 && shape->tile_y == 4);
+    if (!ok_tile || shape->blocks_per_sm < 1 || shape->blocks_per_sm > 64 ||
+        (shape->dynamic != 0 && shape->dynamic != 1)) {
+        set_error("lbm_batch_set_shape: tiles 32x4, 32x8, 32x16 or 64x4; 1..64 blocks per SM");
+        return LBM_ERR_ARG;
+    }
+    b->shape = *shape;
+    b->tables_dirty = true;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_reset(lbm_batch b) {
+    set_error("");
+    if (!b) {
+        set_error("lbm_batch_reset: NULL batch");
+        return LBM_ERR_ARG;
+    }
+    for (auto &I : b->inst) {
+        lbm_status st = lbm_reset(I.h);
+        if (st != LBM_OK) return st;
+        I.done = 0;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_sync(lbm_batch b) {
+    set_error("");
+    if (!b) {
+        set_error("lbm_batch_sync: NULL batch");
+        return LBM_ERR_ARG;
+    }
+    for (auto &I : b->inst) {
+        lbm_status st = lbm_sync(I.h);
+        if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_tune(lbm_batch b, int32_t steps_per_trial,
+                                     lbm_launch_shape *chosen) {
+    set_error("");
+    if (!b || steps_per_trial < 1) {
+        set_error("lbm_batch_tune: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    const lbm_launch_shape cands[] = {
+        {32, 8, 8, 0}, {32, 8, 8, 1}, {32, 8, 4, 0}, {32, 8, 4, 1}, {32, 4, 16, 0},
+        {32, 4, 16, 1}, {64, 4, 8, 0}, {64, 4, 8, 1}, {32, 16, 4, 0}, {32, 16, 4, 1}};
+    float best = 1e30f;
+    lbm_launch_shape best_shape = b->shape;
+    for (const auto &c : cands) {
+        lbm_status st = lbm_batch_set_shape(b, &c);
+        if (st == LBM_OK) st = engine_steps(b, 2);  // warm-up (tables, caches)
+        if (st != LBM_OK) return st;
+        cudaEventRecord(b->ev0, b->stream);
+        st = engine_steps(b, steps_per_trial);
+        if (st != LBM_OK) return st;
+        cudaEventRecord(b->ev1, b->stream);
+        cudaError_t e = cudaEventSynchronize(b->ev1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+        if (e != cudaSuccess) return fail_cuda(e, "lbm_batch_tune");
+        if (ms < best) {
+            best = ms;
+            best_shape = c;
+        }
+    }
+    lbm_status st = lbm_batch_set_shape(b, &best_shape);
+    if (st == LBM_OK) st = lbm_batch_reset(b);
+    if (st == LBM_OK && chosen) *chosen = best_shape;
+    return st;
+}
+
+extern "C" lbm_status lbm_batch_info(lbm_batch b, lbm_batch_stats *stats) {
+    set_error("");
+    if (!b || !stats) {
+        set_error("lbm_batch_info: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    std::memset(stats, 0, sizeof *stats);
+    stats->instances = (int32_t)b->inst.size();
+    for (auto &I : b->inst) stats->nodes += I.nodes;
+    stats->steps = b->step_count;
+    stats->device_bytes = b->arena.used();
+    stats->kernel_launches = b->launches;
+    stats->shape = b->shape;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_destroy(lbm_batch b) {
+    delete b;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Continuous-batching server.
+
+extern "C" lbm_status lbm_server_create(uint64_t hbm_budget_bytes, int32_t storage, void *stream,
+                                        lbm_server *out) {
+    set_error("");
+    if (!out || hbm_budget_bytes < (1u << 20) || storage < LBM_F32 || storage > LBM_BF16_DEV) {
+        set_error("lbm_server_create: bad arguments (budget >= 1 MiB, known storage)");
+        return LBM_ERR_ARG;
+    }
+    *out = nullptr;
+    std::unique_ptr<lbm_engine> E(new lbm_engine());
+    E->server = true;
+    lbm_status st = engine_init(E.get(), storage, stream);
+    if (st == LBM_OK) st = E->arena.init(hbm_budget_bytes);
+    if (st != LBM_OK) return st;
+    *out = E.release();
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_server_submit(lbm_server s, const lbm_desc *desc, int64_t nsteps,
+                                        int64_t *id) {
+    set_error("");
+    if (!s || !desc || nsteps < 1 || !id) {
+        set_error("lbm_server_submit: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    // validate now, so a bad request fails at submission
+    uint64_t bytes = 0;
+    lbm_status st = lbm_workspace_size(desc, &bytes);
+    if (st != LBM_OK) return st;
+    if (bytes > s->arena.capacity()) {
+        set_error("lbm_server_submit: the request alone exceeds the device budget");
+        return LBM_ERR_NOMEM;
+    }
+    Request r;
+    r.id = s->next_id++;
+    r.desc.reset(new DescCopy(*desc));
+    r.steps = nsteps;
+    *id = r.id;
+    s->queue.push_back(r.id);
+    s->requests.emplace(r.id, std::move(r));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_server_tick(lbm_server s, int32_t max_steps, lbm_server_stats *stats) {
+    set_error("");
+    if (!s || max_steps < 1) {
+        set_error("lbm_server_tick: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    int32_t admitted = 0, finished = 0;
+    // admit queued requests in arrival order while they fit
+    while (!s->queue.empty()) {
+        Request &r = s->requests.at(s->queue.front());
+        lbm_status st = admit(s, r.desc->d, r.id, r.steps);
+        if (st == LBM_ERR_NOMEM) break;
+        s->queue.erase(s->queue.begin());
+        if (st != LBM_OK) {
+            r.state = 3;
+            r.error = lbm_last_error();
+            continue;
+        }
+        r.state = 1;
+        ++admitted;
+    }
+    // advance: at most max_steps, and no further than the nearest completion
+    int64_t adv = max_steps;
+    for (auto &I : s->inst) adv = std::min(adv, I.steps - I.done);
+    if (!s->inst.empty()) {
+        if (adv < 1) adv = 1;
+        lbm_status st = engine_steps(s, adv);
+        if (st != LBM_OK) return st;
+    }
+    // retire finished instances: fields to host, free their memory
+    for (size_t k = 0; k < s->inst.size();) {
+        Instance &I = s->inst[k];
+        if (I.done < I.steps) {
+            ++k;
+            continue;
+        }
+        Request &r = s->requests.at(I.id);
+        const int64_t N = (int64_t)I.h->L.nx * I.h->L.ny;
+        r.result.assign(7 * N, 0.0f);
+        lbm_status st = lbm_get_fields(I.h, r.result.data(), r.result.data() + 2 * N,
+                                       r.result.data() + 4 * N, 0);
+        if (st == LBM_OK) st = lbm_sync(I.h);
+        r.state = st == LBM_OK ? 2 : 3;
+        if (st != LBM_OK) r.error = lbm_last_error();
+        r.desc.reset();
+        retire(s, k);
+        ++finished;
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->active = (int32_t)s->inst.size();
+        stats->queued = (int32_t)s->queue.size();
+        stats->admitted = admitted;
+        stats->finished = finished;
+        stats->steps = adv;
+        for (auto &I : s->inst) stats->active_nodes += I.nodes;
+        stats->device_bytes = s->arena.used();
+        stats->kernel_launches = s->launches;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_server_result(lbm_server s, int64_t id, int32_t *state, float *u,
+                                        float *v, float *sigma) {
+    set_error("");
+    if (!s || !state) {
+        set_error("lbm_server_result: bad arguments");
+        return LBM_ERR_ARG;
+    }
+    auto it = s->requests.find(id);
+    if (it == s->requests.end()) {
+        set_error("lbm_server_result: unknown or already collected request");
+        return LBM_ERR_ARG;
+    }
+    Request &r = it->second;
+    *state = r.state;
+    if (r.state == 3) {
+        set_error("lbm_server_result: request failed: " + r.error);
+        s->requests.erase(it);
+        return LBM_ERR_ARG;
+    }
+    if (r.state != 2) return LBM_OK;
+    const size_t N = r.result.size() / 7;
+    if (u) std::memcpy(u, r.result.data(), 2 * N * sizeof(float));
+    if (v) std::memcpy(v, r.result.data() + 2 * N, 2 * N * sizeof(float));
+    if (sigma) std::memcpy(sigma, r.result.data() + 4 * N, 3 * N * sizeof(float));
+    s->requests.erase(it);
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_server_destroy(lbm_server s) {
+    delete s;
+    return LBM_OK;
+}

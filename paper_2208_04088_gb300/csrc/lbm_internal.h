@@ -135,3 +135,33 @@ cudaError_t launch_gather_probe(const Lattice &L, const DevState &S, int count,
 cudaError_t launch_reset(int storage, const Lattice &L, const DevState &S, cudaStream_t s);
 
 }  // namespace lbm
+
+// One solver instance (the object behind lbm_handle).
+struct lbm_solver {
+    lbm::Tables tab;
+    lbm::Units units;
+    lbm::Lattice L;
+    lbm::DevState S;
+    int storage = LBM_F32;
+    cudaStream_t stream = nullptr;  // caller's stream
+    cudaStream_t cap_main = nullptr, cap_side = nullptr;  // private capture streams
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t gfork = nullptr, gjoin = nullptr;         // events used inside graphs
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};        // chunk starting in buffer 0/1
+    int cur = 0;
+    int64_t time = 0;
+    void *owned = nullptr;  // cudaMalloc'ed workspace, if the library allocated it
+    void *base = nullptr;
+    uint64_t bytes = 0;
+    int32_t *h_probe_idx = nullptr;  // pinned host staging for probes
+    float *h_probe_out = nullptr;
+    uint32_t *h_status = nullptr;    // pinned copy of the status word
+    cudaEvent_t status_ready = nullptr;
+    bool status_pending = false;
+    int64_t launches = 0;            // kernels launched by this handle
+    // timing mode: events around every interior and boundary kernel
+    bool timing = false;
+    std::vector<lbm::StepEvents> ev_pool;
+    size_t ev_used = 0;
+};
+
