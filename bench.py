@@ -37,7 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS (giga lattice updates per second, whole job)"
-WORKLOADS = ("crack", "plate")
+WORKLOADS = ("crack", "plate", "batch", "serve")
 
 
 def _workload(name):
@@ -216,6 +216,171 @@ def run_profile(args):
     s.close()
     print(json.dumps({"profile_steps": args.profile, "workload": wl.name,
                       "storage": args.storage}), flush=True)
+    return 0
+
+
+def run_batch(args):
+    """Config 4: 256 seeded plate-with-hole instances, 5000 steps each, advanced
+    together by the batched persistent launch (autotuned shape, replayed
+    graphs); beside it the same instances solved one after another through
+    lbm_step in FP32 (the per-instance loop)."""
+    import torch
+
+    from paper_2208_04088_gb300 import _native as N
+    from paper_2208_04088_gb300 import workloads as W
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N.load(build_if_missing=False)
+    wls = W.batched_instances(args.batch_count, seed=4, steps=args.batch_steps)
+    stream = torch.cuda.Stream(device=dev)
+    wall_node = args.wall_values == "node"
+    descs = [N.desc_from_workload(w, storage=args.storage, wall_node=wall_node) for w in wls]
+    b = N.Batch(descs, stream=stream)
+    shape = b.tune(steps_per_trial=20)
+    nodes = b.info()["nodes"]
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        b.reset()
+        b.step(args.batch_steps)
+    barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        start.record(stream)
+        for _ in range(args.steps):
+            b.reset()
+            b.step(args.batch_steps)
+        stop.record(stream)
+        barrier()
+    unstable = b.info()["unstable"]
+    ms = start.elapsed_time(stop)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item())
+    value = nodes * args.batch_steps * args.steps * world / (ms * 1e-3) / 1e9
+    launches = b.info()["kernel_launches"]
+    b.close()
+
+    # the per-instance FP32 loop over the same instances (one pass)
+    loop = None
+    if not args.no_loop:
+        s_loop = torch.cuda.Event(enable_timing=True)
+        e_loop = torch.cuda.Event(enable_timing=True)
+        solvers = [N.Solver(N.desc_from_workload(w, wall_node=wall_node), stream=stream)
+                   for w in wls]
+        barrier()
+        s_loop.record(stream)
+        for sv in solvers:
+            sv.step(args.batch_steps)
+        e_loop.record(stream)
+        barrier()
+        lms = s_loop.elapsed_time(e_loop)
+        loop = {"value": nodes * args.batch_steps / (lms * 1e-3) / 1e9, "unit": "GLUPS",
+                "storage": "f32", "how": "lbm_step per instance, one after another"}
+        for sv in solvers:
+            sv.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": f"batched_{len(wls)}_hole_plates_seed4",
+                       "instances": len(wls), "material_nodes": nodes,
+                       "time_steps": args.batch_steps, "storage": args.storage + " deviations",
+                       "wall_values": args.wall_values, "tuned_shape": shape,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2"},
+            "unstable_instances": unstable,
+            "per_instance_loop": loop,
+            "clocks": clocks.summary(), "gpu_launches": int(launches),
+            "roofline": None, "e2e": None, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_serve(args):
+    """Config 5: a seeded trace of solve requests with Poisson arrivals, served
+    by the continuous-batching server under an HBM budget; p50/p99 latency from
+    arrival to fields-on-host, and aggregate GLUPS over the makespan."""
+    import torch
+
+    from paper_2208_04088_gb300 import _native as N
+    from paper_2208_04088_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    N.load(build_if_missing=False)
+    trace = W.serving_trace(args.requests, seed=5, rate=args.rate,
+                            max_side=args.max_side, max_steps=args.max_steps)
+    wall_node = args.wall_values == "node"
+    stream = torch.cuda.Stream()
+    srv = N.Server(int(args.budget_gb * (1 << 30)), storage=args.storage, stream=stream)
+    # warm the kernels and the graph on a small request
+    wid = srv.submit(N.desc_from_workload(W.square_plate(64, 0), storage=args.storage,
+                                          wall_node=wall_node), 64)
+    while srv.result(wid) is None:
+        srv.tick(args.tick_steps)
+    lat = []
+    lu = 0
+    unstable = 0
+    pending = list(trace)
+    live = {}
+    t0 = time.perf_counter()
+    with ClockSampler(0) as clocks:
+        while pending or live:
+            now = time.perf_counter() - t0
+            while pending and pending[0][0] <= now:
+                at, w = pending.pop(0)
+                d = N.desc_from_workload(w, storage=args.storage, wall_node=wall_node)
+                live[srv.submit(d, w.steps)] = (at, w.nodes * w.steps)
+            if not live:
+                time.sleep(min(0.01, max(0.0, pending[0][0] - now)))
+                continue
+            srv.tick(args.tick_steps)
+            for rid in list(live):
+                r = srv.result(rid)
+                if r is not None:
+                    unstable += int(r["unstable"])
+                    at, work = live.pop(rid)
+                    lat.append(time.perf_counter() - t0 - at)
+                    lu += work
+    makespan = time.perf_counter() - t0
+    srv.close()
+    lat = sorted(lat)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    line = {
+        "metric": METRIC, "value": lu / makespan / 1e9, "unit": "GLUPS", "n_gpus": 1,
+        "steps": len(lat), "warmup": 1, "ms_per_step": makespan / len(lat) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": f"serving_trace_seed5_rate{args.rate:g}_n{len(lat)}",
+                   "rate_per_s": args.rate, "requests": len(lat),
+                   "sides": f"64..{args.max_side} (powers of two)",
+                   "steps": f"1000..{args.max_steps} log-uniform",
+                   "budget_gb": args.budget_gb, "tick_steps": args.tick_steps,
+                   "storage": args.storage + " deviations", "wall_values": args.wall_values},
+        "latency_s": {"p50": p50, "p99": p99, "max": lat[-1]},
+        "unstable_requests": unstable,
+        "makespan_s": makespan, "clocks": clocks.summary(),
+        "roofline": None, "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -406,6 +571,15 @@ def main():
     ap.add_argument("--timing-solves", type=int, default=3,
                     help="solves of the second timed pass that times each kernel launch")
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--no-loop", action="store_true", help="batch: skip the per-instance loop")
+    ap.add_argument("--rate", type=float, default=2.0, help="serve: mean arrivals per second")
+    ap.add_argument("--requests", type=int, default=60)
+    ap.add_argument("--max-side", type=int, default=2048)
+    ap.add_argument("--max-steps", type=int, default=50000)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--tick-steps", type=int, default=256)
     ap.add_argument("--profile", type=int, default=0,
                     help="run this many direct-launch steps of the workload and exit (for ncu)")
     ap.add_argument("--traffic", type=float, default=None,
@@ -415,6 +589,10 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 

@@ -261,16 +261,17 @@ typedef struct lbm_engine *lbm_batch;
 typedef struct lbm_engine *lbm_server;
 
 /* Launch shape of the batched interior kernel: a tile of tile_x x tile_y
- * threads (one node each; 32x4, 32x8, 32x16 or 64x4), a persistent grid of
- * blocks_per_sm blocks per SM, tiles handed out statically (dynamic = 0,
- * grid stride) or by an atomic counter (dynamic = 1). */
+ * threads (one node each; 32x4, 32x8, 32x16 or 64x4) and a schedule
+ * (`dynamic`): 0 a persistent grid of blocks_per_sm blocks per SM walking the
+ * tiles with a grid stride, 1 the same grid taking tiles from an atomic
+ * counter, 2 one block per tile. */
 typedef struct {
     int32_t tile_x, tile_y, blocks_per_sm, dynamic;
 } lbm_launch_shape;
 
 typedef struct {
     int32_t instances;
-    int32_t pad;
+    int32_t unstable;        /* instances that produced a non-finite moment */
     int64_t nodes;           /* material nodes over all instances */
     int64_t steps;           /* steps run */
     uint64_t device_bytes;   /* arena bytes in use */
@@ -295,6 +296,7 @@ lbm_status lbm_batch_set_shape(lbm_batch b, const lbm_launch_shape *shape);
 lbm_status lbm_batch_reset(lbm_batch b);
 /* Wait; LBM_ERR_UNSTABLE if any instance produced a non-finite moment. */
 lbm_status lbm_batch_sync(lbm_batch b);
+/* Statistics; waits for the batch's stream to count unstable instances. */
 lbm_status lbm_batch_info(lbm_batch b, lbm_batch_stats *stats);
 lbm_status lbm_batch_destroy(lbm_batch b);
 
@@ -321,7 +323,9 @@ lbm_status lbm_server_submit(lbm_server s, const lbm_desc *desc, int64_t nsteps,
 lbm_status lbm_server_tick(lbm_server s, int32_t max_steps, lbm_server_stats *stats);
 /* *state: 0 queued, 1 running, 2 done (fields copied to the host arrays, any
  * may be NULL, layouts of lbm_get_fields; the request is then forgotten).
- * A failed request returns LBM_ERR_ARG with its error text. */
+ * A done request whose run produced a non-finite moment still delivers its
+ * fields but returns LBM_ERR_UNSTABLE.  A failed request returns LBM_ERR_ARG
+ * with its error text. */
 lbm_status lbm_server_result(lbm_server s, int64_t id, int32_t *state, float *u, float *v,
                              float *sigma);
 lbm_status lbm_server_destroy(lbm_server s);

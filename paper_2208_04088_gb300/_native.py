@@ -72,7 +72,7 @@ class lbm_launch_shape(C.Structure):
 
 
 class lbm_batch_stats(C.Structure):
-    _fields_ = [("instances", C.c_int32), ("pad", C.c_int32), ("nodes", C.c_int64),
+    _fields_ = [("instances", C.c_int32), ("unstable", C.c_int32), ("nodes", C.c_int64),
                 ("steps", C.c_int64), ("device_bytes", C.c_uint64),
                 ("kernel_launches", C.c_int64), ("shape", lbm_launch_shape)]
 
@@ -472,13 +472,15 @@ class Server:
         v = np.empty_like(u)
         s = np.empty((3, ny, nx), np.float32)
         state = C.c_int32(0)
-        _check(load().lbm_server_result(self.h, C.c_int64(rid), C.byref(state),
-                                        C.c_void_p(u.ctypes.data), C.c_void_p(v.ctypes.data),
-                                        C.c_void_p(s.ctypes.data)))
+        st = load().lbm_server_result(self.h, C.c_int64(rid), C.byref(state),
+                                      C.c_void_p(u.ctypes.data), C.c_void_p(v.ctypes.data),
+                                      C.c_void_p(s.ctypes.data))
+        if st not in (LBM_OK, LBM_ERR_UNSTABLE):
+            _check(st)
         if state.value != self.DONE:
             return None
         del self.shapes[rid]
-        return {"u": u, "v": v, "sigma": s}
+        return {"u": u, "v": v, "sigma": s, "unstable": st == LBM_ERR_UNSTABLE}
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

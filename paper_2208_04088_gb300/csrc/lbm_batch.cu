@@ -50,27 +50,48 @@ namespace {
 
 constexpr int kChunk = 16;  // steps per replayed graph
 
+// Batched interior kernel.  The descriptor of the tile's instance is staged in
+// shared memory once per tile, so the per-node code reads its lattice
+// parameters from shared memory (as the single-solver kernel reads them from
+// the parameter bank).  Schedules: 0 persistent grid stride, 1 persistent with
+// tiles handed out by an atomic counter, 2 one tile per block.
 template <class T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) k_batch_interior(const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(TX *TY, 2048 / (TX * TY)) k_batch_interior(const InstDev *__restrict__ insts,
                                                            const int2 *__restrict__ tiles,
                                                            BatchCounts *__restrict__ counts,
-                                                           int dynamic) {
+                                                           int schedule) {
+    constexpr int kWords = (int)(sizeof(InstDev) / 4);
+    static_assert(sizeof(InstDev) % 4 == 0, "InstDev is copied as 32-bit words");
+    __shared__ __align__(16) uint32_t s_inst[kWords];
+    __shared__ int s_tile, s_local;
+    __shared__ long long s_time;
+    const int tid = threadIdx.y * TX + threadIdx.x;
     const int ntiles = counts->ntiles;
-    __shared__ int s_tile;
-    int tile;
-    if (dynamic) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) s_tile = atomicAdd(&counts->tile_counter, 1);
+    int tile = schedule == 1 ? -1 : (int)blockIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            if (schedule == 1) tile = atomicAdd(&counts->tile_counter, 1);
+            s_tile = tile;
+            if (tile < ntiles) {
+                const int2 t = tiles[tile];
+                s_local = t.y;
+                s_time = (long long)*insts[t.x].time;
+                s_inst[0] = (uint32_t)t.x;  // placeholder, overwritten below
+            }
+        }
         __syncthreads();
         tile = s_tile;
-    } else {
-        tile = blockIdx.x;
-    }
-    while (tile < ntiles) {
-        const int2 t = tiles[tile];
-        const InstDev &I = insts[t.x];
-        const int64_t time = *I.time;
+        if (tile >= ntiles) break;
+        // copy the descriptor (a few hundred bytes) with the whole block
+        const int inst = tiles[tile].x;
+        const uint32_t *src_words = reinterpret_cast<const uint32_t *>(insts + inst);
+        for (int w = tid; w < kWords; w += TX * TY) s_inst[w] = __ldg(src_words + w);
+        __syncthreads();
+        const InstDev &I = *reinterpret_cast<const InstDev *>(s_inst);
+        const int64_t time = s_time;
         if (time < I.target) {
-            const int tx = t.y % I.tiles_x, ty = t.y / I.tiles_x;
+            const int local = s_local;
+            const int tx = local % I.tiles_x, ty = local / I.tiles_x;
             const int x = tx * TX + threadIdx.x, y = ty * TY + threadIdx.y;
             if (x < I.L.nx && y < I.L.ny) {
                 const int cur = (int)(time & 1);
@@ -78,14 +99,9 @@ __global__ void __launch_bounds__(TX *TY) k_batch_interior(const InstDev *__rest
                                  I.uc, I.cls, nullptr, I.L, (int64_t)y * I.L.pitch + x, I.status);
             }
         }
-        if (dynamic) {
-            __syncthreads();
-            if (threadIdx.x == 0 && threadIdx.y == 0) s_tile = atomicAdd(&counts->tile_counter, 1);
-            __syncthreads();
-            tile = s_tile;
-        } else {
-            tile += gridDim.x;
-        }
+        if (schedule == 2) break;
+        if (schedule == 0) tile += gridDim.x;
+        __syncthreads();  // the next tile overwrites the staged descriptor
     }
 }
 
@@ -214,6 +230,7 @@ struct Request {
     std::unique_ptr<DescCopy> desc;
     int64_t steps;
     int state = 0;  // 0 queued, 1 active, 2 done, 3 failed
+    bool unstable = false;      // done, but a non-finite moment was produced
     std::vector<float> result;  // u(2N), v(2N), sigma(3N) when done
     std::string error;
 };
@@ -239,6 +256,7 @@ struct lbm_engine {
     BatchCounts *d_counts = nullptr;
     int cap_inst = 0;
     int64_t cap_tiles = 0, cap_bnodes = 0;
+    int64_t ntiles = 0;  // tiles in the current table (grid of schedule 2)
     bool tables_dirty = true;
     lbm_launch_shape shape{32, 8, 8, 0};
     int sms = 0;
@@ -311,6 +329,12 @@ lbm_status rebuild_tables(lbm_engine *E) {
     }
     lbm_status st = ensure_capacity(E, (int)hi.size(), (int64_t)tiles.size(), (int64_t)bmap.size());
     if (st != LBM_OK) return st;
+    if (E->shape.dynamic == 2 && (int64_t)tiles.size() != E->ntiles && E->graph) {
+        // one block per tile: the captured grid must match the table
+        cudaGraphExecDestroy(E->graph);
+        E->graph = nullptr;
+    }
+    E->ntiles = (int64_t)tiles.size();
     BatchCounts c;
     std::memset(&c, 0, sizeof c);
     c.ntiles = (int32_t)tiles.size();
@@ -346,9 +370,11 @@ int high_priority_value() {
 
 template <class T, int TX, int TY>
 cudaError_t launch_interior_shape(lbm_engine *E, cudaStream_t s) {
-    const dim3 blk(TX, TY), grd(E->shape.blocks_per_sm * E->sms);
-    k_batch_interior<T, TX, TY><<<grd, blk, 0, s>>>(E->d_inst, E->d_tiles, E->d_counts,
-                                                     E->shape.dynamic);
+    const int sched = E->shape.dynamic;
+    const unsigned blocks = sched == 2 ? (unsigned)std::max<int64_t>(1, E->ntiles)
+                                       : (unsigned)(E->shape.blocks_per_sm * E->sms);
+    const dim3 blk(TX, TY), grd(blocks);
+    k_batch_interior<T, TX, TY><<<grd, blk, 0, s>>>(E->d_inst, E->d_tiles, E->d_counts, sched);
     return cudaGetLastError();
 }
 
@@ -595,8 +621,9 @@ extern "C" lbm_status lbm_batch_set_shape(lbm_batch b, const lbm_launch_shape *s
                                                   shape->tile_y == 16)) ||
                          (shape->tile_x == 64 && shape->tile_y == 4);
     if (!ok_tile || shape->blocks_per_sm < 1 || shape->blocks_per_sm > 64 ||
-        (shape->dynamic != 0 && shape->dynamic != 1)) {
-        set_error("lbm_batch_set_shape: tiles 32x4, 32x8, 32x16 or 64x4; 1..64 blocks per SM");
+        shape->dynamic < 0 || shape->dynamic > 2) {
+        set_error("lbm_batch_set_shape: tiles 32x4, 32x8, 32x16 or 64x4; 1..64 blocks per SM; "
+                  "schedule 0, 1 or 2");
         return LBM_ERR_ARG;
     }
     b->shape = *shape;
@@ -643,8 +670,9 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch b, int32_t steps_per_trial,
         return LBM_ERR_ARG;
     }
     const lbm_launch_shape cands[] = {
-        {32, 8, 8, 0}, {32, 8, 8, 1}, {32, 8, 4, 0}, {32, 8, 4, 1}, {32, 4, 16, 0},
-        {32, 4, 16, 1}, {64, 4, 8, 0}, {64, 4, 8, 1}, {32, 16, 4, 0}, {32, 16, 4, 1}};
+        {32, 8, 8, 2},  {32, 4, 16, 2}, {64, 4, 8, 2},  {32, 16, 4, 2}, {32, 8, 8, 0},
+        {32, 8, 8, 1},  {32, 8, 4, 0},  {32, 4, 16, 0}, {32, 4, 16, 1}, {64, 4, 8, 0},
+        {64, 4, 8, 1},  {32, 16, 4, 0}, {32, 16, 4, 1}};
     float best = 1e30f;
     lbm_launch_shape best_shape = b->shape;
     for (const auto &c : cands) {
@@ -678,6 +706,14 @@ extern "C" lbm_status lbm_batch_info(lbm_batch b, lbm_batch_stats *stats) {
     }
     std::memset(stats, 0, sizeof *stats);
     stats->instances = (int32_t)b->inst.size();
+    for (auto &I : b->inst) {
+        const lbm_status st = lbm_sync(I.h);
+        if (st == LBM_ERR_UNSTABLE)
+            ++stats->unstable;
+        else if (st != LBM_OK)
+            return st;
+    }
+    set_error("");
     for (auto &I : b->inst) stats->nodes += I.nodes;
     stats->steps = b->step_count;
     stats->device_bytes = b->arena.used();
@@ -778,6 +814,10 @@ extern "C" lbm_status lbm_server_tick(lbm_server s, int32_t max_steps, lbm_serve
         lbm_status st = lbm_get_fields(I.h, r.result.data(), r.result.data() + 2 * N,
                                        r.result.data() + 4 * N, 0);
         if (st == LBM_OK) st = lbm_sync(I.h);
+        if (st == LBM_ERR_UNSTABLE) {
+            r.unstable = true;
+            st = LBM_OK;
+        }
         r.state = st == LBM_OK ? 2 : 3;
         if (st != LBM_OK) r.error = lbm_last_error();
         r.desc.reset();
@@ -822,7 +862,12 @@ extern "C" lbm_status lbm_server_result(lbm_server s, int64_t id, int32_t *state
     if (u) std::memcpy(u, r.result.data(), 2 * N * sizeof(float));
     if (v) std::memcpy(v, r.result.data() + 2 * N, 2 * N * sizeof(float));
     if (sigma) std::memcpy(sigma, r.result.data() + 4 * N, 3 * N * sizeof(float));
+    const bool unstable = r.unstable;
     s->requests.erase(it);
+    if (unstable) {
+        set_error("lbm_server_result: the run produced a non-finite moment (unstable)");
+        return LBM_ERR_UNSTABLE;
+    }
     return LBM_OK;
 }
 

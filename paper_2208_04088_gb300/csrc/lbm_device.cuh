@@ -169,8 +169,11 @@ __device__ __forceinline__ void integrate_u(float4 *uc, float jx, float jy, floa
     *uc = w;
 }
 
+// Raise the non-finite flag once: after the first, a plain read of the (cached)
+// status word keeps a diverged lattice from serialising on the atomic.
 __device__ __forceinline__ void flag_nonfinite(uint32_t *status, float a, float b, float c) {
-    if (!isfinite(a + b + c)) atomicOr(status, 1u);
+    if (!isfinite(a + b + c) && !(*reinterpret_cast<volatile uint32_t *>(status) & 1u))
+        atomicOr(status, 1u);
 }
 
 // Amplitude of a boundary value at (lattice) time t: step or ramp-then-hold.
