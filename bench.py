@@ -116,6 +116,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, device) -> float:
+    """Largest value over all ranks (the job takes as long as its slowest
+    replica); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -265,10 +276,7 @@ def run_batch(args):
         barrier()
     unstable = b.info()["unstable"]
     ms = start.elapsed_time(stop)
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     value = nodes * args.batch_steps * args.steps * world / (ms * 1e-3) / 1e9
     launches = b.info()["kernel_launches"]
     b.close()
@@ -440,10 +448,7 @@ def run_gpu(args):
     solver.sync()
     elapsed_ms = start.elapsed_time(stop)
     launches = solver.info()["kernel_launches"] - launches0
-    t = torch.tensor([elapsed_ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dev)
     total_lu = nodes * wl.steps * args.steps * world
     value = total_lu / (elapsed_ms * 1e-3) / 1e9
 
@@ -499,10 +504,7 @@ def run_gpu(args):
             e2e_solve()
         barrier()
         el = time.perf_counter() - t0
-        te = torch.tensor([el], device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        el = float(te.item())
+        el = max_over_ranks(el, dev)
         e2e = {"value": nodes * wl.steps * n_e2e * world / el / 1e9, "unit": "GLUPS",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(7 * 4 * wl.nx * wl.ny),
                "steps": n_e2e,

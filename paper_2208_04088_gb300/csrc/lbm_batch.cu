@@ -122,8 +122,8 @@ __global__ void __launch_bounds__(kB8) k_batch_boundary(const InstDev *__restric
         const bool live = in_list && time < I.target;
         const int cur = (int)(time & 1);
         boundary8_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]), I.uc,
-                          I.bn, I.bl, I.bcs, nullptr, I.L, m.y, live, j, (float)(time - 1),
-                          I.status);
+                          I.bn, I.bl, I.bcs, I.cls, nullptr, I.L, m.y, live, j,
+                          (float)(time - 1), I.status);
     }
 }
 

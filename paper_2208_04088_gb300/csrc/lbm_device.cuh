@@ -497,6 +497,56 @@ __device__ __forceinline__ void source_boundary(const float *__restrict__ rho, c
 }
 
 
+// Density deviation at time t of material node k: from the boundary pass for a
+// boundary node (rho holds it), the sum of the pulled populations otherwise.
+template <class T>
+__device__ __forceinline__ float node_drho(const T *__restrict__ src,
+                                           const uint8_t *__restrict__ cls,
+                                           const float *__restrict__ rho, int64_t k,
+                                           const Lattice &L) {
+    if (__ldg(cls + k) != kInterior) return rho[k];
+    float f[9];
+    pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
+    return moments(f).dr;
+}
+
+// Source S = F + (mu - lambda)/rho grad rho (Eq. sourceterm) at a boundary node,
+// one-sided where an axis neighbour is across a wall.  Lanes 0..3 of the group
+// fetch the density of the neighbour in direction j + 1; the lanes then agree
+// on the gradient through shuffles.  rho holds the boundary pass's deviations.
+template <class T>
+__device__ __forceinline__ void source_boundary8(const T *__restrict__ src,
+                                                 const uint8_t *__restrict__ cls,
+                                                 const float *__restrict__ rho, const BNode &b,
+                                                 int64_t kn, const Lattice &L, int j, float &sx,
+                                                 float &sy) {
+    const int d = j < 4 ? j + 1 : 1;  // axis direction handled by this lane
+    const bool open = !((b.cut >> d) & 1u);
+    float mine = 0.0f;
+    if (j < 4 && open) {
+        const int64_t kk = kn + (int64_t)c_cy(d) * L.pitch + c_cx(d);
+        mine = node_drho(src, cls, rho, kk, L);
+    }
+    const int base = threadIdx.x & ~7;
+    const float rxp = __shfl_sync(0xffffffffu, mine, base + 0);
+    const float ryp = __shfl_sync(0xffffffffu, mine, base + 1);
+    const float rxm = __shfl_sync(0xffffffffu, mine, base + 2);
+    const float rym = __shfl_sync(0xffffffffu, mine, base + 3);
+    const bool xp = !((b.cut >> 1) & 1u), yp = !((b.cut >> 2) & 1u);
+    const bool xm = !((b.cut >> 3) & 1u), ym = !((b.cut >> 4) & 1u);
+    const float r0 = rho[kn];
+    float gx = 0.0f, gy = 0.0f;
+    if (xp && xm) gx = 0.5f * (rxp - rxm);
+    else if (xp) gx = rxp - r0;
+    else if (xm) gx = r0 - rxm;
+    if (yp && ym) gy = 0.5f * (ryp - rym);
+    else if (yp) gy = ryp - r0;
+    else if (ym) gy = r0 - rym;
+    const float c = L.mu_m_lam / (L.rho0 + r0);
+    sx += c * gx;
+    sy += c * gy;
+}
+
 // ---------------------------------------------------------------------------
 // One interior node: pull (Eq. stream), moments with the source, collision
 // (Eq. coll), store, displacement.  Every load -- the nine pulled
@@ -533,6 +583,7 @@ __device__ __forceinline__ void boundary8_node(const T *__restrict__ src, T *__r
                                                const BNode *__restrict__ bnodes,
                                                const BLink *__restrict__ blinks,
                                                const BCDev *__restrict__ bcs,
+                                               const uint8_t *__restrict__ cls,
                                                const float *__restrict__ rho, const Lattice &L,
                                                int g, bool live, int j, float tb,
                                                uint32_t *__restrict__ status) {
@@ -543,7 +594,7 @@ __device__ __forceinline__ void boundary8_node(const T *__restrict__ src, T *__r
     const float fk = pull_boundary8(src, b, kdir, blinks + (int64_t)g * 8, bcs, tb, L, lane0, f0);
     const int64_t kn = (int64_t)b.y * L.pitch + b.x;
     float sx = L.fx, sy = L.fy;
-    if (L.grad) source_boundary(rho, b, kn, rho[kn], L, sx, sy);
+    if (L.grad) source_boundary8(src, cls, rho, b, kn, L, j, sx, sy);
     // collision on the raw moments (as collide())
     const int cx = lane_cx(kdir), cy = lane_cy(kdir);
     Raw m = grp8_raw(fk, f0, cx, cy, lane0);

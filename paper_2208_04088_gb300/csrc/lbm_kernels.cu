@@ -47,6 +47,90 @@ __global__ void __launch_bounds__(kBX *kBY) k_interior(const T *__restrict__ src
     }
 }
 
+// Interior kernel for lambda != mu: the density deviations of the tile and a
+// one-node ring around it are formed in shared memory (tile nodes from their
+// own pulled populations, ring nodes by pulling theirs, boundary nodes from the
+// boundary density pass), then the central differences of grad rho feed the
+// source of Eq. (sourceterm).  No full-lattice density pass is needed.
+template <class T>
+__global__ void __launch_bounds__(kBX *kBY) k_interior_grad(const T *__restrict__ src,
+                                                            T *__restrict__ dst,
+                                                            float4 *__restrict__ uc,
+                                                            const uint8_t *__restrict__ cls,
+                                                            const float *__restrict__ rho,
+                                                            Lattice L,
+                                                            uint32_t *__restrict__ status) {
+    __shared__ float rs[kBY + 2][kBX + 2];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
+    const int x = x0 + tx, y = y0 + ty;
+    bool live = false;
+    float f[9];
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t k = 0;
+    float own = 0.0f;
+    if (x < L.nx && y < L.ny) {
+        k = (int64_t)y * L.pitch + x;
+        const uint8_t c = __ldg(cls + k);
+        if (c == kInterior) {
+            live = true;
+            pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
+            w = uc[k];
+            own = moments(f).dr;
+        } else if (c == kBoundary) {
+            own = rho[k];
+        }
+    }
+    rs[ty + 1][tx + 1] = own;
+    // the ring: top and bottom rows (kBX + 2 each), left and right columns (kBY each)
+    const int tid = ty * kBX + tx;
+    constexpr int kRing = 2 * (kBX + 2) + 2 * kBY;
+    if (tid < kRing) {
+        int hx, hy;
+        if (tid < kBX + 2) {
+            hx = tid;
+            hy = 0;
+        } else if (tid < 2 * (kBX + 2)) {
+            hx = tid - (kBX + 2);
+            hy = kBY + 1;
+        } else if (tid < 2 * (kBX + 2) + kBY) {
+            hx = 0;
+            hy = tid - 2 * (kBX + 2) + 1;
+        } else {
+            hx = kBX + 1;
+            hy = tid - 2 * (kBX + 2) - kBY + 1;
+        }
+        const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+        float v = 0.0f;
+        if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
+            const int64_t kk = (int64_t)gy * L.pitch + gx;
+            const uint8_t c = __ldg(cls + kk);
+            if (c == kInterior) {
+                float g[9];
+                pull_interior(src, kk, L.pitch, L.plane, L.inv_scale, g);
+                v = moments(g).dr;
+            } else if (c == kBoundary) {
+                v = rho[kk];
+            }
+        }
+        rs[hy][hx] = v;
+    }
+    __syncthreads();
+    if (!live) return;
+    // interior nodes have all four axis neighbours: central differences
+    const float gxr = 0.5f * (rs[ty + 1][tx + 2] - rs[ty + 1][tx]);
+    const float gyr = 0.5f * (rs[ty + 2][tx + 1] - rs[ty][tx + 1]);
+    const float cc = L.mu_m_lam / (L.rho0 + own);
+    const float sx = L.fx + cc * gxr, sy = L.fy + cc * gyr;
+    float dr, jx, jy;
+    collide(f, sx, sy, L, dr, jx, jy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.plane + k, f[i], L.scale);
+    integrate_u_value(w, jx, jy, L.rho0 + dr);
+    uc[k] = w;
+    flag_nonfinite(status, dr, jx, jy);
+}
+
 template <class T>
 __global__ void __launch_bounds__(kBB) k_boundary(const T *__restrict__ src, T *__restrict__ dst,
                                                   float4 *__restrict__ uc,
@@ -80,6 +164,7 @@ __global__ void __launch_bounds__(kB8) k_boundary8(const T *__restrict__ src, T 
                                                    const BNode *__restrict__ bnodes,
                                                    const BLink *__restrict__ blinks,
                                                    const BCDev *__restrict__ bcs,
+                                                   const uint8_t *__restrict__ cls,
                                                    const float *__restrict__ rho, Lattice L,
                                                    const int64_t *__restrict__ time, int toff,
                                                    uint32_t *__restrict__ status) {
@@ -87,7 +172,7 @@ __global__ void __launch_bounds__(kB8) k_boundary8(const T *__restrict__ src, T 
     const float tb = (float)(*time + toff - 1);           // boundary data at the time of f^col
     // groups past the end of the list work on node 0 and store nothing
     const bool live = g < L.nb;
-    boundary8_node(src, dst, uc, bnodes, blinks, bcs, rho, L, live ? g : 0, live,
+    boundary8_node(src, dst, uc, bnodes, blinks, bcs, cls, rho, L, live ? g : 0, live,
                    threadIdx.x & 7, tb, status);
 }
 
@@ -234,13 +319,18 @@ static cudaError_t launch_boundary(const T *src, T *dst, const DevState &S, cons
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_boundary8<T>, src, dst, S.ucomp,
                               (const BNode *)S.bnodes, (const BLink *)S.blinks,
-                              (const BCDev *)S.bcs, (const float *)S.rho, L,
+                              (const BCDev *)S.bcs, (const uint8_t *)S.cls, (const float *)S.rho, L,
                               (const int64_t *)S.time, toff, S.status);
 }
 
 template <class T>
 static void launch_interior(const T *src, T *dst, const DevState &S, const Lattice &L,
                             cudaStream_t s) {
+    if (L.grad) {
+        const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
+        k_interior_grad<T><<<grd, blk, 0, s>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status);
+        return;
+    }
     // one row per thread measured fastest for every storage (2 and 4 rows cost
     // occupancy: 58+ registers)
     constexpr int NR = 1;
@@ -256,12 +346,11 @@ static cudaError_t step_t(const Lattice &L, const DevState &S, int cur, int toff
     T *dst = static_cast<T *>(S.f[cur ^ 1]);
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
     const int nbb = (L.nb + kBB - 1) / kBB;
-    if (L.grad) {
-        k_density_interior<T><<<grd, blk, 0, s_main>>>(src, S.cls, S.rho, L);
-        if (L.nb > 0)
-            k_density_boundary<T><<<nbb, kBB, 0, s_main>>>(src, S.bnodes, S.blinks, S.bcs, S.rho,
-                                                           L, S.time, toff);
-    }
+    // lambda != mu: densities of the boundary nodes first (the interior kernel
+    // forms all other densities it needs in shared memory)
+    if (L.grad && L.nb > 0)
+        k_density_boundary<T><<<nbb, kBB, 0, s_main>>>(src, S.bnodes, S.blinks, S.bcs, S.rho, L,
+                                                       S.time, toff);
     const bool split = s_side && fork && join && L.nb > 0;
     cudaStream_t s_b = split ? s_side : s_main;
     if (split) {
@@ -298,8 +387,8 @@ cudaError_t launch_step(int storage, const Lattice &L, const DevState &S, int cu
     }
 }
 
-int kernels_per_step(const Lattice &L) { return (L.grad ? (L.nb > 0 ? 2 : 1) : 0) + 1 + (L.nb > 0 ? 1 : 0); }
-int kernels_per_fields(const Lattice &L) { return kernels_per_step(L); }
+int kernels_per_step(const Lattice &L) { return (L.grad && L.nb > 0 ? 1 : 0) + 1 + (L.nb > 0 ? 1 : 0); }
+int kernels_per_fields(const Lattice &L) { return (L.grad ? (L.nb > 0 ? 2 : 1) : 0) + 1 + (L.nb > 0 ? 1 : 0); }
 
 cudaError_t launch_advance(const DevState &S, int64_t n, cudaStream_t s) {
     k_advance<<<1, 1, 0, s>>>(S.time, n);
