@@ -52,17 +52,19 @@ __global__ void __launch_bounds__(kBX *kBY) k_interior(const T *__restrict__ src
 // own pulled populations, ring nodes by pulling theirs, boundary nodes from the
 // boundary density pass), then the central differences of grad rho feed the
 // source of Eq. (sourceterm).  No full-lattice density pass is needed.
+constexpr int kGY = 8;  // rows of the lambda != mu tile (16 measured slower)
+
 template <class T>
-__global__ void __launch_bounds__(kBX *kBY) k_interior_grad(const T *__restrict__ src,
+__global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict__ src,
                                                             T *__restrict__ dst,
                                                             float4 *__restrict__ uc,
                                                             const uint8_t *__restrict__ cls,
                                                             const float *__restrict__ rho,
                                                             Lattice L,
                                                             uint32_t *__restrict__ status) {
-    __shared__ float rs[kBY + 2][kBX + 2];
+    __shared__ float rs[kGY + 2][kBX + 2];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kGY;
     const int x = x0 + tx, y = y0 + ty;
     bool live = false;
     float f[9];
@@ -82,9 +84,9 @@ __global__ void __launch_bounds__(kBX *kBY) k_interior_grad(const T *__restrict_
         }
     }
     rs[ty + 1][tx + 1] = own;
-    // the ring: top and bottom rows (kBX + 2 each), left and right columns (kBY each)
+    // the ring: top and bottom rows (kBX + 2 each), left and right columns (kGY each)
     const int tid = ty * kBX + tx;
-    constexpr int kRing = 2 * (kBX + 2) + 2 * kBY;
+    constexpr int kRing = 2 * (kBX + 2) + 2 * kGY;
     if (tid < kRing) {
         int hx, hy;
         if (tid < kBX + 2) {
@@ -92,13 +94,13 @@ __global__ void __launch_bounds__(kBX *kBY) k_interior_grad(const T *__restrict_
             hy = 0;
         } else if (tid < 2 * (kBX + 2)) {
             hx = tid - (kBX + 2);
-            hy = kBY + 1;
-        } else if (tid < 2 * (kBX + 2) + kBY) {
+            hy = kGY + 1;
+        } else if (tid < 2 * (kBX + 2) + kGY) {
             hx = 0;
             hy = tid - 2 * (kBX + 2) + 1;
         } else {
             hx = kBX + 1;
-            hy = tid - 2 * (kBX + 2) - kBY + 1;
+            hy = tid - 2 * (kBX + 2) - kGY + 1;
         }
         const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
         float v = 0.0f;
@@ -327,7 +329,7 @@ template <class T>
 static void launch_interior(const T *src, T *dst, const DevState &S, const Lattice &L,
                             cudaStream_t s) {
     if (L.grad) {
-        const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
+        const dim3 blk(kBX, kGY), grd((L.nx + kBX - 1) / kBX, (L.ny + kGY - 1) / kGY);
         k_interior_grad<T><<<grd, blk, 0, s>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status);
         return;
     }
