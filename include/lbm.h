@@ -102,11 +102,14 @@ typedef struct {
                      a corner link the signs (+-1, +-1) of the two edge normals */
 } lbm_link;
 
-/* Analytic geometry: a box, optionally with a circular hole or an edge crack.
+/* Analytic geometry: a box, optionally with a circular hole or a crack.
  * Box edges cut links at mid-link.  A node is void iff strictly inside the
  * hole; a link is cut by the hole iff its end node is void, with q the first
- * crossing of the circle.  The edge crack runs from the left edge along
- * y = ny/2 - 1/2 (ny even) to its tip at x = crack_len - 1/2. */
+ * crossing of the circle.  The crack lies on y = ny/2 - 1/2 (ny even): with
+ * crack_x0 = 0 it runs from the left edge to its tip at x = crack_len - 1/2
+ * (an edge crack, Sec. 5.2 in half-plane form); with crack_x0 > 0 it lies
+ * between the tips crack_x0 - 1/2 and crack_x0 + crack_len - 1/2 (the centre
+ * crack of Sec. 5.2).  Links crossing exactly at a tip are not cut. */
 typedef struct {
     int32_t nx, ny;
     int32_t edge_bc[4]; /* bc index of the left, right, bottom, top edge */
@@ -114,7 +117,7 @@ typedef struct {
     int32_t hole_bc;
     int32_t crack_len; /* <= 0: no crack */
     int32_t crack_bc;  /* both crack faces */
-    int32_t reserved;  /* must be 0 */
+    int32_t crack_x0;  /* first column of the crack (>= 0) */
 } lbm_geom;
 
 /* Problem description.  Physical units: the lattice spacing dx and the time

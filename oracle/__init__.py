@@ -80,7 +80,7 @@ def _load():
     lib.ora_feq.restype = None
     lib.ora_collide.argtypes = [dp, d, d, d, dp, dp]
     lib.ora_collide.restype = None
-    lib.ora_geometry.argtypes = [i32, i32, C.POINTER(i32), d, d, d, i32, i32, i32,
+    lib.ora_geometry.argtypes = [i32, i32, C.POINTER(i32), d, d, d, i32, i32, i32, i32,
                                  C.POINTER(C.c_uint8), C.POINTER(Link), i64]
     lib.ora_geometry.restype = i64
     lib.ora_create.argtypes = [i32, i32, d, d, d, d, d, d, i32, i32,
@@ -142,18 +142,19 @@ def geometry(nx, ny, edge_bc=(0, 0, 0, 0), hole=None, crack=None):
     edge_bc: boundary-condition index of the (left, right, bottom, top) edge;
              -1 on both sides of an axis makes that axis periodic.
     hole:    (cx, cy, R, bc) or None.
-    crack:   (length, bc) or None -- edge crack from the left edge along
-             y = ny/2 - 1/2.
+    crack:   (length, bc) or (length, bc, x0) or None -- a crack along
+             y = ny/2 - 1/2: from the left edge (x0 = 0, the default) or
+             between the tips x0 - 1/2 and x0 + length - 1/2.
     Returns (node_type uint8 [ny, nx], links structured array, canonical order:
     node row-major, then direction 1..8).
     """
     lib = _load()
     eb = (C.c_int32 * 4)(*[int(v) for v in edge_bc])
     hx, hy, hr, hb = hole if hole is not None else (0.0, 0.0, 0.0, -1)
-    cl, cb = crack if crack is not None else (0, -1)
+    cl, cb, cx0 = (tuple(crack) + (0,))[:3] if crack is not None else (0, -1, 0)
     nt = np.zeros(nx * ny, dtype=np.uint8)
     args = (int(nx), int(ny), eb, float(hx), float(hy), float(hr), int(hb), int(cl), int(cb),
-            nt.ctypes.data_as(C.POINTER(C.c_uint8)))
+            int(cx0), nt.ctypes.data_as(C.POINTER(C.c_uint8)))
     n = lib.ora_geometry(*args, None, 0)
     if n < 0:
         raise ValueError(f"ora_geometry rejected the arguments (status {n})")

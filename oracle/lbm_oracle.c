@@ -47,7 +47,8 @@
  *     [-1/2, ny-1/2]; a node is void iff strictly inside the hole circle; a
  *     link is cut by the hole iff its end node is void, with s/l the smaller
  *     root of |x + q c_i - centre| = R; the edge crack lies on
- *     y = ny/2 - 1/2 for x < crack_len - 1/2.
+ *     y = ny/2 - 1/2 for x < crack_len - 1/2 (edge crack), or between the tips
+ *     crack_x0 - 1/2 and crack_x0 + crack_len - 1/2 (crack_x0 > 0).
  *
  * Parity: pinned by tests/test_oracle_*.py (moment identities, conservation,
  * wave speeds, exact uniform states, 1-D impact closed forms, hand-derived
@@ -168,12 +169,13 @@ void ora_collide(const double *f, double Sx, double Sy, double tau, double *fcol
  * small (links may be NULL to count only), or -2 on a bad argument. */
 int64_t ora_geometry(int32_t nx, int32_t ny, const int32_t *edge_bc, double hole_cx,
                      double hole_cy, double hole_r, int32_t hole_bc, int32_t crack_len,
-                     int32_t crack_bc, uint8_t *node_type, ora_link *links, int64_t cap) {
+                     int32_t crack_bc, int32_t crack_x0, uint8_t *node_type, ora_link *links,
+                     int64_t cap) {
     if (nx < 1 || ny < 1) return -2;
     const int per_x = (edge_bc[0] < 0), per_y = (edge_bc[2] < 0);
     if (per_x != (edge_bc[1] < 0) || per_y != (edge_bc[3] < 0)) return -2;
     const int has_hole = hole_r > 0.0, has_crack = crack_len > 0;
-    if (has_crack && (ny % 2 != 0 || per_y)) return -2;
+    if (has_crack && (ny % 2 != 0 || per_y || crack_x0 < 0)) return -2;
     const double ycrack = 0.5 * ny - 0.5; /* crack plane y* */
 
     /* material iff outside the hole circle */
@@ -197,12 +199,16 @@ int64_t ora_geometry(int32_t nx, int32_t ny, const int32_t *edge_bc, double hole
                 const int out_y = !per_y && (ty < 0 || ty >= ny);
                 /* a link crossing y* between rows ny/2-1 and ny/2 at abscissa
                  * x + c_ix/2 is cut by the crack iff that abscissa lies on the
-                 * crack, i.e. left of the tip at crack_len - 1/2 */
+                 * crack: left of the tip at crack_x0 + crack_len - 1/2 and, for
+                 * a crack away from the left edge (crack_x0 > 0), right of its
+                 * other tip at crack_x0 - 1/2; crossings at a tip are not cut */
                 int on_crack = 0;
                 if (has_crack && CY[i] != 0) {
                     const double ymid = y + 0.5 * CY[i];
                     const double xmid = x + 0.5 * CX[i];
-                    if (ymid == ycrack && xmid < crack_len - 0.5) on_crack = 1;
+                    const int right_of_start = (crack_x0 == 0) || (xmid > crack_x0 - 0.5);
+                    if (ymid == ycrack && right_of_start && xmid < crack_x0 + crack_len - 0.5)
+                        on_crack = 1;
                 }
                 ora_link L;
                 memset(&L, 0, sizeof L);

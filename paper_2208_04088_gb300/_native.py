@@ -46,7 +46,7 @@ class lbm_geom(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("edge_bc", C.c_int32 * 4),
                 ("hole_cx", C.c_double), ("hole_cy", C.c_double), ("hole_r", C.c_double),
                 ("hole_bc", C.c_int32), ("crack_len", C.c_int32), ("crack_bc", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("crack_x0", C.c_int32)]
 
 
 class lbm_desc(C.Structure):
@@ -184,6 +184,7 @@ def lbm_geom_build(nx, ny, edge_bc=(0, 0, 0, 0), hole=None, crack=None):
         g.hole_cx, g.hole_cy, g.hole_r, g.hole_bc = float(hole[0]), float(hole[1]), float(hole[2]), int(hole[3])
     if crack is not None:
         g.crack_len, g.crack_bc = int(crack[0]), int(crack[1])
+        g.crack_x0 = int(crack[2]) if len(crack) > 2 else 0
     nt = np.zeros(int(nx) * int(ny), dtype=np.uint8)
     n = C.c_int64(0)
     ntp = nt.ctypes.data_as(C.POINTER(C.c_uint8))

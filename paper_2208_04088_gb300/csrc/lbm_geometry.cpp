@@ -64,8 +64,8 @@ static lbm_status build_geometry(const lbm_geom &g, uint8_t *node_type, std::vec
         set_error("lbm_geom_build: an edge crack needs an even ny");
         return LBM_ERR_ARG;
     }
-    if (g.reserved != 0) {
-        set_error("lbm_geom_build: reserved must be 0");
+    if (g.crack_x0 < 0) {
+        set_error("lbm_geom_build: crack_x0 must be >= 0");
         return LBM_ERR_ARG;
     }
     if (hole && !(is_finite(g.hole_cx) && is_finite(g.hole_cy) && is_finite(g.hole_r))) {
@@ -91,8 +91,12 @@ static lbm_status build_geometry(const lbm_geom &g, uint8_t *node_type, std::vec
         if (!crack || kCy[i] == 0) return false;
         const int32_t ty = y + kCy[i];
         if (!((y == yb && ty == yb + 1) || (y == yb + 1 && ty == yb))) return false;
-        // abscissa of the crossing is x + c_x/2 < crack_len - 1/2  <=>  2x + c_x < 2 crack_len - 1
-        return 2 * x + kCx[i] < 2 * g.crack_len - 1;
+        // abscissa of the crossing, doubled: 2x + c_x; the crack spans
+        // (2 crack_x0 - 1, 2 (crack_x0 + crack_len) - 1), open at both tips,
+        // and reaches the left edge when crack_x0 = 0
+        const int32_t xm2 = 2 * x + kCx[i];
+        const bool right_of_start = g.crack_x0 == 0 || xm2 > 2 * g.crack_x0 - 1;
+        return right_of_start && xm2 < 2 * (g.crack_x0 + g.crack_len) - 1;
     };
 
     // (1) box edges and crack faces: walls at mid-link
@@ -149,7 +153,8 @@ static lbm_status build_geometry(const lbm_geom &g, uint8_t *node_type, std::vec
     if (crack)
         for (int32_t y : {yb, yb + 1})
             if (y > 0 && y < ny - 1)  // rows 0 and ny-1 were visited with the box
-                for (int32_t x = 1; x < std::min(nx - 1, g.crack_len + 1); ++x)
+                for (int32_t x = std::max(1, g.crack_x0 - 1);
+                     x < std::min(nx - 1, g.crack_x0 + g.crack_len + 1); ++x)
                     for (int i = 1; i < kQ; ++i) add_midlink(x, y, i);
 
     // (2) hole rim: links from a material node to a void node

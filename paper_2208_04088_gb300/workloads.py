@@ -40,7 +40,7 @@ class Workload:
     lam_over_mu: float = 1.0  # 1.0 is the Poisson solid, nu = 1/4
     edge_bc: Tuple[int, int, int, int] = (0, 0, 0, 0)
     hole: Optional[Tuple[float, float, float, int]] = None  # (cx, cy, R, bc)
-    crack: Optional[Tuple[int, int]] = None  # (length, bc)
+    crack: Optional[Tuple[int, ...]] = None  # (length, bc[, first column]); edge crack if 0
     bcs: List[dict] = dataclasses.field(default_factory=list)
     tau: float = TAU
     # Neumann wall values at the boundary node instead of the extrapolation of
@@ -116,6 +116,19 @@ def edge_crack(n: int = 2048, length: int = 512, steps: int = 1500, sigma0: floa
     return Workload(
         name=f"edge_crack_{n}x{ny}_L{length}", nx=n, ny=ny, steps=steps,
         lam_over_mu=lam_over_mu, edge_bc=(0, 0, 0, 0), crack=(int(length), 1),
+        bcs=[bc(TRACTION, (0.0, 0.0)), bc(PRESSURE, (sigma0,))])
+
+
+def centre_crack(length: int = 100, steps: int = 210, sigma0: float = 1e-3,
+                 lam_over_mu: float = 1.0, side: Optional[int] = None) -> Workload:
+    """The centre crack of Sec. 5.2: a crack of the given length in the middle
+    of a square plate of side 4 x length (the paper: 400 x 400 nodes, crack
+    length 100), faces under a step pressure sigma0, outer edges traction-free."""
+    side = 4 * length if side is None else side
+    x0 = (side - length) // 2
+    return Workload(
+        name=f"centre_crack_{side}x{side}_L{length}", nx=side, ny=side, steps=steps,
+        lam_over_mu=lam_over_mu, edge_bc=(0, 0, 0, 0), crack=(int(length), 1, int(x0)),
         bcs=[bc(TRACTION, (0.0, 0.0)), bc(PRESSURE, (sigma0,))])
 
 

@@ -34,7 +34,8 @@ def test_library_exports_every_declared_symbol():
 
 @pytest.mark.parametrize("wl", [W.square_plate(64, 0), W.hole_plate(256, 128, 16.0, 0),
                                 W.hole_plate(1024, 512, 64.0, 0), W.hole_plate(101, 77, 12.5, 0),
-                                W.edge_crack(128, 40, 0), W.edge_crack(64, 64, 0, ny=32)],
+                                W.edge_crack(128, 40, 0), W.edge_crack(64, 64, 0, ny=32),
+                                W.centre_crack(25, 0), W.centre_crack(100, 0)],
                          ids=lambda w: w.name)
 def test_geometry_tables_bit_exact_with_oracle(oracle_mod, wl):
     nt_o, lk_o = oracle_mod.geometry(**wl.geometry_args())

@@ -187,3 +187,9 @@ def test_unstable_run_is_reported_not_hidden():
         s.step(1)
     assert e.value.status == N.LBM_ERR_UNSTABLE
     s.close()
+
+
+def test_centre_crack_non_poisson(oracle_mod):
+    """The centre crack of Sec. 5.2 (both tips inside the plate), nu = 0.2174."""
+    wl = W.centre_crack(50, 150, lam_over_mu=W.CRACK_PAPER_LAM_OVER_MU)
+    _assert_parity(run_gpu(wl, wl.steps), run_oracle(oracle_mod, wl, wl.steps))

@@ -102,3 +102,25 @@ def test_rejects_bad_arguments(oracle_mod):
         oracle_mod.geometry(10, 9, crack=(3, 0))      # odd ny has no mid-row plane
     with pytest.raises(ValueError):
         oracle_mod.geometry(10, 10, edge_bc=(-1, 0, 0, 0))   # half-periodic axis
+
+
+def test_centre_crack_links(oracle_mod):
+    nx, ny, Lc, x0 = 40, 20, 11, 14
+    nt, links = oracle_mod.geometry(nx, ny, edge_bc=(0, 0, 0, 0), crack=(Lc, 1, x0))
+    crack = links[(links["bc"] == 1) | (links["bc2"] == 1)]
+    ys = 0.5 * ny - 0.5
+    expect = set()
+    for y in (ny // 2 - 1, ny // 2):
+        for x in range(nx):
+            for i in range(1, 9):
+                if C[i, 1] == 0:
+                    continue
+                xm = x + 0.5 * C[i, 0]
+                if y + 0.5 * C[i, 1] == ys and x0 - 0.5 < xm < x0 + Lc - 0.5:
+                    expect.add((y * nx + x, i))
+    assert set(zip(crack["node"].tolist(), crack["dir"].tolist())) == expect
+    assert np.all(crack["bc2"] == -1)   # no corner: the crack is away from the edges
+    # both tips: diagonal links crossing exactly at x0 - 1/2 and x0 + Lc - 1/2 stay uncut
+    below = (ny // 2 - 1) * nx
+    assert not np.any((crack["node"] == below + x0 - 1) & (crack["dir"] == 5))
+    assert not np.any((crack["node"] == below + x0 + Lc - 1) & (crack["dir"] == 5))
