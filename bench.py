@@ -198,12 +198,15 @@ def _traffic(wl, storage):
     if the kernels have changed since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2208_04088_gb300", "csrc", "lbm_kernels.cu")
+    csrc = os.path.join(ROOT, "paper_2208_04088_gb300", "csrc")
     try:
         with open(path) as f:
             t = json.load(f)
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for name in ("lbm_kernels.cu", "lbm_device.cuh"):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+        sha = h.hexdigest()[:16]
         if sha != t.get("kernels_sha256_16"):
             return None
         e = t[wl.name][storage]
