@@ -223,9 +223,11 @@ def run_profile(args):
     torch.cuda.set_device(0)
     wl = _workload(args.workload)
     s = N.Solver(N.desc_from_workload(wl, storage=args.storage,
-                                      wall_node=args.wall_values == "node"))
-    for _ in range(args.profile):
-        s.step(1)
+                                      wall_node=args.wall_values == "node",
+                                      time_block=args.time_block))
+    per = s.info()["time_block"]  # steps of one direct launch
+    for _ in range(max(1, args.profile // per)):
+        s.step(per)
     s.sync()
     s.close()
     print(json.dumps({"profile_steps": args.profile, "workload": wl.name,
@@ -412,7 +414,8 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
 
     wall_node = args.wall_values == "node"
-    desc = N.desc_from_workload(wl, storage=args.storage, wall_node=wall_node)
+    desc = N.desc_from_workload(wl, storage=args.storage, wall_node=wall_node,
+                                time_block=args.time_block)
     nodes = int(desc.node_type.sum())
     solver = N.Solver(desc, stream=stream, device=dev)
     info0 = solver.info()
@@ -489,7 +492,8 @@ def run_gpu(args):
 
         def e2e_solve():
             nonlocal h2d
-            d = N.desc_from_workload(wl, storage=args.storage, wall_node=wall_node)
+            d = N.desc_from_workload(wl, storage=args.storage, wall_node=wall_node,
+                                     time_block=args.time_block)
             h = N.lbm_create(d, stream.cuda_stream, 0, 0)
             inf = N.lbm_get_info(h)
             h2d = (inf["pitch"] * wl.ny + 16 * inf["boundary_nodes"] +
@@ -585,6 +589,9 @@ def main():
     ap.add_argument("--max-steps", type=int, default=50000)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--tick-steps", type=int, default=256)
+    ap.add_argument("--time-block", type=int, default=0,
+                    help="steps per launch: 0 library default, 1 one-step kernels, "
+                         "8 temporally blocked kernel")
     ap.add_argument("--profile", type=int, default=0,
                     help="run this many direct-launch steps of the workload and exit (for ncu)")
     ap.add_argument("--traffic", type=float, default=None,

@@ -138,8 +138,19 @@ typedef struct {
     int32_t nbcs;      /* 1..65535 */
     int32_t storage;   /* lbm_storage */
     int32_t wall_values; /* lbm_wall_values */
-    int32_t reserved;    /* must be 0 */
+    int32_t time_block;  /* time steps fused into one kernel launch:
+                            0  library default (one launch per step)
+                            1  one launch per step (bulk and boundary-list kernels)
+                            LBM_TIME_BLOCK  temporal blocking: each launch carries
+                               LBM_TIME_BLOCK steps of a strip of the lattice in
+                               shared memory, so the populations cross HBM once per
+                               LBM_TIME_BLOCK steps; needs FP32 storage, lambda = mu
+                               and nx >= 128 (LBM_ERR_ARG otherwise).  Every stored
+                               value is bit-identical to time_block = 1. */
 } lbm_desc;
+
+/* Steps per launch of the temporally blocked kernel (lbm_desc.time_block). */
+#define LBM_TIME_BLOCK 8
 
 /* Read-only information about a handle. */
 typedef struct {
@@ -151,12 +162,16 @@ typedef struct {
     float storage_scale;    /* power-of-two scale of the 16-bit forms, 1 for FP32 */
     float bytes_per_update; /* algorithmic HBM bytes per interior lattice update */
     int64_t kernel_launches; /* kernels this handle has launched so far */
+    int32_t time_block;      /* steps per launch in use (1 or LBM_TIME_BLOCK) */
+    int32_t reserved;        /* 0 */
 } lbm_info;
 
 /* Accumulated kernel times of timing mode (see lbm_set_timing). */
 typedef struct {
-    double interior_ms; /* sum over steps of the interior (bulk) kernel */
-    double boundary_ms; /* sum over steps of the boundary-list kernel */
+    double interior_ms; /* sum over launches of the interior (bulk) kernel, or of
+                           the temporally blocked kernel (boundary nodes included) */
+    double boundary_ms; /* sum over steps of the boundary-list kernel (0 for
+                           temporally blocked launches) */
     int64_t steps;      /* steps timed */
 } lbm_timing;
 
@@ -240,7 +255,8 @@ lbm_status lbm_get_info(lbm_handle h, lbm_info *info);
 /* Timing mode for profiling.  While enabled, lbm_step launches the kernels of
  * each step directly (no graphs; the boundary kernel on a private stream beside
  * the interior kernel, joined before the next step, as inside the graphs) and
- * records CUDA events around both on their streams.
+ * records CUDA events around both on their streams; with temporal blocking each
+ * launch of LBM_TIME_BLOCK steps is bracketed as one interior kernel.
  * lbm_get_timing synchronises, returns the accumulated times and clears them. */
 lbm_status lbm_set_timing(lbm_handle h, int32_t enable);
 lbm_status lbm_get_timing(lbm_handle h, lbm_timing *out);

@@ -490,8 +490,17 @@ lbm_status engine_init(lbm_engine *E, int storage, void *stream) {
     return LBM_OK;
 }
 
+// The batched kernels step every instance one step per launch, so instances
+// are created without the tables of the temporally blocked kernel.
+lbm_desc one_step(const lbm_desc &d) {
+    lbm_desc o = d;
+    o.time_block = 1;
+    return o;
+}
+
 // Admit one instance into the arena; LBM_ERR_NOMEM if it does not fit now.
-lbm_status admit(lbm_engine *E, const lbm_desc &d, int64_t id, int64_t steps) {
+lbm_status admit(lbm_engine *E, const lbm_desc &d_in, int64_t id, int64_t steps) {
+    const lbm_desc d = one_step(d_in);
     uint64_t bytes = 0;
     lbm_status st = lbm_workspace_size(&d, &bytes);
     if (st != LBM_OK) return st;
@@ -576,7 +585,8 @@ extern "C" lbm_status lbm_batch_create(const lbm_desc *descs, int32_t count, voi
     uint64_t total = 0;
     for (int32_t i = 0; i < count; ++i) {
         uint64_t b = 0;
-        st = lbm_workspace_size(&descs[i], &b);
+        const lbm_desc di = one_step(descs[i]);
+        st = lbm_workspace_size(&di, &b);
         if (st != LBM_OK) return st;
         total += (b + 255) / 256 * 256;
     }
@@ -756,7 +766,8 @@ extern "C" lbm_status lbm_server_submit(lbm_server s, const lbm_desc *desc, int6
     }
     // validate now, so a bad request fails at submission
     uint64_t bytes = 0;
-    lbm_status st = lbm_workspace_size(desc, &bytes);
+    const lbm_desc d1 = one_step(*desc);
+    lbm_status st = lbm_workspace_size(&d1, &bytes);
     if (st != LBM_OK) return st;
     if (bytes > s->arena.capacity()) {
         set_error("lbm_server_submit: the request alone exceeds the device budget");

@@ -26,10 +26,20 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct Layout {
     size_t f0, f1, ucomp, cls, bnodes, blinks, bcs, rho, status, time, stage, probe, probe_idx,
-        total;
+        nw, total;
 };
 
-Layout layout(const Tables &t, int storage, bool grad) {
+// Steps per launch for a description: the temporally blocked kernel needs FP32
+// storage, lambda = mu and a lattice at least one strip wide.  Returns 0 if
+// the description asks for blocking that this lattice cannot have.
+int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
+    const bool ok = d.storage == LBM_F32 && u.lam == u.mu && t.nx >= kWaveC &&
+                    t.bnodes.size() < (size_t(1) << 28);
+    if (d.time_block == LBM_TIME_BLOCK) return ok ? kWaveK : 0;
+    return 1;  // the library default: one step per launch
+}
+
+Layout layout(const Tables &t, int storage, bool grad, int block) {
     const size_t plane = (size_t)t.pitch * t.ny;
     const size_t esz = storage == LBM_F32 ? 4 : 2;
     const size_t N = (size_t)t.nx * t.ny;
@@ -53,8 +63,8 @@ Layout layout(const Tables &t, int storage, bool grad) {
     l.stage = take(7 * N * sizeof(float));
     l.probe = take(7 * (size_t)kMaxProbe * sizeof(float));
     l.probe_idx = take((size_t)kMaxProbe * sizeof(int32_t));
+    l.nw = block > 1 ? take(plane * sizeof(uint64_t)) : 0;
     l.total = o;
-    (void)grad;
     return l;
 }
 
@@ -110,16 +120,26 @@ void destroy_graphs(lbm_solver *h) {
         }
 }
 
-// Capture kGraphChunk steps starting in buffer `start`, with the boundary
-// kernel on a side branch that runs beside the interior kernel.
+// Capture kGraphChunk steps starting in buffer `start`: one-step launches
+// with the boundary kernel on a side branch beside the interior kernel, or
+// kGraphChunk / kWaveK temporally blocked launches (an even number, so the
+// chunk ends in the buffer it started from either way).
+static_assert(kGraphChunk % (2 * kWaveK) == 0, "graph chunk and time block");
+
 lbm_status build_graph(lbm_solver *h, int start) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->cap_main, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "lbm_step: begin capture");
     int cur = start;
-    for (int s = 0; s < kGraphChunk && e == cudaSuccess; ++s) {
-        e = launch_step(h->storage, h->L, h->S, cur, s, h->cap_main, h->cap_side, h->gfork,
-                        h->gjoin, nullptr);
+    for (int s = 0; s < kGraphChunk && e == cudaSuccess;) {
+        if (h->block > 1) {
+            e = launch_wave(h->L, h->S, h->wave, cur, s, h->cap_main);
+            s += h->block;
+        } else {
+            e = launch_step(h->storage, h->L, h->S, cur, s, h->cap_main, h->cap_side, h->gfork,
+                            h->gjoin, nullptr);
+            s += 1;
+        }
         cur ^= 1;
     }
     if (e == cudaSuccess) e = launch_advance(h->S, kGraphChunk, h->cap_main);
@@ -146,7 +166,12 @@ extern "C" lbm_status lbm_workspace_size(const lbm_desc *desc, uint64_t *bytes) 
     Units u;
     lbm_status st = prepare(desc, &t, &u);
     if (st != LBM_OK) return st;
-    *bytes = layout(t, desc->storage, u.lam != u.mu).total;
+    const int block = steps_per_launch(*desc, t, u);
+    if (block == 0) {
+        set_error("lbm_workspace_size: time_block = LBM_TIME_BLOCK needs FP32 storage, lambda = mu and nx >= 128");
+        return LBM_ERR_ARG;
+    }
+    *bytes = layout(t, desc->storage, u.lam != u.mu, block).total;
     return LBM_OK;
 }
 
@@ -168,7 +193,13 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
     h->stream = static_cast<cudaStream_t>(stream);
     h->L = make_lattice(h->tab, h->units, h->storage);
     h->L.wall_node = desc->wall_values == LBM_WALL_NODE ? 1 : 0;
-    const Layout lay = layout(h->tab, h->storage, h->L.grad != 0);
+    h->block = steps_per_launch(*desc, h->tab, h->units);
+    if (h->block == 0) {
+        set_error("lbm_create: time_block = LBM_TIME_BLOCK needs FP32 storage, lambda = mu and nx >= 128");
+        delete h;
+        return LBM_ERR_ARG;
+    }
+    const Layout lay = layout(h->tab, h->storage, h->L.grad != 0, h->block);
     h->bytes = lay.total;
     cudaError_t e = cudaSuccess;
     if (workspace) {
@@ -215,6 +246,7 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
     S.stage = reinterpret_cast<float *>(b + lay.stage);
     S.probe = reinterpret_cast<float *>(b + lay.probe);
     S.probe_idx = reinterpret_cast<int32_t *>(b + lay.probe_idx);
+    S.nw = h->block > 1 ? reinterpret_cast<uint64_t *>(b + lay.nw) : nullptr;
 
     auto fail = [&](cudaError_t err, const char *where) {
         lbm_status s = cuda_fail(err, where);
@@ -233,6 +265,18 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
         e = cudaMemcpyAsync(S.bcs, t.bcs.data(), t.bcs.size() * sizeof(BCDev),
                             cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = launch_reset(h->storage, h->L, S, h->stream);
+    if (e == cudaSuccess && h->block > 1) {
+        if (!wave_supported(h->L)) {
+            if (desc->time_block == LBM_TIME_BLOCK) {
+                set_error("lbm_create: the temporally blocked kernel is unavailable (tensor-map encoder)");
+                lbm_destroy(h);
+                return LBM_ERR_ARG;
+            }
+            h->block = 1;  // default: fall back to one step per launch
+        } else {
+            e = wave_prepare(h->L, S, &h->wave, h->stream);
+        }
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail(e, "lbm_create: upload");
     e = cudaStreamCreateWithFlags(&h->cap_main, cudaStreamNonBlocking);
@@ -262,6 +306,10 @@ extern "C" lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
         const cudaError_t q = cudaEventQuery(h->status_ready);
         if (q == cudaSuccess) {
             h->status_pending = false;
+            if (*h->h_status & 2u) {
+                set_error("lbm_step: a bounded wait for a tile copy expired on the device");
+                return LBM_ERR_TIMEOUT;
+            }
             if (*h->h_status & 1u) {
                 set_error("lbm_step: a non-finite moment was produced (unstable run)");
                 return LBM_ERR_UNSTABLE;
@@ -287,12 +335,26 @@ extern "C" lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
                 if (e != cudaSuccess) return cuda_fail(e, "lbm_step: timing events");
                 h->ev_pool.push_back(ev);
             }
-            e = launch_step(h->storage, h->L, h->S, h->cur, (int)s, h->stream, h->cap_side,
-                            h->fork, h->join, &h->ev_pool[h->ev_used++]);
+            StepEvents &ev = h->ev_pool[h->ev_used++];
+            ev.nsteps = 1;
+            if (h->block > 1 && nsteps - s >= h->block) {
+                ev.nsteps = h->block;
+                // one blocked launch as the bulk kernel; the boundary nodes are inside it
+                e = cudaEventRecord(ev.before_interior, h->stream);
+                if (e == cudaSuccess) e = launch_wave(h->L, h->S, h->wave, h->cur, (int)s, h->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(ev.after_interior, h->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(ev.before_boundary, h->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(ev.after_boundary, h->stream);
+                s += h->block - 1;
+                h->launches += 1;
+            } else {
+                e = launch_step(h->storage, h->L, h->S, h->cur, (int)s, h->stream, h->cap_side,
+                                h->fork, h->join, &ev);
+                h->launches += per_step;
+            }
             if (e != cudaSuccess) return cuda_fail(e, "lbm_step: launch");
             h->cur ^= 1;
         }
-        h->launches += nsteps * per_step;
         done = nsteps;
     }
     if (nsteps - done >= kGraphChunk) {
@@ -304,17 +366,24 @@ extern "C" lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
             }
             e = cudaGraphLaunch(h->graph[h->cur], h->stream);
             if (e != cudaSuccess) return cuda_fail(e, "lbm_step: graph launch");
-            h->launches += kGraphChunk * per_step + 1;
+            h->launches += (h->block > 1 ? kGraphChunk / h->block : kGraphChunk * per_step) + 1;
         }
     }
     const int64_t rest = nsteps - done;
-    for (int64_t s = 0; s < rest; ++s) {
-        e = launch_step(h->storage, h->L, h->S, h->cur, (int)s, h->stream, nullptr, nullptr,
-                        nullptr, nullptr);
+    for (int64_t s = 0; s < rest;) {
+        if (h->block > 1 && rest - s >= h->block) {
+            e = launch_wave(h->L, h->S, h->wave, h->cur, (int)s, h->stream);
+            s += h->block;
+            h->launches += 1;
+        } else {
+            e = launch_step(h->storage, h->L, h->S, h->cur, (int)s, h->stream, nullptr, nullptr,
+                            nullptr, nullptr);
+            s += 1;
+            h->launches += per_step;
+        }
         if (e != cudaSuccess) return cuda_fail(e, "lbm_step: launch");
         h->cur ^= 1;
     }
-    h->launches += rest * per_step;
     const int64_t direct = rest + (h->timing ? nsteps : 0);
     if (direct > 0) {
         e = launch_advance(h->S, direct, h->stream);
@@ -433,6 +502,10 @@ extern "C" lbm_status lbm_sync(lbm_handle h) {
                                     h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "lbm_sync");
+    if (status & 2u) {
+        set_error("lbm_sync: a bounded wait for a tile copy expired on the device");
+        return LBM_ERR_TIMEOUT;
+    }
     if (status & 1u) {
         set_error("lbm_sync: a non-finite moment was produced (unstable run)");
         return LBM_ERR_UNSTABLE;
@@ -458,6 +531,8 @@ extern "C" lbm_status lbm_get_info(lbm_handle h, lbm_info *info) {
     const float esz = h->storage == LBM_F32 ? 4.0f : 2.0f;
     info->bytes_per_update = 2.0f * 9.0f * esz + 32.0f;  // f read + write, u and compensation R+W
     info->kernel_launches = h->launches;
+    info->time_block = h->block;
+    info->reserved = 0;
     return LBM_OK;
 }
 
@@ -488,8 +563,8 @@ extern "C" lbm_status lbm_get_timing(lbm_handle h, lbm_timing *out) {
         if (e != cudaSuccess) return cuda_fail(e, "lbm_get_timing: elapsed");
         out->interior_ms += a;
         out->boundary_ms += b;
+        out->steps += h->ev_pool[k].nsteps;
     }
-    out->steps = (int64_t)h->ev_used;
     h->ev_used = 0;
     return LBM_OK;
 }

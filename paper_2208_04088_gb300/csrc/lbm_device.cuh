@@ -61,6 +61,17 @@ static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2 && opp(5)
               "opposite directions");
 
 // ---------------------------------------------------------------------------
+// Explicitly rounded arithmetic.  The relaxation, the displacement update and
+// the boundary rules are written with it (products, sums and fused
+// multiply-adds in a fixed order), so every kernel that evaluates them -- the
+// one-step kernels, the batched kernels and the temporally blocked kernel --
+// rounds identically, whatever the compiler would fuse in each context.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// ---------------------------------------------------------------------------
 // Raw moments m_pq = sum_i f_i c_ix^p c_iy^q (p, q in 0..2) of the nine
 // populations.  D2Q9 is the tensor product of {-1, 0, 1} in x and y, so the
 // transform is two passes of the 1-D map (a-, a0, a+) -> (a- + a0 + a+,
@@ -124,48 +135,49 @@ __device__ __forceinline__ Mom moments(const float f[9]) {
 // moments.  rho and P pass through untouched and j gains exactly S, so the
 // collision invariants are not disturbed by the rounding of 1/3 and 1/9.
 // On return f holds f^col, jx/jy the momentum j = m + S/2, dr the density deviation.
+// The relaxation of Eq. (coll) on the raw moments (see collide); returns the
+// momentum j = m + S/2 in jx, jy.
+__device__ __forceinline__ void relax_raw(Raw &m, float sx, float sy, const Lattice &L, float &jx,
+                                          float &jy) {
+    jx = rfma(0.5f, sx, m.m10);
+    jy = rfma(0.5f, sy, m.m01);
+    const float w = L.omega;
+    const float s3 = rmul(L.src, 1.0f / 3.0f);
+    m.m10 = radd(m.m10, sx);
+    m.m01 = radd(m.m01, sy);
+    m.m21 = radd(m.m21, rfma(s3, sy, rmul(w, rfma(jy, 1.0f / 3.0f, -m.m21))));
+    m.m12 = radd(m.m12, rfma(s3, sx, rmul(w, rfma(jx, 1.0f / 3.0f, -m.m12))));
+    const float e = rfma(-m.m00, 1.0f / 9.0f, rmul(radd(m.m20, m.m02), 1.0f / 3.0f));
+    m.m22 = rfma(w, rsub(e, m.m22), m.m22);
+}
+
 __device__ __forceinline__ void collide(float f[9], float sx, float sy, const Lattice &L,
                                         float &dr_out, float &jx_out, float &jy_out) {
     Raw m = raw_moments(f);
-    const float jx = m.m10 + 0.5f * sx, jy = m.m01 + 0.5f * sy;
-    const float w = L.omega;
-    const float s3 = L.src * (1.0f / 3.0f);
-    m.m10 += sx;
-    m.m01 += sy;
-    m.m21 += w * (jy * (1.0f / 3.0f) - m.m21) + s3 * sy;
-    m.m12 += w * (jx * (1.0f / 3.0f) - m.m12) + s3 * sx;
-    m.m22 += w * ((m.m20 + m.m02) * (1.0f / 3.0f) - m.m00 * (1.0f / 9.0f) - m.m22);
+    relax_raw(m, sx, sy, L, jx_out, jy_out);
     dr_out = m.m00;
-    jx_out = jx;
-    jy_out = jy;
     populations(m, f);
 }
 
 // u(t+1) = u(t) + j/rho with Kahan compensation per component; w holds
 // (u_x, u_y, compensation_x, compensation_y).
 __device__ __forceinline__ void integrate_u_value(float4 &w, float jx, float jy, float rho) {
-    const float vx = jx / rho, vy = jy / rho;
-    float y = vx - w.z;
-    float t = w.x + y;
-    w.z = (t - w.x) - y;
+    // v = j/rho as j times the correctly rounded 1/rho (one reciprocal, no divisions)
+    const float ir = __frcp_rn(rho);
+    const float vx = rmul(jx, ir), vy = rmul(jy, ir);
+    float y = rsub(vx, w.z);
+    float t = radd(w.x, y);
+    w.z = rsub(rsub(t, w.x), y);
     w.x = t;
-    y = vy - w.w;
-    t = w.y + y;
-    w.w = (t - w.y) - y;
+    y = rsub(vy, w.w);
+    t = radd(w.y, y);
+    w.w = rsub(rsub(t, w.y), y);
     w.y = t;
 }
 
 __device__ __forceinline__ void integrate_u(float4 *uc, float jx, float jy, float rho) {
     float4 w = *uc;
-    const float vx = jx / rho, vy = jy / rho;
-    float y = vx - w.z;
-    float t = w.x + y;
-    w.z = (t - w.x) - y;
-    w.x = t;
-    y = vy - w.w;
-    t = w.y + y;
-    w.w = (t - w.y) - y;
-    w.y = t;
+    integrate_u_value(w, jx, jy, rho);
     *uc = w;
 }
 
@@ -179,7 +191,7 @@ __device__ __forceinline__ void flag_nonfinite(uint32_t *status, float a, float 
 // Amplitude of a boundary value at (lattice) time t: step or ramp-then-hold.
 __device__ __forceinline__ float amplitude(const BCDev &b, float t) {
     if (t < 0.0f) return 0.0f;
-    if (b.profile == LBM_PROFILE_RAMP) return fminf(t / b.t_ramp, 1.0f);
+    if (b.profile == LBM_PROFILE_RAMP) return fminf(__fdiv_rn(t, b.t_ramp), 1.0f);
     return 1.0f;
 }
 
@@ -188,14 +200,14 @@ __device__ __forceinline__ void traction(const BCDev &b, float n0, float n1, flo
                                          float &ty) {
     const float a = amplitude(b, t);
     if (b.kind == LBM_BC_PRESSURE) {
-        tx = -b.v0 * n0 * a;
-        ty = -b.v0 * n1 * a;
+        tx = rmul(rmul(-b.v0, n0), a);
+        ty = rmul(rmul(-b.v0, n1), a);
     } else if (b.kind == LBM_BC_STRESS) {
-        tx = (b.v0 * n0 + b.v2 * n1) * a;
-        ty = (b.v2 * n0 + b.v1 * n1) * a;
+        tx = rmul(rfma(b.v0, n0, rmul(b.v2, n1)), a);
+        ty = rmul(rfma(b.v2, n0, rmul(b.v1, n1)), a);
     } else {
-        tx = b.v0 * a;
-        ty = b.v1 * a;
+        tx = rmul(b.v0, a);
+        ty = rmul(b.v1, a);
     }
 }
 
@@ -212,6 +224,183 @@ __device__ __forceinline__ void pull_interior(const T *__restrict__ src, int64_t
     f[6] = Store<T>::ld(src + 6 * plane + k - pitch + 1, inv_scale);
     f[7] = Store<T>::ld(src + 7 * plane + k + pitch + 1, inv_scale);
     f[8] = Store<T>::ld(src + 8 * plane + k + pitch - 1, inv_scale);
+}
+
+
+// ---------------------------------------------------------------------------
+// Cooperative boundary update: eight lanes per boundary node.  Lane j owns the
+// population k = j + 1 and the link i = opp(k) through which it arrives.  Every
+// lane reads the node's nine post-collision populations (the same addresses,
+// a broadcast) and forms their moments with moments(); after the rules, the
+// nine incoming populations are gathered with shuffles and every lane runs
+// collide() on them.  The arithmetic is therefore that of a one-lane update
+// (the same functions in the same order), whichever form a kernel uses.
+__device__ __forceinline__ int lane_cx(int k) {
+    return (k == 1 || k == 5 || k == 8) ? 1 : (k == 3 || k == 6 || k == 7) ? -1 : 0;
+}
+__device__ __forceinline__ int lane_cy(int k) {
+    return (k == 2 || k == 5 || k == 6) ? 1 : (k == 4 || k == 7 || k == 8) ? -1 : 0;
+}
+
+
+// Pieces of the cut-link rules of Sec. 4, shared by every boundary path so
+// that each evaluates the same expressions.
+//
+// kappa = (l - 2 s)/(l + 2 s) and 1 + kappa = 2 l/(l + 2 s) of the curved rules
+// (Eqs. bbnoncon, abbnoncon) for q = s/l; q = 1/2 gives 0 and 1.
+__device__ __forceinline__ void link_kappa(float q, float &kap, float &fac) {
+    const float den = rfma(2.0f, q, 1.0f);
+    kap = __fdiv_rn(rfma(-2.0f, q, 1.0f), den);
+    fac = __fdiv_rn(2.0f, den);
+}
+
+// Dirichlet data j* = rho0 d(u*)/dt (Eq. bcchaindir); a corner link takes the
+// mean of its two Dirichlet edges (bc2 = bc on a plain edge).
+__device__ __forceinline__ void dirichlet_momentum(const BLink &lk, const BCDev *__restrict__ bcs,
+                                                   float tb, const Lattice &L, float &jsx,
+                                                   float &jsy) {
+    const BCDev ba = bcs[lk.bc], bb = bcs[lk.bc2];
+    const float aa = amplitude(ba, tb), ab = amplitude(bb, tb);
+    const float h = rmul(L.rho0, 0.5f);
+    jsx = rmul(h, rfma(ba.v0, aa, rmul(bb.v0, ab)));
+    jsy = rmul(h, rfma(ba.v1, aa, rmul(bb.v1, ab)));
+}
+
+// Traction of a non-corner Neumann link in its boundary frame (e^n = n,
+// e^t = (-n1, n0)): normal and tangential components (Eq. trafocauchy).
+struct WallFrame {
+    float n0, n1, t0, t1, tn, tt;
+};
+
+__device__ __forceinline__ WallFrame wall_frame(const BLink &lk, const BCDev *__restrict__ bcs,
+                                                float tb) {
+    WallFrame w;
+    w.n0 = lk.n0;
+    w.n1 = lk.n1;
+    w.t0 = -w.n1;
+    w.t1 = w.n0;
+    float tx, ty;
+    traction(bcs[lk.bc], w.n0, w.n1, tb, tx, ty);
+    w.tn = rfma(tx, w.n0, rmul(ty, w.n1));
+    w.tt = rfma(tx, w.t0, rmul(ty, w.t1));
+    return w;
+}
+
+// Density deviation and Cauchy stress at the wall: the node's own values, or
+// the linear extrapolation along the link (1 + q) a(x) - q a(x - c_i) when
+// `neu_ex` (Sec. 4; q = 1/2 gives (3 a(x) - a(x - c_i))/2).
+struct WallState {
+    float drb, sxx, syy, sxy;
+};
+
+__device__ __forceinline__ WallState wall_state(bool neu_ex, float q, float dr_x, float pxx_x,
+                                                float pyy_x, float pxy_x, float my_dr,
+                                                float my_xx, float my_yy, float my_xy,
+                                                const Lattice &L) {
+    const float dvx = rmul(-L.lam_m_mu_r0, dr_x);
+    const float sxx_x = radd(-pxx_x, dvx), syy_x = radd(-pyy_x, dvx), sxy_x = -pxy_x;
+    WallState s{dr_x, sxx_x, syy_x, sxy_x};
+    if (neu_ex) {
+        const float dvy = rmul(-L.lam_m_mu_r0, my_dr);
+        const float a1 = radd(1.0f, q);
+        s.drb = rfma(a1, dr_x, -rmul(q, my_dr));
+        s.sxx = rfma(a1, sxx_x, -rmul(q, radd(-my_xx, dvy)));
+        s.syy = rfma(a1, syy_x, -rmul(q, radd(-my_yy, dvy)));
+        s.sxy = rfma(a1, sxy_x, -rmul(q, -my_xy));
+    }
+    return s;
+}
+
+// sigma* = t_n n n + t_t (n t + t n) + sigma_tt t t with sigma_tt of the wall state.
+__device__ __forceinline__ void wall_sigma(const WallFrame &w, const WallState &s, float &sxx,
+                                           float &syy, float &sxy) {
+    const float stt = rfma(rmul(w.t1, w.t1), s.syy,
+                           rfma(rmul(rmul(2.0f, w.t0), w.t1), s.sxy, rmul(rmul(w.t0, w.t0), s.sxx)));
+    sxx = rfma(rmul(stt, w.t0), w.t0,
+               rfma(rmul(rmul(2.0f, w.tt), w.n0), w.t0, rmul(rmul(w.tn, w.n0), w.n0)));
+    syy = rfma(rmul(stt, w.t1), w.t1,
+               rfma(rmul(rmul(2.0f, w.tt), w.n1), w.t1, rmul(rmul(w.tn, w.n1), w.n1)));
+    sxy = rfma(rmul(stt, w.t0), w.t1,
+               rfma(w.tt, rfma(w.n0, w.t1, rmul(w.t0, w.n1)), rmul(rmul(w.tn, w.n0), w.n1)));
+}
+
+// Second moment of the wall equilibrium: P* = -sigma* + (lambda - mu) div u I,
+// div u = (rho0 - rho^bd)/rho0 (Eqs. bcchainneum, approxdiv), in deviation form.
+struct WallMoments {
+    float drb, axx, ayy, pxy;
+};
+
+__device__ __forceinline__ WallMoments wall_moments(float drb, float sxx, float syy, float sxy,
+                                                    const Lattice &L) {
+    const float dv = rmul(-L.lam_m_mu_r0, drb);
+    const float pxx = radd(-sxx, dv), pyy = radd(-syy, dv), pxy = -sxy;
+    return WallMoments{drb, rfma(drb, -(1.0f / 3.0f), pxx), rfma(drb, -(1.0f / 3.0f), pyy), pxy};
+}
+
+// 2 w_i f_i^eq(rho^bd, P*) of the anti-bounce-back rule for link i = opp(k).
+__device__ __forceinline__ float wall_equilibrium(int k, const WallMoments &m) {
+    const int i = k <= 4 ? (k + 1) % 4 + 1 : (k - 3) % 4 + 5;  // opp(k)
+    const float w = (i <= 4) ? (1.0f / 9.0f) : (1.0f / 36.0f);
+    const float cix = (float)(-lane_cx(k)), ciy = (float)(-lane_cy(k));
+    const float quad = rfma(rmul(ciy, ciy), m.ayy,
+                            rfma(rmul(rmul(2.0f, cix), ciy), m.pxy, rmul(rmul(cix, cix), m.axx)));
+    const float con = rmul(4.5f, rfma(-radd(m.axx, m.ayy), 1.0f / 3.0f, quad));
+    return rmul(rmul(2.0f, w), radd(m.drb, con));
+}
+
+// Eq. (bbnoncon) for link i = opp(k) given j*; kappa = 0, 1 + kappa = 1 (q = 1/2)
+// give Eq. (bbcon).
+__device__ __forceinline__ float bounce_back(int k, float kap, float fac, float gk, float gi,
+                                             float gy_i, float jsx, float jsy) {
+    const int i = k <= 4 ? (k + 1) % 4 + 1 : (k - 3) % 4 + 5;
+    const float w = (i <= 4) ? (1.0f / 9.0f) : (1.0f / 36.0f);
+    const float cix = (float)(-lane_cx(k)), ciy = (float)(-lane_cy(k));
+    const float cj = rfma(cix, jsx, rmul(ciy, jsy));
+    return rfma(-rmul(fac, rmul(6.0f, w)), cj, rfma(kap, rsub(gy_i, gk), gi));
+}
+
+// Eq. (abbnoncon) for link i = opp(k) given its wall equilibrium term.
+__device__ __forceinline__ float anti_bounce_back(float kap, float fac, float gk, float gi,
+                                                  float gy_i, float eq) {
+    return rfma(fac, eq, rfma(-kap, radd(gy_i, gk), -gi));
+}
+
+// f_k(x, t) arriving through the cut link i = opp(k) of a boundary node:
+// Eq. (bbnoncon) for a Dirichlet link, Eq. (abbnoncon) for a Neumann one (both
+// reduce to Eqs. bbcon/abbcon at q = 1/2).  gk, gi: f_k^col(x), f_i^col(x) at
+// t-1; gy_i: f_i^col(x - c_i) (0 if the upstream node is unusable, `miss`);
+// dr_x, p**_x: density deviation and P of f^col(x); my_*: the same moments at
+// x - c_i, used when the Neumann wall values are extrapolated (`neu_ex`).
+__device__ __forceinline__ float cut_link_value(int k, bool miss, bool dirich, bool corner,
+                                                bool neu_ex, const BLink &lk, float gk, float gi,
+                                                float gy_i, float dr_x, float pxx_x, float pyy_x,
+                                                float pxy_x, float my_dr, float my_xx,
+                                                float my_yy, float my_xy,
+                                                const BCDev *__restrict__ bcs, float tb,
+                                                const Lattice &L) {
+    const float q = miss ? 0.5f : lk.q;
+    float kap, fac;
+    link_kappa(q, kap, fac);
+    if (dirich) {
+        float jsx, jsy;
+        dirichlet_momentum(lk, bcs, tb, L, jsx, jsy);
+        return bounce_back(k, kap, fac, gk, gi, gy_i, jsx, jsy);
+    }
+    const WallState st = wall_state(neu_ex, q, dr_x, pxx_x, pyy_x, pxy_x, my_dr, my_xx, my_yy,
+                                    my_xy, L);
+    float sxx, syy, sxy;  // sigma* (Eq. trafocauchy)
+    if (corner) {
+        float tax, tay, tbx, tby;
+        traction(bcs[lk.bc], lk.n0, 0.0f, tb, tax, tay);
+        traction(bcs[lk.bc2], 0.0f, lk.n1, tb, tbx, tby);
+        sxx = rmul(tax, lk.n0);
+        syy = rmul(tby, lk.n1);
+        sxy = rmul(0.5f, rfma(tay, lk.n0, rmul(tbx, lk.n1)));
+    } else {
+        wall_sigma(wall_frame(lk, bcs, tb), st, sxx, syy, sxy);
+    }
+    const float eq = wall_equilibrium(k, wall_moments(st.drb, sxx, syy, sxy, L));
+    return anti_bounce_back(kap, fac, gk, gi, gy_i, eq);
 }
 
 // Populations f(x, t) of a boundary node: pulled where the link is intact,
@@ -244,10 +433,6 @@ __device__ __forceinline__ void pull_boundary(const T *__restrict__ src, const B
         gy1[i] = Store<T>::ld(src + i * P + ku, L.inv_scale);
     }
     const Mom mx = moments(gx);
-    // Cauchy stress at x (Eq. poissonstress with Eq. approxdiv), deviation form
-    const float dvx = -L.lam_m_mu_r0 * mx.dr;
-    const float sxx_x = -mx.pxx + dvx, syy_x = -mx.pyy + dvx, sxy_x = -mx.pxy;
-
     f[0] = gx[0];
 #pragma unroll
     for (int kk = 1; kk < 9; ++kk) {
@@ -258,203 +443,108 @@ __device__ __forceinline__ void pull_boundary(const T *__restrict__ src, const B
             f[kk] = pl[kk];
             continue;
         }
-        const BLink lk = links[i - 1];
         const bool miss = (b.miss & bit) != 0;
-        const float q = miss ? 0.5f : lk.q;
-        const float kap = (1.0f - 2.0f * q) / (1.0f + 2.0f * q);
-        const float fac = 2.0f / (1.0f + 2.0f * q);  // 1 + kappa = 2 l/(l + 2 s)
-        const float w = (i <= 4) ? (1.0f / 9.0f) : (1.0f / 36.0f);
-        const float cix = (float)c_cx(i), ciy = (float)c_cy(i);
-        const float gy_i = miss ? 0.0f : gy1[i];
-        if (b.dirich & bit) {
-            const BCDev ba = bcs[lk.bc], bb = bcs[lk.bc2];
-            const float aa = amplitude(ba, tb), ab = amplitude(bb, tb);
-            // j* = rho0 d(u*)/dt (Eq. bcchaindir); corners: mean of the Dirichlet edges
-            const float jsx = L.rho0 * 0.5f * (ba.v0 * aa + bb.v0 * ab);
-            const float jsy = L.rho0 * 0.5f * (ba.v1 * aa + bb.v1 * ab);
-            const float cj = cix * jsx + ciy * jsy;
-            // Eq. (bbnoncon); kappa = 0 and 1 + kappa = 1 give Eq. (bbcon)
-            f[kk] = gx[i] + kap * (gy_i - gx[kk]) - fac * (6.0f * w) * cj;
-            continue;
-        }
-        // Neumann: density and stress at the wall by extrapolation along the link
-        // (or the node's own values with the wall-node option)
-        float drb = mx.dr, sbxx = sxx_x, sbyy = syy_x, sbxy = sxy_x;
-        if (!miss && !L.wall_node) {
+        const bool dirich = (b.dirich & bit) != 0;
+        const bool neu_ex = !miss && !L.wall_node && !dirich;
+        float my_dr = 0.0f, my_xx = 0.0f, my_yy = 0.0f, my_xy = 0.0f;
+        if (neu_ex) {
             const int64_t ku = k - (int64_t)c_cy(i) * L.pitch - c_cx(i);
             float gy[9];
 #pragma unroll
             for (int m = 0; m < 9; ++m) gy[m] = Store<T>::ld(src + m * P + ku, L.inv_scale);
             const Mom my = moments(gy);
-            const float dvy = -L.lam_m_mu_r0 * my.dr;
-            const float a1 = 1.0f + q;
-            drb = a1 * mx.dr - q * my.dr;
-            sbxx = a1 * sxx_x - q * (-my.pxx + dvy);
-            sbyy = a1 * syy_x - q * (-my.pyy + dvy);
-            sbxy = a1 * sxy_x - q * (-my.pxy);
+            my_dr = my.dr;
+            my_xx = my.pxx;
+            my_yy = my.pyy;
+            my_xy = my.pxy;
         }
-        float sxx, syy, sxy;  // sigma* (Eq. trafocauchy)
-        if (b.corner & bit) {
-            float tax, tay, tbx, tby;
-            traction(bcs[lk.bc], lk.n0, 0.0f, tb, tax, tay);
-            traction(bcs[lk.bc2], 0.0f, lk.n1, tb, tbx, tby);
-            sxx = tax * lk.n0;
-            syy = tby * lk.n1;
-            sxy = 0.5f * (tay * lk.n0 + tbx * lk.n1);
-        } else {
-            const float n0 = lk.n0, n1 = lk.n1, t0 = -n1, t1 = n0;  // e^n, e^t
-            float tx, ty;
-            traction(bcs[lk.bc], n0, n1, tb, tx, ty);
-            const float tn = tx * n0 + ty * n1, tt = tx * t0 + ty * t1;
-            const float stt = t0 * t0 * sbxx + 2.0f * t0 * t1 * sbxy + t1 * t1 * sbyy;
-            sxx = tn * n0 * n0 + 2.0f * tt * n0 * t0 + stt * t0 * t0;
-            syy = tn * n1 * n1 + 2.0f * tt * n1 * t1 + stt * t1 * t1;
-            sxy = tn * n0 * n1 + tt * (n0 * t1 + t0 * n1) + stt * t0 * t1;
-        }
-        // P* = -sigma* + (lambda - mu) div u I, div u = (rho0 - rho^bd)/rho0 (Eq. bcchainneum)
-        const float dv = -L.lam_m_mu_r0 * drb;
-        const float pxx = -sxx + dv, pyy = -syy + dv, pxy = -sxy;
-        const float axx = pxx - drb * (1.0f / 3.0f), ayy = pyy - drb * (1.0f / 3.0f);
-        const float con = 4.5f * (cix * cix * axx + 2.0f * cix * ciy * pxy + ciy * ciy * ayy -
-                                  (axx + ayy) * (1.0f / 3.0f));
-        const float eq = 2.0f * w * (drb + con);
-        // Eq. (abbnoncon); kappa = 0 and 1 + kappa = 1 give Eq. (abbcon)
-        f[kk] = -gx[i] - kap * (gy_i + gx[kk]) + fac * eq;
+        f[kk] = cut_link_value(kk, miss, dirich, (b.corner & bit) != 0, neu_ex, links[i - 1],
+                               gx[kk], gx[i], miss ? 0.0f : gy1[i], mx.dr, mx.pxx, mx.pyy,
+                               mx.pxy, my_dr, my_xx, my_yy, my_xy, bcs, tb, L);
     }
 }
 
-// ---------------------------------------------------------------------------
-// Cooperative boundary update: eight lanes per boundary node.  Lane j owns the
-// population k = j + 1 and the link i = opp(k) through which it arrives; lane
-// 0 also carries the rest population.  Moments are formed with butterfly
-// shuffles inside the 8-lane group (every lane ends with bit-identical sums,
-// since each pairwise addition is commutative), so a node's loads are issued
-// by eight lanes at once and its serial chain is an eighth of the single-thread
-// form above.
-__device__ __forceinline__ float grp8_sum(float v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    return v;
-}
-
-__device__ __forceinline__ int lane_cx(int k) {
-    return (k == 1 || k == 5 || k == 8) ? 1 : (k == 3 || k == 6 || k == 7) ? -1 : 0;
-}
-__device__ __forceinline__ int lane_cy(int k) {
-    return (k == 2 || k == 5 || k == 6) ? 1 : (k == 4 || k == 7 || k == 8) ? -1 : 0;
-}
-
-// Raw moments of a node's populations held one per lane (+ f0 on lane 0).
-__device__ __forceinline__ Raw grp8_raw(float fk, float f0, int cx, int cy, bool lane0) {
-    const float cxx = (float)(cx * cx), cyy = (float)(cy * cy);
-    Raw m;
-    m.m00 = grp8_sum(fk + (lane0 ? f0 : 0.0f));
-    m.m10 = grp8_sum(cx * fk);
-    m.m01 = grp8_sum(cy * fk);
-    m.m20 = grp8_sum(cxx * fk);
-    m.m02 = grp8_sum(cyy * fk);
-    m.m11 = grp8_sum((float)(cx * cy) * fk);
-    m.m21 = grp8_sum(cxx * cy * fk);
-    m.m12 = grp8_sum(cx * cyy * fk);
-    m.m22 = grp8_sum(cxx * cyy * fk);
-    return m;
-}
-
-// f_k(x, t) for lane k of a boundary node (and f_0 on lane 0): pulled where
-// link opp(k) is intact, otherwise Eqs. (bbnoncon)/(abbnoncon).  Same rules
-// and data as pull_boundary.
-template <class T>
-__device__ __forceinline__ float pull_boundary8(const T *__restrict__ src, const BNode &b, int k,
-                                                const BLink *__restrict__ links,
-                                                const BCDev *__restrict__ bcs, float tb,
-                                                const Lattice &L, bool lane0, float &f0) {
-    const int64_t kn = (int64_t)b.y * L.pitch + b.x;
-    const int64_t P = L.plane;
+// f_k(x, t) for lane k of a boundary node: pulled where link opp(k) is intact,
+// otherwise Eqs. (bbnoncon)/(abbnoncon).  Same rules and data as
+// pull_boundary.  `ld(m, dx, dy)` returns f_m^col(t-1) at the node offset by
+// (dx, dy); `link(i)` the link record of cut direction i; the masks are those
+// of BNode.  g0 receives f_0^col(x), which is f_0(x, t).
+template <class Ld, class Lk>
+__device__ __forceinline__ float boundary8_pull(const Ld &ld, uint32_t cutm, uint32_t dirm,
+                                                uint32_t corm, uint32_t missm, int k,
+                                                const Lk &link, const BCDev *__restrict__ bcs,
+                                                float tb, const Lattice &L, float &g0) {
     const int i = k <= 4 ? (k + 1) % 4 + 1 : (k - 3) % 4 + 5;  // opp(k)
     const int cxk = lane_cx(k), cyk = lane_cy(k);
-    const int cxi = -cxk, cyi = -cyk;
     const uint32_t bit = 1u << i;
-    const bool cut = (b.cut & bit) != 0;
-    const bool miss = (b.miss & bit) != 0;
+    const bool cut = (cutm & bit) != 0;
+    const bool miss = (missm & bit) != 0;
     // loads, all independent
-    const float gk = Store<T>::ld(src + k * P + kn, L.inv_scale);      // f_k^col(x)
-    const float gi = Store<T>::ld(src + i * P + kn, L.inv_scale);      // f_i^col(x)
-    f0 = lane0 ? Store<T>::ld(src + kn, L.inv_scale) : 0.0f;           // f_0^col(x)
-    const int64_t kpull = cut ? kn : kn - (int64_t)cyk * L.pitch - cxk;
-    const float pulled = Store<T>::ld(src + k * P + kpull, L.inv_scale);
-    const int64_t ku = (cut && !miss) ? kn - (int64_t)cyi * L.pitch - cxi : kn;
-    const float gy_i = (cut && !miss) ? Store<T>::ld(src + i * P + ku, L.inv_scale) : 0.0f;
-    const bool neu_ex = cut && !miss && !L.wall_node && !(b.dirich & bit);
+    float g[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) g[m] = ld(m, 0, 0);  // f^col(x), the same on every lane
+    g0 = g[0];
+    const float gk = ld(k, 0, 0);                     // f_k^col(x)
+    const float gi = ld(i, 0, 0);                     // f_i^col(x)
+    const float pulled = cut ? gk : ld(k, -cxk, -cyk);
+    const bool up = cut && !miss;                     // upstream node x - c_i = x + c_k usable
+    const float gy_i = up ? ld(i, cxk, cyk) : 0.0f;
+    const bool neu_ex = up && !L.wall_node && !(dirm & bit);
     float my_dr = 0.0f, my_xx = 0.0f, my_yy = 0.0f, my_xy = 0.0f;
     if (neu_ex) {
         float gy[9];
 #pragma unroll
-        for (int m = 0; m < 9; ++m) gy[m] = Store<T>::ld(src + m * P + ku, L.inv_scale);
+        for (int m = 0; m < 9; ++m) gy[m] = ld(m, cxk, cyk);
         const Mom my = moments(gy);
         my_dr = my.dr;
         my_xx = my.pxx;
         my_yy = my.pyy;
         my_xy = my.pxy;
     }
-    BLink lk;
-    if (cut) lk = links[i - 1];
-    // moments of f^col(x, t-1) (rho and P are collision invariants)
-    const float cxf = (float)cxk, cyf = (float)cyk;
-    const float dr_x = grp8_sum(gk + f0);
-    const float pxx_x = grp8_sum(cxf * cxf * gk);
-    const float pyy_x = grp8_sum(cyf * cyf * gk);
-    const float pxy_x = grp8_sum(cxf * cyf * gk);
     if (!cut) return pulled;
-    const float q = miss ? 0.5f : lk.q;
-    const float kap = (1.0f - 2.0f * q) / (1.0f + 2.0f * q);
-    const float fac = 2.0f / (1.0f + 2.0f * q);
-    const float w = (i <= 4) ? (1.0f / 9.0f) : (1.0f / 36.0f);
-    const float cix = (float)cxi, ciy = (float)cyi;
-    if (b.dirich & bit) {
-        const BCDev ba = bcs[lk.bc], bb = bcs[lk.bc2];
-        const float aa = amplitude(ba, tb), ab = amplitude(bb, tb);
-        const float jsx = L.rho0 * 0.5f * (ba.v0 * aa + bb.v0 * ab);
-        const float jsy = L.rho0 * 0.5f * (ba.v1 * aa + bb.v1 * ab);
-        const float cj = cix * jsx + ciy * jsy;
-        return gi + kap * (gy_i - gk) - fac * (6.0f * w) * cj;
-    }
-    const float dvx = -L.lam_m_mu_r0 * dr_x;
-    const float sxx_x = -pxx_x + dvx, syy_x = -pyy_x + dvx, sxy_x = -pxy_x;
-    float drb = dr_x, sbxx = sxx_x, sbyy = syy_x, sbxy = sxy_x;
-    if (neu_ex) {
-        const float dvy = -L.lam_m_mu_r0 * my_dr;
-        const float a1 = 1.0f + q;
-        drb = a1 * dr_x - q * my_dr;
-        sbxx = a1 * sxx_x - q * (-my_xx + dvy);
-        sbyy = a1 * syy_x - q * (-my_yy + dvy);
-        sbxy = a1 * sxy_x - q * (-my_xy);
-    }
-    float sxx, syy, sxy;
-    if (b.corner & bit) {
-        float tax, tay, tbx, tby;
-        traction(bcs[lk.bc], lk.n0, 0.0f, tb, tax, tay);
-        traction(bcs[lk.bc2], 0.0f, lk.n1, tb, tbx, tby);
-        sxx = tax * lk.n0;
-        syy = tby * lk.n1;
-        sxy = 0.5f * (tay * lk.n0 + tbx * lk.n1);
-    } else {
-        const float n0 = lk.n0, n1 = lk.n1, t0 = -n1, t1 = n0;
-        float tx, ty;
-        traction(bcs[lk.bc], n0, n1, tb, tx, ty);
-        const float tn = tx * n0 + ty * n1, tt = tx * t0 + ty * t1;
-        const float stt = t0 * t0 * sbxx + 2.0f * t0 * t1 * sbxy + t1 * t1 * sbyy;
-        sxx = tn * n0 * n0 + 2.0f * tt * n0 * t0 + stt * t0 * t0;
-        syy = tn * n1 * n1 + 2.0f * tt * n1 * t1 + stt * t1 * t1;
-        sxy = tn * n0 * n1 + tt * (n0 * t1 + t0 * n1) + stt * t0 * t1;
-    }
-    const float dv = -L.lam_m_mu_r0 * drb;
-    const float pxx = -sxx + dv, pyy = -syy + dv, pxy = -sxy;
-    const float axx = pxx - drb * (1.0f / 3.0f), ayy = pyy - drb * (1.0f / 3.0f);
-    const float con = 4.5f * (cix * cix * axx + 2.0f * cix * ciy * pxy + ciy * ciy * ayy -
-                              (axx + ayy) * (1.0f / 3.0f));
-    const float eq = 2.0f * w * (drb + con);
-    return -gi - kap * (gy_i + gk) + fac * eq;
+    const Mom mx = moments(g);  // rho and P are collision invariants: those of f^col(x, t-1)
+    return cut_link_value(k, miss, (dirm & bit) != 0, (corm & bit) != 0, neu_ex, link(i), gk, gi,
+                          gy_i, mx.dr, mx.pxx, mx.pyy, mx.pxy, my_dr, my_xx, my_yy, my_xy, bcs, tb,
+                          L);
+}
+
+// The same from the distributions in global memory.
+template <class T>
+__device__ __forceinline__ float pull_boundary8(const T *__restrict__ src, const BNode &b, int k,
+                                                const BLink *__restrict__ links,
+                                                const BCDev *__restrict__ bcs, float tb,
+                                                const Lattice &L, float &f0) {
+    const int64_t kn = (int64_t)b.y * L.pitch + b.x;
+    const int64_t P = L.plane;
+    const int pitch = L.pitch;
+    const float inv = L.inv_scale;
+    auto ld = [&](int m, int dx, int dy) {
+        return Store<T>::ld(src + m * P + kn + (int64_t)dy * pitch + dx, inv);
+    };
+    auto link = [&](int i) { return links[i - 1]; };
+    return boundary8_pull(ld, b.cut, b.dirich, b.corner, b.miss, k, link, bcs, tb, L, f0);
+}
+
+// Collision of a boundary node held one population per lane (group of eight
+// lanes, direction kdir on lane kdir - 1; g0 = f_0): the nine populations are
+// gathered on every lane and collide() runs on them.  Returns the
+// post-collision population of the lane's direction; on every lane f0_out,
+// jx, jy and dr are the node's rest population, momentum and density deviation.
+__device__ __forceinline__ float boundary8_collide(float fk, float g0, int kdir, float sx,
+                                                   float sy, const Lattice &L, float &f0_out,
+                                                   float &jx, float &jy, float &dr) {
+    const int base = threadIdx.x & 24;  // first lane of the group within the warp
+    float f[9];
+    f[0] = g0;
+#pragma unroll
+    for (int m = 1; m < 9; ++m) f[m] = __shfl_sync(0xffffffffu, fk, base + m - 1);
+    collide(f, sx, sy, L, dr, jx, jy);
+    float mine = f[1];
+#pragma unroll
+    for (int q = 2; q < 9; ++q)
+        if (kdir == q) mine = f[q];
+    f0_out = f[0];
+    return mine;
 }
 
 // Source S = F + (mu - lambda)/rho grad rho at an interior node (central
@@ -591,33 +681,18 @@ __device__ __forceinline__ void boundary8_node(const T *__restrict__ src, T *__r
     const BNode b = bnodes[g];
     const int kdir = j + 1;
     float f0;
-    const float fk = pull_boundary8(src, b, kdir, blinks + (int64_t)g * 8, bcs, tb, L, lane0, f0);
+    const float fk = pull_boundary8(src, b, kdir, blinks + (int64_t)g * 8, bcs, tb, L, f0);
     const int64_t kn = (int64_t)b.y * L.pitch + b.x;
     float sx = L.fx, sy = L.fy;
     if (L.grad) source_boundary8(src, cls, rho, b, kn, L, j, sx, sy);
-    // collision on the raw moments (as collide())
-    const int cx = lane_cx(kdir), cy = lane_cy(kdir);
-    Raw m = grp8_raw(fk, f0, cx, cy, lane0);
-    const float jx = m.m10 + 0.5f * sx, jy = m.m01 + 0.5f * sy;
-    const float w = L.omega;
-    const float s3 = L.src * (1.0f / 3.0f);
-    m.m10 += sx;
-    m.m01 += sy;
-    m.m21 += w * (jy * (1.0f / 3.0f) - m.m21) + s3 * sy;
-    m.m12 += w * (jx * (1.0f / 3.0f) - m.m12) + s3 * sx;
-    m.m22 += w * ((m.m20 + m.m02) * (1.0f / 3.0f) - m.m00 * (1.0f / 9.0f) - m.m22);
-    float f[9];
-    populations(m, f);
-    float mine = f[1];
-#pragma unroll
-    for (int q = 2; q < 9; ++q)
-        if (kdir == q) mine = f[q];
+    float fr, jx, jy, m00;
+    const float mine = boundary8_collide(fk, f0, kdir, sx, sy, L, fr, jx, jy, m00);
     if (!live) return;
     Store<T>::st(dst + kdir * L.plane + kn, mine, L.scale);
     if (lane0) {
-        Store<T>::st(dst + kn, f[0], L.scale);
-        integrate_u(uc + kn, jx, jy, L.rho0 + m.m00);
-        flag_nonfinite(status, m.m00, jx, jy);
+        Store<T>::st(dst + kn, fr, L.scale);
+        integrate_u(uc + kn, jx, jy, L.rho0 + m00);
+        flag_nonfinite(status, m00, jx, jy);
     }
 }
 

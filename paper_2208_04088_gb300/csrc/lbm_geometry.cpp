@@ -294,8 +294,8 @@ lbm_status classify(const lbm_desc &d, const Units &u, Tables *t) {
         return LBM_ERR_ARG;
     }
     if ((d.wall_values != LBM_WALL_EXTRAPOLATE && d.wall_values != LBM_WALL_NODE) ||
-        d.reserved != 0) {
-        set_error("lbm_create: unknown wall_values, or reserved != 0");
+        (d.time_block != 0 && d.time_block != 1 && d.time_block != LBM_TIME_BLOCK)) {
+        set_error("lbm_create: unknown wall_values, or time_block not 0, 1 or LBM_TIME_BLOCK");
         return LBM_ERR_ARG;
     }
     const int64_t N = (int64_t)nx * ny;

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <string>
 #include <vector>
@@ -110,6 +111,7 @@ struct DevState {
     float *stage = nullptr;           // field staging [7][ny][nx]
     float *probe = nullptr;           // probe staging [7][max_probe]
     int32_t *probe_idx = nullptr;
+    uint64_t *nw = nullptr;           // per-node words of the temporally blocked kernel
 };
 
 constexpr int kMaxProbe = 4096;
@@ -120,6 +122,7 @@ constexpr int kMaxProbe = 4096;
 struct StepEvents {
     cudaEvent_t before_interior, after_interior;  // on the main stream
     cudaEvent_t before_boundary, after_boundary;  // on the stream of the boundary kernel
+    int nsteps = 1;                               // steps the bracketed launch carries
 };
 
 cudaError_t launch_step(int storage, const Lattice &L, const DevState &S, int cur, int toff,
@@ -133,6 +136,30 @@ cudaError_t launch_fields(int storage, const Lattice &L, const DevState &S, int 
 cudaError_t launch_gather_probe(const Lattice &L, const DevState &S, int count,
                                 cudaStream_t s);
 cudaError_t launch_reset(int storage, const Lattice &L, const DevState &S, cudaStream_t s);
+
+// Temporally blocked stepping (lbm_wave.cu): kWaveK steps per launch, FP32
+// storage, lambda = mu.  A block owns kWaveC columns, of which the middle
+// kWaveW are its core.
+constexpr int kWaveK = 8;
+constexpr int kWaveC = 128;
+constexpr int kWaveW = kWaveC - 2 * kWaveK;
+
+struct WaveMaps {
+    CUtensorMap f[2];  // the two distribution buffers, [9][ny][pitch] FP32
+    CUtensorMap nw;    // node words [ny][pitch]
+    CUtensorMap u;     // displacement records [ny][pitch] float4
+    int nstrips = 0, nseg = 0, H = 0;
+};
+
+bool wave_supported(const Lattice &L);
+size_t wave_smem_bytes();
+// Builds the node words from the class and boundary tables and the TMA
+// descriptors; S.nw must be allocated (8 bytes per node of the pitched plane).
+cudaError_t wave_prepare(const Lattice &L, const DevState &S, WaveMaps *m, cudaStream_t s);
+// kWaveK steps from buffer `cur` into buffer cur ^ 1; the first of them is
+// step `toff` after *S.time.
+cudaError_t launch_wave(const Lattice &L, const DevState &S, const WaveMaps &m, int cur, int toff,
+                        cudaStream_t s);
 
 }  // namespace lbm
 
@@ -163,5 +190,8 @@ struct lbm_solver {
     bool timing = false;
     std::vector<lbm::StepEvents> ev_pool;
     size_t ev_used = 0;
+    // temporal blocking: steps per launch (1: one-step kernels) and its tables
+    int block = 1;
+    lbm::WaveMaps wave;
 };
 

@@ -32,7 +32,7 @@ constexpr int kBB = 64;  // threads per block of the boundary-list kernels
 // record -- is issued before any arithmetic, so all of them are in flight
 // together.
 template <class T, int NR>
-__global__ void __launch_bounds__(kBX *kBY) k_interior(const T *__restrict__ src, T *__restrict__ dst,
+__global__ void __launch_bounds__(kBX *kBY, 8) k_interior(const T *__restrict__ src, T *__restrict__ dst,
                                                        float4 *__restrict__ uc,
                                                        const uint8_t *__restrict__ cls,
                                                        const float *__restrict__ rho, Lattice L,

@@ -1,0 +1,550 @@
+// lbm_wave.cu -- temporally blocked time stepping: kWaveK steps of the solid
+// LBM (Eqs. stream, moments, fieq, coll and the boundary rules of Sec. 4) per
+// kernel launch, FP32 storage, lambda = mu (no density gradient in the source).
+//
+// One step reads and writes every population once, so the one-step kernels
+// are bound by HBM at 104 B per lattice update.  Here a block owns a strip of
+// kWaveC columns (kWaveW core columns plus kWaveK halo columns on each side)
+// and a segment of rows, and sweeps the segment bottom-up.  Time level l
+// (1..kWaveK) of row y is computed at sweep step y + 2(l - 1): the levels run
+// side by side, two rows apart, so every level reads rows y - 1 .. y + 1 of
+// the level below that are complete by the previous sweep step.  Level l - 1
+// keeps its last four rows in a shared-memory ring; level 0 (the populations
+// f^col(t0 - 1) in HBM) arrives by TMA into an eight-row ring, together with
+// the per-node words and the displacement of each row, kWaveD rows ahead of
+// use.  Level kWaveK writes f^col(t0 + kWaveK - 1) and u of the core nodes to
+// HBM.  The halo shrinks by one node per level, so the core of every strip is
+// exact; strips and segments overlap only in what they read.
+//
+// Per node and level the arithmetic is that of the one-step kernels: the
+// incoming populations (pulled, or given by the rules of Sec. 4) go through
+// collide().  Box edges and crack faces ("simple" boundary nodes) are updated
+// one lane per node; other boundary nodes by eight lanes, as in the
+// cooperative boundary kernel.  The rules are explicitly rounded and the
+// moments formed in one order, so every stored value is bit-identical to the
+// one-step path.
+#include <cstdint>
+#include <cstring>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+constexpr int kC = kWaveC, kK = kWaveK, kW = kWaveW;
+constexpr int kNI = 8;                // rows of the level-0 ring (and mbarriers)
+constexpr int kD = kNI - 3;           // rows issued ahead of the row level 1 needs
+constexpr int kNU = 2 * kK + kD;      // rows of the node-word and displacement rings
+constexpr int kThreads = kK * kC;
+constexpr int kRowF = 9 * kC;         // floats per ring row (nine planes of kC)
+constexpr uint32_t kFRowBytes = kRowF * 4;
+constexpr uint32_t kNwRowBytes = kC * 8;
+constexpr uint32_t kURowBytes = kW * 16;
+constexpr uint32_t kTxBytes = kFRowBytes + kNwRowBytes + kURowBytes;
+constexpr size_t kOffIn = 0;
+constexpr size_t kOffLev = kOffIn + (size_t)kNI * kFRowBytes;
+constexpr size_t kOffU = kOffLev + (size_t)(kK - 1) * 4 * kFRowBytes;
+constexpr size_t kOffNw = kOffU + (size_t)kNU * kURowBytes;
+constexpr size_t kOffBar = kOffNw + (size_t)kNU * kNwRowBytes;
+constexpr size_t kSmem = kOffBar + (size_t)kNI * 8;
+static_assert(kSmem <= 232448, "shared memory of one block");
+static_assert(kThreads <= 1024 && kC % 32 == 0, "block shape");
+static_assert(kOffLev % 128 == 0 && kOffU % 128 == 0 && kOffNw % 128 == 0 &&
+                  kURowBytes % 128 == 0 && kNwRowBytes % 128 == 0 && kFRowBytes % 128 == 0,
+              "TMA destinations 128-byte aligned");
+static_assert(kW % 4 == 0 && kK % 2 == 0, "TMA x coordinates on 16-byte boundaries");
+
+// Node word: bits 0-1 class; 2-9 cut, 10-17 Dirichlet, 18-25 corner, 26-33
+// upstream-missing masks (bit d - 1 for direction d); bit 34 "simple": every
+// cut link is a mid-link wall with the same BC and the same axis-aligned
+// normal, given by bits 35-50 (BC index) and 51-52 (normal +x, -x, +y, -y);
+// otherwise bits 35-63 hold the node's index in the boundary list.
+__device__ __forceinline__ uint32_t nw_mask(uint64_t w, int shift) {
+    return (uint32_t)((w >> shift) & 0xffu) << 1;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for a phase of an mbarrier, giving up after about a second.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (int outer = 0; outer < (1 << 24); ++outer) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+// The common link record of a simple node (node-word bits 35-52).
+__device__ __forceinline__ BLink simple_link(uint32_t hi) {
+    const uint32_t code = (hi >> 16) & 3u;
+    BLink sl;
+    sl.q = 0.5f;
+    sl.n0 = code == 0 ? 1.0f : (code == 1 ? -1.0f : 0.0f);
+    sl.n1 = code == 2 ? 1.0f : (code == 3 ? -1.0f : 0.0f);
+    sl.bc = (uint16_t)(hi & 0xffffu);
+    sl.bc2 = sl.bc;
+    return sl;
+}
+
+// Three consecutive ring rows of the level below and the node's column.
+struct Rows {
+    const float *rm, *r0, *rp;
+    int c;
+    __device__ __forceinline__ float operator()(int i, int dx, int dy) const {
+        const float *r = dy < 0 ? rm : (dy > 0 ? rp : r0);
+        return r[i * kC + c + dx];
+    }
+};
+
+// Incoming populations f(x, t) of a "simple" boundary node (every cut link a
+// mid-link wall, kappa = 0 and 1 + kappa = 1, of one BC and one axis-aligned
+// normal: box edges and crack faces), one lane per node.  The wall data that
+// do not depend on the link are formed once; every value is computed by the
+// same explicitly rounded functions as in cut_link_value, so the result is
+// that of the cooperative form bit for bit.
+__device__ __forceinline__ void simple_pull(const Rows &ld, uint64_t nw,
+                                            const BCDev *__restrict__ bcs, float tb,
+                                            const Lattice &L, float f[9]) {
+    const uint32_t cut = nw_mask(nw, 2), dirich = nw_mask(nw, 10), miss = nw_mask(nw, 26);
+    const BLink sl = simple_link((uint32_t)(nw >> 35));
+    float g[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) g[m] = ld(m, 0, 0);
+    f[0] = g[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) f[k] = ld(k, -c_cx(k), -c_cy(k));  // intact links (cut ones replaced)
+    const Mom mx = moments(g);
+    float kap, fac;
+    link_kappa(0.5f, kap, fac);
+    if (dirich) {
+        float jsx, jsy;
+        dirichlet_momentum(sl, bcs, tb, L, jsx, jsy);
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+            const int i = opp(k);
+            const uint32_t bit = 1u << i;
+            if (!(cut & bit)) continue;
+            const float gy_i = (miss & bit) ? 0.0f : ld(i, c_cx(k), c_cy(k));
+            f[k] = bounce_back(k, kap, fac, g[k], g[i], gy_i, jsx, jsy);
+        }
+        return;
+    }
+    const WallFrame wf = wall_frame(sl, bcs, tb);
+    // wall values at the node: the wall-node option, or no usable upstream node
+    const WallState st0 = wall_state(false, 0.5f, mx.dr, mx.pxx, mx.pyy, mx.pxy, 0.0f, 0.0f, 0.0f,
+                                     0.0f, L);
+    float sxx, syy, sxy;
+    wall_sigma(wf, st0, sxx, syy, sxy);
+    const WallMoments wm0 = wall_moments(st0.drb, sxx, syy, sxy, L);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+        const int i = opp(k);
+        const uint32_t bit = 1u << i;
+        if (!(cut & bit)) continue;
+        const int cxk = c_cx(k), cyk = c_cy(k);
+        const bool ms = (miss & bit) != 0;
+        const float gy_i = ms ? 0.0f : ld(i, cxk, cyk);
+        WallMoments wm = wm0;
+        if (!ms && !L.wall_node) {
+            // extrapolation along the link from the upstream node x - c_i
+            float gy[9];
+#pragma unroll
+            for (int m = 0; m < 9; ++m) gy[m] = ld(m, cxk, cyk);
+            const Mom my = moments(gy);
+            const WallState st = wall_state(true, 0.5f, mx.dr, mx.pxx, mx.pyy, mx.pxy, my.dr,
+                                            my.pxx, my.pyy, my.pxy, L);
+            float ax, ay, axy;
+            wall_sigma(wf, st, ax, ay, axy);
+            wm = wall_moments(st.drb, ax, ay, axy, L);
+        }
+        f[k] = anti_bounce_back(kap, fac, g[k], g[i], gy_i, wall_equilibrium(k, wm));
+    }
+}
+
+// One launch: kWaveK steps of every material node.  Block b handles strip
+// b % nstrips (core columns [X0, X0 + kWaveW)) and row segment b / nstrips
+// (core rows [Y0, Y0 + H)).  Each warp computes one level of one 32-column
+// chunk of the ring (ring column c is lattice column X0 - kWaveK + c).
+__global__ void __launch_bounds__(kThreads, 1)
+    k_wave(const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tnw,
+           const __grid_constant__ CUtensorMap tu, float *__restrict__ dst,
+           float4 *__restrict__ uc, const BLink *__restrict__ blinks,
+           const BCDev *__restrict__ bcs, Lattice L, const int64_t *__restrict__ time, int toff,
+           int nstrips, int H, uint32_t *__restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float *in = reinterpret_cast<float *>(sm + kOffIn);
+    float *lev = reinterpret_cast<float *>(sm + kOffLev);
+    float4 *ur = reinterpret_cast<float4 *>(sm + kOffU);
+    const uint64_t *nwr = reinterpret_cast<const uint64_t *>(sm + kOffNw);
+    const uint32_t bar0 = smem_addr(sm + kOffBar);
+
+    // Warp w runs on sub-partition w % 4 of the SM.  Warp w = 4 l' + s takes
+    // level l' + 1 and column chunk (s - l') mod 4: the warps of one level, and
+    // the warps of one column chunk across the levels, are spread over the four
+    // sub-partitions, so neither a wall row (boundary nodes in every chunk of
+    // a level) nor a wall column (one chunk, every level) piles its boundary
+    // updates onto one of them.
+    static_assert(kC == 128, "four column chunks of 32");
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lv = (warp >> 2) + 1;  // time level of this thread (warp-uniform)
+    const int c = ((((warp & 3) - (warp >> 2)) & 3) << 5) | (tid & 31);
+    const int X0 = (int)(blockIdx.x % (unsigned)nstrips) * kW;
+    const int Y0 = (int)(blockIdx.x / (unsigned)nstrips) * H;
+    const int Hs = min(H, L.ny - Y0);
+    const int xin = X0 - kK;     // lattice column of ring column 0
+    const int y_in0 = Y0 - kK;   // lattice row of input row index 0
+    const int j_last = Hs - 1 + 2 * kK;
+    const int nsweep = Hs + 3 * kK - 3;
+    const float tb = (float)(*time + toff + lv - 2);  // boundary data at the time of f^col
+
+    auto issue = [&](int j) {
+        const uint32_t bar = bar0 + 8u * (uint32_t)(j & (kNI - 1));
+        const int y = y_in0 + j;
+        mbar_expect_tx(bar, kTxBytes);
+        tma_load_3d(smem_addr(in + (size_t)(j & (kNI - 1)) * kRowF), &tf, xin, y, 0, bar);
+        tma_load_2d(smem_addr(sm + kOffNw + (size_t)(j % kNU) * kNwRowBytes), &tnw, xin, y, bar);
+        tma_load_3d(smem_addr(sm + kOffU + (size_t)(j % kNU) * kURowBytes), &tu, 0, X0, y, bar);
+    };
+    auto wait_row = [&](int j) {
+        return mbar_wait(bar0 + 8u * (uint32_t)(j & (kNI - 1)), (uint32_t)((j / kNI) & 1));
+    };
+
+    bool ok = true;       // thread 0: every wait so far completed
+    int j_issued = -1;    // thread 0: last input row issued
+    int last_waited = -1; // thread 0: last input row known to have landed
+    if (tid == 0) {
+        for (int s = 0; s < kNI; ++s) mbar_init(bar0 + 8u * s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int j = 0; j <= kD + 1 && j <= j_last; ++j) {
+            issue(j);
+            j_issued = j;
+        }
+        for (int j = 0; j <= 2 && j <= j_last && ok; ++j) {
+            ok = wait_row(j);
+            last_waited = ok ? j : j - 1;
+        }
+    }
+    __syncthreads();
+
+    const bool col_live = c >= lv && c < kC - lv;
+    const int lo = Y0 - (kK - lv), hi = Y0 + Hs - 1 + (kK - lv);
+    const float *prev_base = lv == 1 ? in : lev + (size_t)(lv - 2) * 4 * kRowF;
+    const int pmask = lv == 1 ? kNI - 1 : 3;
+    float *own_base = lev + (size_t)(lv - 1) * 4 * kRowF;  // unused by level kWaveK
+
+    for (int n = 0; n < nsweep; ++n) {
+        if (tid == 0 && n + kD + 2 <= j_last && ok) {
+            // order the block's earlier shared-memory accesses before the copy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(n + kD + 2);
+            j_issued = n + kD + 2;
+        }
+        const int y = y_in0 + 1 + n - 2 * (lv - 1);
+        if (y >= lo && y <= hi) {  // warp-uniform: one level per warp
+            const int j = y - y_in0;
+            const int ju = j % kNU;
+            const uint64_t nw = col_live ? nwr[(size_t)ju * kC + c] : 0ull;
+            const uint32_t cl = (uint32_t)(nw & 3u);
+            const float *rm = prev_base + (size_t)((j - 1) & pmask) * kRowF;
+            const float *r0 = prev_base + (size_t)(j & pmask) * kRowF;
+            const float *rp = prev_base + (size_t)((j + 1) & pmask) * kRowF;
+            float *own = own_base + (size_t)(j & 3) * kRowF;
+            const int64_t krow = (int64_t)y * L.pitch + xin;  // lattice index of ring column 0
+            const bool core_row = y >= Y0 && y < Y0 + Hs;
+            const bool simple_b = cl == kBoundary && ((nw >> 34) & 1u);
+            if (cl == kInterior || simple_b) {
+                float f[9];
+                float dr, jx, jy;
+                if (cl == kInterior) {
+                    f[0] = r0[c];
+                    f[1] = r0[kC + c - 1];
+                    f[2] = rm[2 * kC + c];
+                    f[3] = r0[3 * kC + c + 1];
+                    f[4] = rp[4 * kC + c];
+                    f[5] = rm[5 * kC + c - 1];
+                    f[6] = rm[6 * kC + c + 1];
+                    f[7] = rp[7 * kC + c + 1];
+                    f[8] = rp[8 * kC + c - 1];
+                } else {
+                    simple_pull(Rows{rm, r0, rp, c}, nw, bcs, tb, L, f);
+                }
+                collide(f, L.fx, L.fy, L, dr, jx, jy);
+                if (lv < kK) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) own[i * kC + c] = f[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) dst[i * L.plane + krow + c] = f[i];
+                }
+                if (core_row && c >= kK && c < kC - kK) {
+                    float4 *up = ur + (size_t)ju * kW + (c - kK);
+                    float4 w = *up;
+                    integrate_u_value(w, jx, jy, L.rho0 + dr);
+                    if (lv < kK) {
+                        *up = w;
+                    } else {
+                        uc[krow + c] = w;
+                        flag_nonfinite(status, dr, jx, jy);
+                    }
+                }
+            }
+            // the other boundary nodes of the warp (curved walls, corners): eight
+            // lanes each, the update of the cooperative boundary kernel (four
+            // nodes per pass)
+            const unsigned bmask = __ballot_sync(0xffffffffu, cl == kBoundary && !simple_b);
+            if (bmask) {  // warp-uniform
+                const int lane = tid & 31, grp = lane >> 3, kdir = (lane & 7) + 1;
+                const bool lane0 = kdir == 1;  // lane 0 of the group stores f_0 and u
+                unsigned rem = bmask;
+                while (rem) {
+                    // group g takes the g-th remaining node; spare groups redo the
+                    // first one and store nothing
+                    unsigned r = rem;
+                    for (int q = 0; q < grp; ++q) r &= r - 1;
+                    const bool live = r != 0;
+                    const int src = __ffs(live ? r : rem) - 1;
+                    for (int q = 0; q < 4; ++q) rem &= rem - 1;
+                    const uint64_t wb = __shfl_sync(0xffffffffu, nw, src);
+                    const int cb = (c & ~31) + src;
+                    const bool simple = (wb >> 34) & 1u;
+                    const uint32_t hi = (uint32_t)(wb >> 35);
+                    const BLink sl = simple_link(hi);
+                    const BLink *lrec = blinks + (int64_t)hi * 8;
+                    auto link = [&](int i) { return simple ? sl : lrec[i - 1]; };
+                    float f0;
+                    const float fk = boundary8_pull(Rows{rm, r0, rp, cb}, nw_mask(wb, 2),
+                                                    nw_mask(wb, 10), nw_mask(wb, 18),
+                                                    nw_mask(wb, 26), kdir, link, bcs, tb, L, f0);
+                    float fr, jx, jy, m00;
+                    const float mine =
+                        boundary8_collide(fk, f0, kdir, L.fx, L.fy, L, fr, jx, jy, m00);
+                    if (live) {
+                        if (lv < kK) {
+                            own[kdir * kC + cb] = mine;
+                            if (lane0) own[cb] = fr;
+                        } else {
+                            dst[kdir * L.plane + krow + cb] = mine;
+                            if (lane0) dst[krow + cb] = fr;
+                        }
+                        if (lane0 && core_row && cb >= kK && cb < kC - kK) {
+                            float4 *up = ur + (size_t)ju * kW + (cb - kK);
+                            float4 w = *up;
+                            integrate_u_value(w, jx, jy, L.rho0 + m00);
+                            if (lv < kK) {
+                                *up = w;
+                            } else {
+                                uc[krow + cb] = w;
+                                flag_nonfinite(status, m00, jx, jy);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (tid == 0 && n + 3 <= j_last && ok) {
+            ok = wait_row(n + 3);
+            if (!ok) last_waited = n + 2;
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && !ok) {
+        // a copy did not land in time: flag it, and give the copies still in
+        // flight a bounded chance to land before the block's shared memory goes
+        atomicOr(status, 2u);
+        for (int j = last_waited + 1; j <= j_issued; ++j)
+            if (!wait_row(j)) break;
+    }
+}
+
+// Node words: the class of every node, then the boundary records.
+__global__ void k_nw_fill(const uint8_t *__restrict__ cls, uint64_t *__restrict__ nw, int64_t n) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) nw[k] = cls[k];
+}
+
+__device__ __forceinline__ int normal_code(float n0, float n1) {
+    if (n1 == 0.0f && n0 == 1.0f) return 0;
+    if (n1 == 0.0f && n0 == -1.0f) return 1;
+    if (n0 == 0.0f && n1 == 1.0f) return 2;
+    if (n0 == 0.0f && n1 == -1.0f) return 3;
+    return -1;
+}
+
+__global__ void k_nw_boundary(const BNode *__restrict__ bnodes, const BLink *__restrict__ blinks,
+                              int nb, int pitch, uint64_t *__restrict__ nw) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nb) return;
+    const BNode b = bnodes[g];
+    bool simple = b.corner == 0;
+    int bc = -1, code = -1;
+    for (int i = 1; i < 9; ++i) {
+        if (!((b.cut >> i) & 1u)) continue;
+        const BLink lk = blinks[(int64_t)g * 8 + i - 1];
+        const int cd = normal_code(lk.n0, lk.n1);
+        if (lk.q != 0.5f || lk.bc != lk.bc2 || cd < 0) simple = false;
+        if (bc < 0) {
+            bc = lk.bc;
+            code = cd;
+        } else if (lk.bc != bc || cd != code) {
+            simple = false;
+        }
+    }
+    uint64_t w = (uint64_t)kBoundary | ((uint64_t)((b.cut >> 1) & 0xffu) << 2) |
+                 ((uint64_t)((b.dirich >> 1) & 0xffu) << 10) |
+                 ((uint64_t)((b.corner >> 1) & 0xffu) << 18) |
+                 ((uint64_t)((b.miss >> 1) & 0xffu) << 26);
+    if (simple && bc >= 0)
+        w |= (1ull << 34) | ((uint64_t)bc << 35) | ((uint64_t)code << 51);
+    else
+        w |= (uint64_t)g << 35;
+    nw[(int64_t)b.y * pitch + b.x] = w;
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiled) nullptr;
+        }
+        return reinterpret_cast<EncodeTiled>(p);
+    }();
+    return fn;
+}
+
+bool encode(CUtensorMap *map, CUtensorMapDataType type, cuuint32_t rank, void *base,
+            const cuuint64_t *dims, const cuuint64_t *strides, const cuuint32_t *box) {
+    EncodeTiled fn = encoder();
+    if (!fn) return false;
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(map, type, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t wave_smem_bytes() { return kSmem; }
+
+bool wave_supported(const Lattice &L) {
+    return L.nx >= kC && L.ny >= 1 && L.nb < (1 << 28) && !L.grad && encoder() != nullptr;
+}
+
+cudaError_t wave_prepare(const Lattice &L, const DevState &S, WaveMaps *m, cudaStream_t s) {
+    const int64_t n = L.plane;
+    k_nw_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S.cls, S.nw, n);
+    if (L.nb > 0)
+        k_nw_boundary<<<(L.nb + 127) / 128, 128, 0, s>>>(S.bnodes, S.blinks, L.nb, L.pitch, S.nw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const cuuint64_t fdims[3] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, 9};
+    const cuuint64_t fstr[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
+    const cuuint32_t fbox[3] = {(cuuint32_t)kC, 1, 9};
+    for (int b = 0; b < 2; ++b)
+        if (!encode(&m->f[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S.f[b], fdims, fstr, fbox))
+            return cudaErrorInvalidValue;
+    const cuuint64_t ndims[2] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny};
+    const cuuint64_t nstr[1] = {(cuuint64_t)L.pitch * 8};
+    const cuuint32_t nbox[2] = {(cuuint32_t)kC, 1};
+    if (!encode(&m->nw, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, S.nw, ndims, nstr, nbox))
+        return cudaErrorInvalidValue;
+    const cuuint64_t udims[3] = {4, (cuuint64_t)L.nx, (cuuint64_t)L.ny};
+    const cuuint64_t ustr[2] = {16, (cuuint64_t)L.pitch * 16};
+    const cuuint32_t ubox[3] = {4, (cuuint32_t)kW, 1};
+    if (!encode(&m->u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S.ucomp, udims, ustr, ubox))
+        return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(k_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e != cudaSuccess) return e;
+    // segments: at most one block per SM (one block fits an SM), each at least
+    // 4 kWaveK rows high; a second partial wave would double the launch time
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    m->nstrips = (L.nx + kW - 1) / kW;
+    int nseg = sms / m->nstrips;
+    nseg = nseg < 1 ? 1 : nseg;
+    int H = (L.ny + nseg - 1) / nseg;
+    if (H < 4 * kK) H = 4 * kK;
+    m->H = H;
+    m->nseg = (L.ny + H - 1) / H;
+    return cudaSuccess;
+}
+
+cudaError_t launch_wave(const Lattice &L, const DevState &S, const WaveMaps &m, int cur, int toff,
+                        cudaStream_t s) {
+    const unsigned grid = (unsigned)(m.nstrips * m.nseg);
+    k_wave<<<grid, kThreads, kSmem, s>>>(m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]),
+                                         S.ucomp, S.blinks, S.bcs, L, S.time, toff, m.nstrips,
+                                         m.H, S.status);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -103,3 +103,31 @@ def test_physical_units_are_accepted():
     # the paper's printed, rounded time step 7.217e-3 l/c_s is within the tolerance
     d = N.Desc(nt, links, wl.bcs, lam=1.0, mu=1.0, rho0=1.0, dx=dx, dt=7.217e-3)
     assert N.lbm_workspace_size(d) > 0
+
+
+def test_time_block_selection_and_validation():
+    """lbm_desc.time_block: 0 (default, one step per launch), 1 or
+    LBM_TIME_BLOCK (temporal blocking, FP32 storage, lambda = mu, nx >= 128);
+    the blocked form adds the 8-byte node words to the workspace."""
+    wl = W.hole_plate(256, 128, 16.0, 0)
+    plane = 256 * 128
+    one = N.lbm_workspace_size(_desc(wl, time_block=1))
+    blk = N.lbm_workspace_size(_desc(wl, time_block=N.LBM_TIME_BLOCK))
+    dflt = N.lbm_workspace_size(_desc(wl))
+    assert blk - one == (8 * plane + 255) // 256 * 256
+    assert dflt == one
+    # the default falls back to one step per launch where blocking is unsupported
+    assert N.lbm_workspace_size(_desc(wl, storage="f16")) == \
+        N.lbm_workspace_size(_desc(wl, storage="f16", time_block=1))
+    for bad in (2, 3, 16, -1):
+        with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
+            N.lbm_workspace_size(_desc(wl, time_block=bad))
+    with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
+        N.lbm_workspace_size(_desc(wl, storage="bf16", time_block=N.LBM_TIME_BLOCK))
+    nonpoisson = W.hole_plate(256, 128, 16.0, 0, lam_over_mu=0.8)
+    with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
+        N.lbm_workspace_size(_desc(nonpoisson, time_block=N.LBM_TIME_BLOCK))
+    narrow = W.square_plate(64, 0)
+    with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
+        N.lbm_workspace_size(_desc(narrow, time_block=N.LBM_TIME_BLOCK))
+    assert N.lbm_workspace_size(_desc(narrow)) == N.lbm_workspace_size(_desc(narrow, time_block=1))
