@@ -37,6 +37,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS (giga lattice updates per second, whole job)"
+# FP32 operations of one lattice update in the temporally blocked kernel (FMA =
+# 2): raw moments 24, relaxation 26, populations 30, displacement update 11
+FLOPS_PER_UPDATE = 91
+# the kernel sources each kernel's recorded DRAM traffic depends on
+KERNEL_SOURCES = {"k_interior": ("lbm_kernels.cu", "lbm_device.cuh"),
+                  "k_wave": ("lbm_wave.cu", "lbm_device.cuh")}
 WORKLOADS = ("crack", "plate", "batch", "serve")
 
 
@@ -193,21 +199,24 @@ def run_reference(args):
     return 0
 
 
-def _traffic(wl, storage):
-    """Measured DRAM bytes of one interior launch (profiles/traffic.json), or None
-    if the kernels have changed since the capture."""
+def _sources_sha(kernel):
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
     csrc = os.path.join(ROOT, "paper_2208_04088_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(wl, storage, kernel):
+    """Measured DRAM bytes of one launch of `kernel` (profiles/traffic.json), or
+    None if its sources have changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            t = json.load(f)
-        h = hashlib.sha256()
-        for name in ("lbm_kernels.cu", "lbm_device.cuh"):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
-        sha = h.hexdigest()[:16]
-        if sha != t.get("kernels_sha256_16"):
+            t = json.load(f)[kernel]
+        if t.get("sources_sha256_16") != _sources_sha(kernel):
             return None
         e = t[wl.name][storage]
         return float(e["dram_read"] + e["dram_write"])
@@ -216,8 +225,9 @@ def _traffic(wl, storage):
 
 
 def run_profile(args):
-    """A short run for ncu captures: --profile N direct-launch steps of the
-    workload (no graphs, no timing events), then exit."""
+    """A short run for ncu captures: --profile N steps of the workload through
+    lbm_step (replayed graphs and direct launches, as a solve) and its fields,
+    then exit."""
     from paper_2208_04088_gb300 import _native as N
     import torch
     torch.cuda.set_device(0)
@@ -225,10 +235,8 @@ def run_profile(args):
     s = N.Solver(N.desc_from_workload(wl, storage=args.storage,
                                       wall_node=args.wall_values == "node",
                                       time_block=args.time_block))
-    per = s.info()["time_block"]  # steps of one direct launch
-    for _ in range(max(1, args.profile // per)):
-        s.step(per)
-    s.sync()
+    s.step(args.profile)  # as a solve does: replayed graphs, then direct launches
+    s.fields_host()
     s.close()
     print(json.dumps({"profile_steps": args.profile, "workload": wl.name,
                       "storage": args.storage}), flush=True)
@@ -458,28 +466,74 @@ def run_gpu(args):
     total_lu = nodes * wl.steps * args.steps * world
     value = total_lu / (elapsed_ms * 1e-3) / 1e9
 
-    # timed region 2 (the kernel durations): the same solves with every
-    # interior and boundary launch bracketed by CUDA events on its own stream
-    # (library timing mode: direct launches, boundary kernel on its side stream)
+    # timed region 2 (the kernel durations): with every launch bracketed by
+    # CUDA events on its own stream (library timing mode: direct launches).
+    # One step per launch: the whole solves, interior and boundary kernels.
+    # Temporally blocked: the solves' blocked launches (a multiple of the block).
+    tblock = int(info0["time_block"])
     n_timed = max(1, min(args.steps, args.timing_solves))
     solver.set_timing(True)
     solver.timing()  # clear
     barrier()
     start.record(stream)
     for _ in range(n_timed):
-        solve()
+        if tblock > 1:
+            solver.reset()
+            solver.step(wl.steps - wl.steps % tblock)
+        else:
+            solve()
     stop.record(stream)
     barrier()
     tim = solver.timing()
     timing_ms = start.elapsed_time(stop)
     solver.set_timing(False)
-
-    # roofline of the interior kernel: algorithmic bytes per launch / mean launch time
-    bpu = info0["bytes_per_update"]
-    interior = info0["interior_nodes"]
-    mean_interior_ms = tim["interior_ms"] / max(1, tim["steps"])
-    achieved_gbs = interior * bpu / (mean_interior_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
+    clk = clocks.summary()
+    if tblock > 1:
+        # temporally blocked kernel: a launch carries tblock steps with one HBM
+        # pass, so HBM is not its bound; it is bound by instruction issue.  The
+        # roofline is FP32 arithmetic: the algorithmic operations of one
+        # lattice update (collision on the raw moments and displacement update,
+        # FMA = 2) against 152 SMs x 128 FP32 lanes x 2 x the measured SM clock.
+        n_launch = max(1, tim["steps"] // tblock)
+        mean_launch_ms = tim["interior_ms"] / n_launch
+        lu_per_launch = nodes * tblock
+        achieved = lu_per_launch * FLOPS_PER_UPDATE / (mean_launch_ms * 1e-3) / 1e12
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak,
+                    "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage, "k_wave"),
+                    "kernel": "k_wave", "steps_per_launch": tblock,
+                    "flops_per_update": FLOPS_PER_UPDATE, "updates_per_launch": lu_per_launch,
+                    "mean_launch_ms": mean_launch_ms,
+                    "peak_kind": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured)",
+                    "hbm_algorithmic_gbs": nodes * info0["bytes_per_update"] / (mean_launch_ms * 1e-3) / 1e9,
+                    "hbm_peak_gbs": peak,
+                    "timing": (f"events around every blocked launch over {n_timed} solves "
+                               f"({tim['steps']} steps) in timing mode; that pass ran at "
+                               f"{timing_ms / max(1, tim['steps']) * 1e3:.1f} us/step vs "
+                               f"{elapsed_ms / args.steps / wl.steps * 1e3:.1f} us/step "
+                               "for the graph-replayed value")}
+    else:
+        # one step per launch: the interior kernel is HBM-bound; algorithmic
+        # bytes per launch / mean launch time
+        bpu = info0["bytes_per_update"]
+        interior = info0["interior_nodes"]
+        mean_interior_ms = tim["interior_ms"] / max(1, tim["steps"])
+        achieved_gbs = interior * bpu / (mean_interior_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak,
+                    "unit": "GB/s", "frac": achieved_gbs / peak,
+                    "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage, "k_interior"),
+                    "kernel": "k_interior",
+                    "bytes_per_update": bpu, "updates_per_launch": interior,
+                    "mean_launch_ms": mean_interior_ms, "peak_kind": peak_kind,
+                    "boundary_kernel_ms_per_step": tim["boundary_ms"] / max(1, tim["steps"]),
+                    "timing": (f"events around every launch over {n_timed} solves "
+                               f"({tim['steps']} steps) in timing mode; that pass ran at "
+                               f"{timing_ms / n_timed / wl.steps * 1e3:.1f} us/step vs "
+                               f"{elapsed_ms / args.steps / wl.steps * 1e3:.1f} us/step "
+                               "for the graph-replayed value")}
 
     # end to end through the public API from host buffers: create (host tables
     # -> device), all steps, fields -> pinned host buffers, destroy
@@ -539,19 +593,9 @@ def run_gpu(args):
                               f"{(2 * 9 * esz + 16) * wl.nx * wl.ny / 1e6:.0f} MB)"
                               if (2 * 9 * esz + 16) * wl.nx * wl.ny > 129e6 else
                               "working set fits in L2; no flush inside a solve")},
-            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak,
-                         "unit": "GB/s", "frac": achieved_gbs / peak,
-                         "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage),
-                         "kernel": "k_interior",
-                         "bytes_per_update": bpu, "updates_per_launch": interior,
-                         "mean_launch_ms": mean_interior_ms, "peak_kind": peak_kind,
-                         "boundary_kernel_ms_per_step": tim["boundary_ms"] / max(1, tim["steps"]),
-                         "timing": (f"events around every launch over {n_timed} solves "
-                                    f"({tim['steps']} steps) in timing mode; that pass ran at "
-                                    f"{timing_ms / n_timed / wl.steps * 1e3:.1f} us/step vs "
-                                    f"{elapsed_ms / args.steps / wl.steps * 1e3:.1f} us/step "
-                                    "for the graph-replayed value")},
-            "clocks": clocks.summary(),
+            "roofline": roofline,
+            "time_block": tblock,
+            "clocks": clk,
             "gpu_launches": int(launches),
             "e2e": e2e,
             "cpu_baseline": cpu,

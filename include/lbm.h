@@ -139,7 +139,7 @@ typedef struct {
     int32_t storage;   /* lbm_storage */
     int32_t wall_values; /* lbm_wall_values */
     int32_t time_block;  /* time steps fused into one kernel launch:
-                            0  library default (one launch per step)
+                            0  library default (LBM_TIME_BLOCK where supported, else 1)
                             1  one launch per step (bulk and boundary-list kernels)
                             LBM_TIME_BLOCK  temporal blocking: each launch carries
                                LBM_TIME_BLOCK steps of a strip of the lattice in

@@ -26,7 +26,7 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct Layout {
     size_t f0, f1, ucomp, cls, bnodes, blinks, bcs, rho, status, time, stage, probe, probe_idx,
-        nw, total;
+        nw, wave_tab, total;
 };
 
 // Steps per launch for a description: the temporally blocked kernel needs FP32
@@ -35,8 +35,9 @@ struct Layout {
 int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
     const bool ok = d.storage == LBM_F32 && u.lam == u.mu && t.nx >= kWaveC &&
                     t.bnodes.size() < (size_t(1) << 28);
+    if (d.time_block == 1) return 1;
     if (d.time_block == LBM_TIME_BLOCK) return ok ? kWaveK : 0;
-    return 1;  // the library default: one step per launch
+    return ok ? kWaveK : 1;  // the library default: blocked where it applies
 }
 
 Layout layout(const Tables &t, int storage, bool grad, int block) {
@@ -64,6 +65,7 @@ Layout layout(const Tables &t, int storage, bool grad, int block) {
     l.probe = take(7 * (size_t)kMaxProbe * sizeof(float));
     l.probe_idx = take((size_t)kMaxProbe * sizeof(int32_t));
     l.nw = block > 1 ? take(plane * sizeof(uint64_t)) : 0;
+    l.wave_tab = block > 1 ? take(wave_table_entries(t.nx, t.ny) * sizeof(int4)) : 0;
     l.total = o;
     return l;
 }
@@ -247,6 +249,7 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
     S.probe = reinterpret_cast<float *>(b + lay.probe);
     S.probe_idx = reinterpret_cast<int32_t *>(b + lay.probe_idx);
     S.nw = h->block > 1 ? reinterpret_cast<uint64_t *>(b + lay.nw) : nullptr;
+    S.wave_tab = h->block > 1 ? reinterpret_cast<int4 *>(b + lay.wave_tab) : nullptr;
 
     auto fail = [&](cudaError_t err, const char *where) {
         lbm_status s = cuda_fail(err, where);
@@ -274,7 +277,7 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
             }
             h->block = 1;  // default: fall back to one step per launch
         } else {
-            e = wave_prepare(h->L, S, &h->wave, h->stream);
+            e = wave_prepare(h->tab, h->L, S, &h->wave, h->stream);
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -112,6 +112,7 @@ struct DevState {
     float *probe = nullptr;           // probe staging [7][max_probe]
     int32_t *probe_idx = nullptr;
     uint64_t *nw = nullptr;           // per-node words of the temporally blocked kernel
+    int4 *wave_tab = nullptr;         // blocks of a temporally blocked launch
 };
 
 constexpr int kMaxProbe = 4096;
@@ -148,14 +149,20 @@ struct WaveMaps {
     CUtensorMap f[2];  // the two distribution buffers, [9][ny][pitch] FP32
     CUtensorMap nw;    // node words [ny][pitch]
     CUtensorMap u;     // displacement records [ny][pitch] float4
-    int nstrips = 0, nseg = 0, H = 0;
+    int nblocks = 0;
 };
 
 bool wave_supported(const Lattice &L);
 size_t wave_smem_bytes();
-// Builds the node words from the class and boundary tables and the TMA
-// descriptors; S.nw must be allocated (8 bytes per node of the pitched plane).
-cudaError_t wave_prepare(const Lattice &L, const DevState &S, WaveMaps *m, cudaStream_t s);
+// Upper bound of the blocks of one launch (entries of S.wave_tab).
+size_t wave_table_entries(int nx, int ny);
+// The blocks of one launch for a device with `sms` SMs: (X0, Y0, rows, has_boundary).
+std::vector<int4> wave_plan(const Tables &t, int sms);
+// Builds the node words from the class and boundary tables, the TMA
+// descriptors and the block table; S.nw (8 bytes per node of the pitched
+// plane) and S.wave_tab must be allocated.
+cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, WaveMaps *m,
+                         cudaStream_t s);
 // kWaveK steps from buffer `cur` into buffer cur ^ 1; the first of them is
 // step `toff` after *S.time.
 cudaError_t launch_wave(const Lattice &L, const DevState &S, const WaveMaps &m, int cur, int toff,

@@ -23,8 +23,11 @@
 // cooperative boundary kernel.  The rules are explicitly rounded and the
 // moments formed in one order, so every stored value is bit-identical to the
 // one-step path.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
+#include <vector>
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -216,16 +219,17 @@ __device__ __forceinline__ void simple_pull(const Rows &ld, uint64_t nw,
     }
 }
 
-// One launch: kWaveK steps of every material node.  Block b handles strip
-// b % nstrips (core columns [X0, X0 + kWaveW)) and row segment b / nstrips
-// (core rows [Y0, Y0 + H)).  Each warp computes one level of one 32-column
-// chunk of the ring (ring column c is lattice column X0 - kWaveK + c).
+// One launch: kWaveK steps of every material node.  Block b handles the
+// region tab[b] = (X0, Y0, rows, has_boundary): core columns [X0, X0 +
+// kWaveW), core rows [Y0, Y0 + rows); has_boundary says whether a boundary
+// node lies in the region or its halo.  Each warp computes one level of one
+// 32-column chunk of the ring (ring column c is lattice column X0 - kWaveK + c).
 __global__ void __launch_bounds__(kThreads, 1)
     k_wave(const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tnw,
            const __grid_constant__ CUtensorMap tu, float *__restrict__ dst,
            float4 *__restrict__ uc, const BLink *__restrict__ blinks,
            const BCDev *__restrict__ bcs, Lattice L, const int64_t *__restrict__ time, int toff,
-           int nstrips, int H, uint32_t *__restrict__ status) {
+           const int4 *__restrict__ tab, uint32_t *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char sm[];
     float *in = reinterpret_cast<float *>(sm + kOffIn);
     float *lev = reinterpret_cast<float *>(sm + kOffLev);
@@ -244,9 +248,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = tid >> 5;
     const int lv = (warp >> 2) + 1;  // time level of this thread (warp-uniform)
     const int c = ((((warp & 3) - (warp >> 2)) & 3) << 5) | (tid & 31);
-    const int X0 = (int)(blockIdx.x % (unsigned)nstrips) * kW;
-    const int Y0 = (int)(blockIdx.x / (unsigned)nstrips) * H;
-    const int Hs = min(H, L.ny - Y0);
+    const int4 region = tab[blockIdx.x];
+    const int X0 = region.x, Y0 = region.y, Hs = region.z;
     const int xin = X0 - kK;     // lattice column of ring column 0
     const int y_in0 = Y0 - kK;   // lattice row of input row index 0
     const int j_last = Hs - 1 + 2 * kK;
@@ -291,121 +294,143 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int pmask = lv == 1 ? kNI - 1 : 3;
     float *own_base = lev + (size_t)(lv - 1) * 4 * kRowF;  // unused by level kWaveK
 
-    for (int n = 0; n < nsweep; ++n) {
-        if (tid == 0 && n + kD + 2 <= j_last && ok) {
-            // order the block's earlier shared-memory accesses before the copy
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(n + kD + 2);
-            j_issued = n + kD + 2;
-        }
-        const int y = y_in0 + 1 + n - 2 * (lv - 1);
-        if (y >= lo && y <= hi) {  // warp-uniform: one level per warp
-            const int j = y - y_in0;
-            const int ju = j % kNU;
-            const uint64_t nw = col_live ? nwr[(size_t)ju * kC + c] : 0ull;
-            const uint32_t cl = (uint32_t)(nw & 3u);
-            const float *rm = prev_base + (size_t)((j - 1) & pmask) * kRowF;
-            const float *r0 = prev_base + (size_t)(j & pmask) * kRowF;
-            const float *rp = prev_base + (size_t)((j + 1) & pmask) * kRowF;
-            float *own = own_base + (size_t)(j & 3) * kRowF;
-            const int64_t krow = (int64_t)y * L.pitch + xin;  // lattice index of ring column 0
-            const bool core_row = y >= Y0 && y < Y0 + Hs;
-            const bool simple_b = cl == kBoundary && ((nw >> 34) & 1u);
-            if (cl == kInterior || simple_b) {
-                float f[9];
-                float dr, jx, jy;
-                if (cl == kInterior) {
-                    f[0] = r0[c];
-                    f[1] = r0[kC + c - 1];
-                    f[2] = rm[2 * kC + c];
-                    f[3] = r0[3 * kC + c + 1];
-                    f[4] = rp[4 * kC + c];
-                    f[5] = rm[5 * kC + c - 1];
-                    f[6] = rm[6 * kC + c + 1];
-                    f[7] = rp[7 * kC + c + 1];
-                    f[8] = rp[8 * kC + c - 1];
-                } else {
-                    simple_pull(Rows{rm, r0, rp, c}, nw, bcs, tb, L, f);
-                }
-                collide(f, L.fx, L.fy, L, dr, jx, jy);
-                if (lv < kK) {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) own[i * kC + c] = f[i];
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) dst[i * L.plane + krow + c] = f[i];
-                }
-                if (core_row && c >= kK && c < kC - kK) {
-                    float4 *up = ur + (size_t)ju * kW + (c - kK);
-                    float4 w = *up;
-                    integrate_u_value(w, jx, jy, L.rho0 + dr);
-                    if (lv < kK) {
-                        *up = w;
-                    } else {
-                        uc[krow + c] = w;
-                        flag_nonfinite(status, dr, jx, jy);
-                    }
-                }
+    // The sweep, compiled twice: with the boundary updates, and without them
+    // for regions that hold no boundary node (their interior update is then
+    // scheduled on its own).
+    auto sweep = [&](auto with_boundary) {
+        constexpr bool kB = decltype(with_boundary)::value;
+        for (int n = 0; n < nsweep; ++n) {
+            if (tid == 0 && n + kD + 2 <= j_last && ok) {
+                // order the block's earlier shared-memory accesses before the copy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(n + kD + 2);
+                j_issued = n + kD + 2;
             }
-            // the other boundary nodes of the warp (curved walls, corners): eight
-            // lanes each, the update of the cooperative boundary kernel (four
-            // nodes per pass)
-            const unsigned bmask = __ballot_sync(0xffffffffu, cl == kBoundary && !simple_b);
-            if (bmask) {  // warp-uniform
-                const int lane = tid & 31, grp = lane >> 3, kdir = (lane & 7) + 1;
-                const bool lane0 = kdir == 1;  // lane 0 of the group stores f_0 and u
-                unsigned rem = bmask;
-                while (rem) {
-                    // group g takes the g-th remaining node; spare groups redo the
-                    // first one and store nothing
-                    unsigned r = rem;
-                    for (int q = 0; q < grp; ++q) r &= r - 1;
-                    const bool live = r != 0;
-                    const int src = __ffs(live ? r : rem) - 1;
-                    for (int q = 0; q < 4; ++q) rem &= rem - 1;
-                    const uint64_t wb = __shfl_sync(0xffffffffu, nw, src);
-                    const int cb = (c & ~31) + src;
-                    const bool simple = (wb >> 34) & 1u;
-                    const uint32_t hi = (uint32_t)(wb >> 35);
-                    const BLink sl = simple_link(hi);
-                    const BLink *lrec = blinks + (int64_t)hi * 8;
-                    auto link = [&](int i) { return simple ? sl : lrec[i - 1]; };
-                    float f0;
-                    const float fk = boundary8_pull(Rows{rm, r0, rp, cb}, nw_mask(wb, 2),
-                                                    nw_mask(wb, 10), nw_mask(wb, 18),
-                                                    nw_mask(wb, 26), kdir, link, bcs, tb, L, f0);
-                    float fr, jx, jy, m00;
-                    const float mine =
-                        boundary8_collide(fk, f0, kdir, L.fx, L.fy, L, fr, jx, jy, m00);
-                    if (live) {
-                        if (lv < kK) {
-                            own[kdir * kC + cb] = mine;
-                            if (lane0) own[cb] = fr;
+            const int y = y_in0 + 1 + n - 2 * (lv - 1);
+            if (y >= lo && y <= hi) {  // warp-uniform: one level per warp
+                const int j = y - y_in0;
+                const int ju = j % kNU;
+                const uint64_t nw = col_live ? nwr[(size_t)ju * kC + c] : 0ull;
+                const uint32_t cl = (uint32_t)(nw & 3u);
+                const float *rm = prev_base + (size_t)((j - 1) & pmask) * kRowF;
+                const float *r0 = prev_base + (size_t)(j & pmask) * kRowF;
+                const float *rp = prev_base + (size_t)((j + 1) & pmask) * kRowF;
+                float *own = own_base + (size_t)(j & 3) * kRowF;
+                const int64_t krow = (int64_t)y * L.pitch + xin;  // lattice index of ring column 0
+                const bool core_row = y >= Y0 && y < Y0 + Hs;
+                // the row's update, compiled with and without the boundary
+                // updates; a warp takes the second unless its row holds a
+                // boundary node, so rows inside the material run the plain
+                // interior update
+                auto row = [&](auto with_boundary_row) {
+                    constexpr bool kR = decltype(with_boundary_row)::value;
+                    const bool simple_b = kR && cl == kBoundary && ((nw >> 34) & 1u);
+                    if (cl == kInterior || simple_b) {
+                        float f[9];
+                        float dr, jx, jy;
+                        if (!kR || cl == kInterior) {
+                            f[0] = r0[c];
+                            f[1] = r0[kC + c - 1];
+                            f[2] = rm[2 * kC + c];
+                            f[3] = r0[3 * kC + c + 1];
+                            f[4] = rp[4 * kC + c];
+                            f[5] = rm[5 * kC + c - 1];
+                            f[6] = rm[6 * kC + c + 1];
+                            f[7] = rp[7 * kC + c + 1];
+                            f[8] = rp[8 * kC + c - 1];
                         } else {
-                            dst[kdir * L.plane + krow + cb] = mine;
-                            if (lane0) dst[krow + cb] = fr;
+                            simple_pull(Rows{rm, r0, rp, c}, nw, bcs, tb, L, f);
                         }
-                        if (lane0 && core_row && cb >= kK && cb < kC - kK) {
-                            float4 *up = ur + (size_t)ju * kW + (cb - kK);
+                        collide(f, L.fx, L.fy, L, dr, jx, jy);
+                        if (lv < kK) {
+        #pragma unroll
+                            for (int i = 0; i < 9; ++i) own[i * kC + c] = f[i];
+                        } else {
+        #pragma unroll
+                            for (int i = 0; i < 9; ++i) dst[i * L.plane + krow + c] = f[i];
+                        }
+                        if (core_row && c >= kK && c < kC - kK) {
+                            float4 *up = ur + (size_t)ju * kW + (c - kK);
                             float4 w = *up;
-                            integrate_u_value(w, jx, jy, L.rho0 + m00);
+                            integrate_u_value(w, jx, jy, L.rho0 + dr);
                             if (lv < kK) {
                                 *up = w;
                             } else {
-                                uc[krow + cb] = w;
-                                flag_nonfinite(status, m00, jx, jy);
+                                uc[krow + c] = w;
+                                flag_nonfinite(status, dr, jx, jy);
                             }
                         }
                     }
-                }
+                    // the other boundary nodes of the warp (curved walls, corners): eight
+                    // lanes each, the update of the cooperative boundary kernel (four
+                    // nodes per pass)
+                    const unsigned bmask =
+                        kR ? __ballot_sync(0xffffffffu, cl == kBoundary && !simple_b) : 0u;
+                    if (kR && bmask) {  // warp-uniform
+                        const int lane = tid & 31, grp = lane >> 3, kdir = (lane & 7) + 1;
+                        const bool lane0 = kdir == 1;  // lane 0 of the group stores f_0 and u
+                        unsigned rem = bmask;
+                        while (rem) {
+                            // group g takes the g-th remaining node; spare groups redo the
+                            // first one and store nothing
+                            unsigned r = rem;
+                            for (int q = 0; q < grp; ++q) r &= r - 1;
+                            const bool live = r != 0;
+                            const int src = __ffs(live ? r : rem) - 1;
+                            for (int q = 0; q < 4; ++q) rem &= rem - 1;
+                            const uint64_t wb = __shfl_sync(0xffffffffu, nw, src);
+                            const int cb = (c & ~31) + src;
+                            const bool simple = (wb >> 34) & 1u;
+                            const uint32_t hi = (uint32_t)(wb >> 35);
+                            const BLink sl = simple_link(hi);
+                            const BLink *lrec = blinks + (int64_t)hi * 8;
+                            auto link = [&](int i) { return simple ? sl : lrec[i - 1]; };
+                            float f0;
+                            const float fk = boundary8_pull(Rows{rm, r0, rp, cb}, nw_mask(wb, 2),
+                                                            nw_mask(wb, 10), nw_mask(wb, 18),
+                                                            nw_mask(wb, 26), kdir, link, bcs, tb, L, f0);
+                            float fr, jx, jy, m00;
+                            const float mine =
+                                boundary8_collide(fk, f0, kdir, L.fx, L.fy, L, fr, jx, jy, m00);
+                            if (live) {
+                                if (lv < kK) {
+                                    own[kdir * kC + cb] = mine;
+                                    if (lane0) own[cb] = fr;
+                                } else {
+                                    dst[kdir * L.plane + krow + cb] = mine;
+                                    if (lane0) dst[krow + cb] = fr;
+                                }
+                                if (lane0 && core_row && cb >= kK && cb < kC - kK) {
+                                    float4 *up = ur + (size_t)ju * kW + (cb - kK);
+                                    float4 w = *up;
+                                    integrate_u_value(w, jx, jy, L.rho0 + m00);
+                                    if (lv < kK) {
+                                        *up = w;
+                                    } else {
+                                        uc[krow + cb] = w;
+                                        flag_nonfinite(status, m00, jx, jy);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                };
+                if (kB && __ballot_sync(0xffffffffu, cl == kBoundary))
+                    row(std::true_type{});
+                else
+                    row(std::false_type{});
             }
+            if (tid == 0 && n + 3 <= j_last && ok) {
+                ok = wait_row(n + 3);
+                if (!ok) last_waited = n + 2;
+            }
+            __syncthreads();
         }
-        if (tid == 0 && n + 3 <= j_last && ok) {
-            ok = wait_row(n + 3);
-            if (!ok) last_waited = n + 2;
-        }
-        __syncthreads();
-    }
+    };
+    if (region.w)
+        sweep(std::true_type{});
+    else
+        sweep(std::false_type{});
     if (tid == 0 && !ok) {
         // a copy did not land in time: flag it, and give the copies still in
         // flight a bounded chance to land before the block's shared memory goes
@@ -491,13 +516,95 @@ bool encode(CUtensorMap *map, CUtensorMapDataType type, cuuint32_t rank, void *b
 
 }  // namespace
 
+size_t wave_table_entries(int nx, int ny) {
+    const size_t strips = (size_t)(nx + kW - 1) / kW;
+    return strips * (size_t)((ny + 4 * kK - 1) / (4 * kK));
+}
+
+// The blocks of one launch.  Every strip of kWaveW columns is cut into row
+// segments of at least 4 kWaveK rows; a segment sweeps 3 kWaveK - 3 rows more
+// than it owns.  A strip that a wall column runs through (boundary nodes in at
+// least half of its rows, e.g. a box edge) updates that wall in every row and
+// level, which makes each of its rows kWallRowCost times as long (measured on
+// GB300 for the 2048^2 crack).  The segment counts of the plain and the wall
+// strips are chosen to minimise the longest block with all blocks in one wave
+// on `sms` SMs (one block per SM).  Each entry also says whether a boundary
+// node lies in the block's region or halo.
+constexpr double kWallRowCost = 2.3;
+
+std::vector<int4> wave_plan(const Tables &t, int sms) {
+    const int nx = t.nx, ny = t.ny;
+    const int nstrips = (nx + kW - 1) / kW;
+    std::vector<int64_t> per_strip(nstrips, 0);
+    // boundary rows seen by each strip's region (core and halo columns)
+    std::vector<std::vector<int>> rows(nstrips);
+    for (const BNode &b : t.bnodes) {
+        per_strip[b.x / kW] += 1;
+        const int s_lo = std::max(0, (b.x - kK) / kW), s_hi = std::min(nstrips - 1, (b.x + kK) / kW);
+        for (int sx = s_lo; sx <= s_hi; ++sx) {
+            const int X0 = sx * kW;
+            if (b.x >= X0 - kK && b.x < X0 + kW + kK) rows[sx].push_back(b.y);
+        }
+    }
+    for (auto &r : rows) std::sort(r.begin(), r.end());
+    std::vector<char> wall(nstrips);
+    int n_wall = 0;
+    for (int sx = 0; sx < nstrips; ++sx) {
+        wall[sx] = 2 * per_strip[sx] >= ny;
+        n_wall += wall[sx];
+    }
+    const int n_plain = nstrips - n_wall;
+    auto seg_rows = [&](int segs) { return std::max((ny + segs - 1) / segs, 4 * kK); };
+    auto cost = [&](int segs, double per_row) {
+        return (seg_rows(segs) + 3 * kK - 3) * per_row;
+    };
+    // segments per plain strip p and per wall strip w
+    int best_p = 1, best_w = 1;
+    double best = 1e300;
+    for (int p = 1; p <= std::max(1, ny / (4 * kK)); ++p) {
+        const int left = sms - n_plain * p;
+        int w = n_wall ? (left > 0 ? left / n_wall : 0) : 1;
+        if (n_wall && w < 1) {
+            if (p > 1) break;
+            w = 1;
+        }
+        const int blocks = n_plain * p + n_wall * w;
+        const int waves = (blocks + sms - 1) / sms;
+        const double tp = n_plain ? cost(p, 1.0) : 0.0;
+        const double tw = n_wall ? cost(w, kWallRowCost) : 0.0;
+        const double tmax = std::max(tp, tw) * waves;
+        if (tmax < best) {
+            best = tmax;
+            best_p = p;
+            best_w = w;
+        }
+    }
+    std::vector<int4> out;
+    for (int sx = 0; sx < nstrips; ++sx) {
+        int segs = wall[sx] ? best_w : best_p;
+        const int H = seg_rows(segs);
+        segs = (ny + H - 1) / H;
+        for (int g = 0; g < segs; ++g) {
+            const int Y0 = g * H, Hs = std::min(H, ny - Y0);
+            const auto &r = rows[sx];
+            const auto it = std::lower_bound(r.begin(), r.end(), Y0 - kK);
+            const int has = (it != r.end() && *it < Y0 + Hs + kK) ? 1 : 0;
+            out.push_back(make_int4(sx * kW, Y0, Hs, has));
+        }
+    }
+    // heavy blocks first
+    std::stable_sort(out.begin(), out.end(), [](const int4 &a, const int4 &b) { return a.w > b.w; });
+    return out;
+}
+
 size_t wave_smem_bytes() { return kSmem; }
 
 bool wave_supported(const Lattice &L) {
     return L.nx >= kC && L.ny >= 1 && L.nb < (1 << 28) && !L.grad && encoder() != nullptr;
 }
 
-cudaError_t wave_prepare(const Lattice &L, const DevState &S, WaveMaps *m, cudaStream_t s) {
+cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, WaveMaps *m,
+                         cudaStream_t s) {
     const int64_t n = L.plane;
     k_nw_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S.cls, S.nw, n);
     if (L.nb > 0)
@@ -522,28 +629,23 @@ cudaError_t wave_prepare(const Lattice &L, const DevState &S, WaveMaps *m, cudaS
         return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute(k_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
-    // segments: at most one block per SM (one block fits an SM), each at least
-    // 4 kWaveK rows high; a second partial wave would double the launch time
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
-    m->nstrips = (L.nx + kW - 1) / kW;
-    int nseg = sms / m->nstrips;
-    nseg = nseg < 1 ? 1 : nseg;
-    int H = (L.ny + nseg - 1) / nseg;
-    if (H < 4 * kK) H = 4 * kK;
-    m->H = H;
-    m->nseg = (L.ny + H - 1) / H;
-    return cudaSuccess;
+    const std::vector<int4> plan = wave_plan(t, sms);
+    m->nblocks = (int)plan.size();
+    if (plan.empty() || plan.size() > wave_table_entries(t.nx, t.ny)) return cudaErrorInvalidValue;
+    // pageable source: the copy is staged before the call returns
+    return cudaMemcpyAsync(S.wave_tab, plan.data(), plan.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice, s);
 }
 
 cudaError_t launch_wave(const Lattice &L, const DevState &S, const WaveMaps &m, int cur, int toff,
                         cudaStream_t s) {
-    const unsigned grid = (unsigned)(m.nstrips * m.nseg);
-    k_wave<<<grid, kThreads, kSmem, s>>>(m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]),
-                                         S.ucomp, S.blinks, S.bcs, L, S.time, toff, m.nstrips,
-                                         m.H, S.status);
+    k_wave<<<(unsigned)m.nblocks, kThreads, kSmem, s>>>(
+        m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]), S.ucomp, S.blinks, S.bcs, L,
+        S.time, toff, S.wave_tab, S.status);
     return cudaGetLastError();
 }
 

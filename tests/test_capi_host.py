@@ -106,16 +106,20 @@ def test_physical_units_are_accepted():
 
 
 def test_time_block_selection_and_validation():
-    """lbm_desc.time_block: 0 (default, one step per launch), 1 or
+    """lbm_desc.time_block: 0 (default: blocked where supported), 1 (one step per launch) or
     LBM_TIME_BLOCK (temporal blocking, FP32 storage, lambda = mu, nx >= 128);
-    the blocked form adds the 8-byte node words to the workspace."""
+    the blocked form adds the 8-byte node words and its block table to the
+    workspace."""
     wl = W.hole_plate(256, 128, 16.0, 0)
     plane = 256 * 128
     one = N.lbm_workspace_size(_desc(wl, time_block=1))
     blk = N.lbm_workspace_size(_desc(wl, time_block=N.LBM_TIME_BLOCK))
     dflt = N.lbm_workspace_size(_desc(wl))
-    assert blk - one == (8 * plane + 255) // 256 * 256
-    assert dflt == one
+    # node words (8 bytes per node) and the block table (16 bytes per strip
+    # and 32-row segment of 112-column strips)
+    table = ((256 + 111) // 112) * ((128 + 31) // 32) * 16
+    assert blk - one == (8 * plane + 255) // 256 * 256 + (table + 255) // 256 * 256
+    assert dflt == blk
     # the default falls back to one step per launch where blocking is unsupported
     assert N.lbm_workspace_size(_desc(wl, storage="f16")) == \
         N.lbm_workspace_size(_desc(wl, storage="f16", time_block=1))
