@@ -299,6 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // scheduled on its own).
     auto sweep = [&](auto with_boundary) {
         constexpr bool kB = decltype(with_boundary)::value;
+        int ju_next = ((1 - 2 * (lv - 1)) % kNU + kNU) % kNU;
         for (int n = 0; n < nsweep; ++n) {
             if (tid == 0 && n + kD + 2 <= j_last && ok) {
                 // order the block's earlier shared-memory accesses before the copy
@@ -307,16 +308,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 j_issued = n + kD + 2;
             }
             const int y = y_in0 + 1 + n - 2 * (lv - 1);
+            const int j = y - y_in0;
+            // ring rows of this step, advanced from the previous one: node-word and
+            // displacement rings (mod kNU), level rings (mod 4 or kNI)
+            const int ju = ju_next;
+            ju_next = ju + 1 == kNU ? 0 : ju + 1;
             if (y >= lo && y <= hi) {  // warp-uniform: one level per warp
-                const int j = y - y_in0;
-                const int ju = j % kNU;
-                const uint64_t nw = col_live ? nwr[(size_t)ju * kC + c] : 0ull;
+                const uint64_t nw = col_live ? nwr[ju * kC + c] : 0ull;
                 const uint32_t cl = (uint32_t)(nw & 3u);
-                const float *rm = prev_base + (size_t)((j - 1) & pmask) * kRowF;
-                const float *r0 = prev_base + (size_t)(j & pmask) * kRowF;
-                const float *rp = prev_base + (size_t)((j + 1) & pmask) * kRowF;
-                float *own = own_base + (size_t)(j & 3) * kRowF;
-                const int64_t krow = (int64_t)y * L.pitch + xin;  // lattice index of ring column 0
+                const float *rm = prev_base + ((j - 1) & pmask) * kRowF;
+                const float *r0 = prev_base + (j & pmask) * kRowF;
+                const float *rp = prev_base + ((j + 1) & pmask) * kRowF;
+                float *own = own_base + (j & 3) * kRowF;
                 const bool core_row = y >= Y0 && y < Y0 + Hs;
                 // the row's update, compiled with and without the boundary
                 // updates; a warp takes the second unless its row holds a
@@ -347,16 +350,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                             for (int i = 0; i < 9; ++i) own[i * kC + c] = f[i];
                         } else {
         #pragma unroll
-                            for (int i = 0; i < 9; ++i) dst[i * L.plane + krow + c] = f[i];
+                            for (int i = 0; i < 9; ++i) dst[i * L.plane + ((int64_t)y * L.pitch + xin) + c] = f[i];
                         }
                         if (core_row && c >= kK && c < kC - kK) {
-                            float4 *up = ur + (size_t)ju * kW + (c - kK);
+                            float4 *up = ur + ju * kW + (c - kK);
                             float4 w = *up;
                             integrate_u_value(w, jx, jy, L.rho0 + dr);
                             if (lv < kK) {
                                 *up = w;
                             } else {
-                                uc[krow + c] = w;
+                                uc[(int64_t)y * L.pitch + xin + c] = w;
                                 flag_nonfinite(status, dr, jx, jy);
                             }
                         }
@@ -397,17 +400,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     own[kdir * kC + cb] = mine;
                                     if (lane0) own[cb] = fr;
                                 } else {
-                                    dst[kdir * L.plane + krow + cb] = mine;
-                                    if (lane0) dst[krow + cb] = fr;
+                                    dst[kdir * L.plane + ((int64_t)y * L.pitch + xin) + cb] = mine;
+                                    if (lane0) dst[(int64_t)y * L.pitch + xin + cb] = fr;
                                 }
                                 if (lane0 && core_row && cb >= kK && cb < kC - kK) {
-                                    float4 *up = ur + (size_t)ju * kW + (cb - kK);
+                                    float4 *up = ur + ju * kW + (cb - kK);
                                     float4 w = *up;
                                     integrate_u_value(w, jx, jy, L.rho0 + m00);
                                     if (lv < kK) {
                                         *up = w;
                                     } else {
-                                        uc[krow + cb] = w;
+                                        uc[(int64_t)y * L.pitch + xin + cb] = w;
                                         flag_nonfinite(status, m00, jx, jy);
                                     }
                                 }
@@ -517,20 +520,28 @@ bool encode(CUtensorMap *map, CUtensorMapDataType type, cuuint32_t rank, void *b
 }  // namespace
 
 size_t wave_table_entries(int nx, int ny) {
+    // the plan makes at most max(number of SMs, strips) blocks; 4096 bounds the
+    // SMs of any device
+    (void)ny;
     const size_t strips = (size_t)(nx + kW - 1) / kW;
-    return strips * (size_t)((ny + 4 * kK - 1) / (4 * kK));
+    return std::max<size_t>(strips, 4096) + strips;
 }
 
 // The blocks of one launch.  Every strip of kWaveW columns is cut into row
-// segments of at least 4 kWaveK rows; a segment sweeps 3 kWaveK - 3 rows more
-// than it owns.  A strip that a wall column runs through (boundary nodes in at
-// least half of its rows, e.g. a box edge) updates that wall in every row and
-// level, which makes each of its rows kWallRowCost times as long (measured on
-// GB300 for the 2048^2 crack).  The segment counts of the plain and the wall
-// strips are chosen to minimise the longest block with all blocks in one wave
-// on `sms` SMs (one block per SM).  Each entry also says whether a boundary
-// node lies in the block's region or halo.
+// segments; a segment sweeps 3 kWaveK - 3 rows more than it owns.  The cost of
+// a block is modelled in row sweeps, measured on GB300 (2048^2 crack):
+//   - a row costs 1, or kWallRowCost in a strip that a wall column runs
+//     through (boundary nodes in at least half of its rows, e.g. a box edge:
+//     that wall is updated in every row and level);
+//   - a row in which at least a quarter of the region's columns are boundary
+//     nodes (a wall along the row: box edge, crack face) adds kWallRowPenalty,
+//     counted also when it lies in the segment's halo.
+// Segments are cut greedily against a target cost, and the smallest target for
+// which all blocks fit one wave on `sms` SMs (one block per SM) is found by
+// bisection.  Each entry also says whether a boundary node lies in the
+// block's region or halo.
 constexpr double kWallRowCost = 2.3;
+constexpr double kWallRowPenalty = 65.0;
 
 std::vector<int4> wave_plan(const Tables &t, int sms) {
     const int nx = t.nx, ny = t.ny;
@@ -546,50 +557,69 @@ std::vector<int4> wave_plan(const Tables &t, int sms) {
             if (b.x >= X0 - kK && b.x < X0 + kW + kK) rows[sx].push_back(b.y);
         }
     }
-    for (auto &r : rows) std::sort(r.begin(), r.end());
-    std::vector<char> wall(nstrips);
-    int n_wall = 0;
+    std::vector<double> row_cost(nstrips);
+    std::vector<std::vector<int>> dense(nstrips);  // rows with a wall along them, sorted
     for (int sx = 0; sx < nstrips; ++sx) {
-        wall[sx] = 2 * per_strip[sx] >= ny;
-        n_wall += wall[sx];
+        auto &r = rows[sx];
+        std::sort(r.begin(), r.end());
+        for (size_t a = 0; a < r.size();) {
+            size_t b = a;
+            while (b < r.size() && r[b] == r[a]) ++b;
+            if ((int)(b - a) * 4 >= kC) dense[sx].push_back(r[a]);
+            a = b;
+        }
+        row_cost[sx] = 2 * per_strip[sx] >= ny ? kWallRowCost : 1.0;
     }
-    const int n_plain = nstrips - n_wall;
-    auto seg_rows = [&](int segs) { return std::max((ny + segs - 1) / segs, 4 * kK); };
-    auto cost = [&](int segs, double per_row) {
-        return (seg_rows(segs) + 3 * kK - 3) * per_row;
+    // cost of the block owning rows [a, b) of strip sx
+    auto cost = [&](int sx, int a, int b) {
+        const auto &d = dense[sx];
+        const auto lo = std::lower_bound(d.begin(), d.end(), a - kK);
+        const auto hi = std::lower_bound(d.begin(), d.end(), b + kK);
+        return row_cost[sx] * (b - a + 3 * kK - 3) + kWallRowPenalty * (double)(hi - lo);
     };
-    // segments per plain strip p and per wall strip w
-    int best_p = 1, best_w = 1;
-    double best = 1e300;
-    for (int p = 1; p <= std::max(1, ny / (4 * kK)); ++p) {
-        const int left = sms - n_plain * p;
-        int w = n_wall ? (left > 0 ? left / n_wall : 0) : 1;
-        if (n_wall && w < 1) {
-            if (p > 1) break;
-            w = 1;
+    // greedy cut of strip sx against target T (every segment at least one row)
+    auto cut = [&](int sx, double T, std::vector<int> *ends) {
+        int count = 0;
+        for (int a = 0; a < ny;) {
+            int lo = a + 1, hi = ny;  // the largest b in [a + 1, ny] with cost(a, b) <= T
+            if (cost(sx, a, lo) <= T) {
+                while (lo < hi) {
+                    const int mid = lo + (hi - lo + 1) / 2;
+                    if (cost(sx, a, mid) <= T) lo = mid;
+                    else hi = mid - 1;
+                }
+            }
+            if (ends) ends->push_back(lo);
+            a = lo;
+            ++count;
         }
-        const int blocks = n_plain * p + n_wall * w;
-        const int waves = (blocks + sms - 1) / sms;
-        const double tp = n_plain ? cost(p, 1.0) : 0.0;
-        const double tw = n_wall ? cost(w, kWallRowCost) : 0.0;
-        const double tmax = std::max(tp, tw) * waves;
-        if (tmax < best) {
-            best = tmax;
-            best_p = p;
-            best_w = w;
-        }
+        return count;
+    };
+    auto blocks_for = [&](double T) {
+        int n = 0;
+        for (int sx = 0; sx < nstrips; ++sx) n += cut(sx, T, nullptr);
+        return n;
+    };
+    const int budget = std::max(sms, nstrips);
+    double hi_T = 0.0, lo_T = 0.0;
+    for (int sx = 0; sx < nstrips; ++sx) hi_T = std::max(hi_T, cost(sx, 0, ny));
+    for (int it = 0; it < 48; ++it) {
+        const double mid = 0.5 * (lo_T + hi_T);
+        if (blocks_for(mid) <= budget) hi_T = mid;
+        else lo_T = mid;
     }
     std::vector<int4> out;
     for (int sx = 0; sx < nstrips; ++sx) {
-        int segs = wall[sx] ? best_w : best_p;
-        const int H = seg_rows(segs);
-        segs = (ny + H - 1) / H;
-        for (int g = 0; g < segs; ++g) {
-            const int Y0 = g * H, Hs = std::min(H, ny - Y0);
+        std::vector<int> ends;
+        cut(sx, hi_T, &ends);
+        int Y0 = 0;
+        for (int e : ends) {
+            const int Hs = e - Y0;
             const auto &r = rows[sx];
             const auto it = std::lower_bound(r.begin(), r.end(), Y0 - kK);
             const int has = (it != r.end() && *it < Y0 + Hs + kK) ? 1 : 0;
             out.push_back(make_int4(sx * kW, Y0, Hs, has));
+            Y0 = e;
         }
     }
     // heavy blocks first

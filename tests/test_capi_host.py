@@ -115,9 +115,10 @@ def test_time_block_selection_and_validation():
     one = N.lbm_workspace_size(_desc(wl, time_block=1))
     blk = N.lbm_workspace_size(_desc(wl, time_block=N.LBM_TIME_BLOCK))
     dflt = N.lbm_workspace_size(_desc(wl))
-    # node words (8 bytes per node) and the block table (16 bytes per strip
-    # and 32-row segment of 112-column strips)
-    table = ((256 + 111) // 112) * ((128 + 31) // 32) * 16
+    # node words (8 bytes per node) and the block table (16 bytes per block;
+    # at most max(strips, 4096) + strips blocks of 112-column strips)
+    strips = (256 + 111) // 112
+    table = (max(strips, 4096) + strips) * 16
     assert blk - one == (8 * plane + 255) // 256 * 256 + (table + 255) // 256 * 256
     assert dflt == blk
     # the default falls back to one step per launch where blocking is unsupported
