@@ -348,9 +348,69 @@ lbm_status classify(const lbm_desc &d, const Units &u, Tables *t) {
     t->blinks.clear();
     t->interior = 0;
     size_t p = 0;
-    for (int32_t y = 0; y < ny; ++y)
+    // full[x] of row y: the node and its eight neighbours are all material.
+    // Formed as the AND of three horizontal 3-ANDs (rows y - 1, y, y + 1;
+    // outside the box counts as void), so most nodes are classified interior
+    // without the per-link checks below.
+    std::vector<uint8_t> h0((size_t)nx, 0), h1((size_t)nx, 0), h2((size_t)nx, 0),
+        full((size_t)nx, 0);
+    auto hrow = [&](int32_t yy, std::vector<uint8_t> &h) {
+        if (yy < 0 || yy >= ny) {
+            std::fill(h.begin(), h.end(), (uint8_t)0);
+            return;
+        }
+        const uint8_t *__restrict__ r = d.node_type + (int64_t)yy * nx;
+        uint8_t *__restrict__ o = h.data();
+        o[0] = 0;
+        o[nx - 1] = 0;
+        for (int32_t x = 1; x < nx - 1; ++x)
+            o[x] = (uint8_t)((r[x - 1] != 0) & (r[x] != 0) & (r[x + 1] != 0));
+    };
+    hrow(-1, h0);
+    hrow(0, h1);
+    for (int32_t y = 0; y < ny; ++y) {
+        hrow(y + 1, h2);
+        {
+            const uint8_t *__restrict__ a = h0.data(), *__restrict__ b = h1.data(),
+                                       *__restrict__ c = h2.data();
+            uint8_t *__restrict__ o = full.data();
+            for (int32_t x = 0; x < nx; ++x) o[x] = (uint8_t)(a[x] & b[x] & c[x]);
+        }
+        std::swap(h0, h1);
+        std::swap(h1, h2);
+        const int64_t row0 = (int64_t)y * nx;
+        uint8_t *crow = t->cls.data() + (size_t)y * t->pitch;
+        static_assert(kInterior == 1, "a full node's class is its flag");
         for (int32_t x = 0; x < nx; ++x) {
-            const int64_t node = (int64_t)y * nx + x;
+            // the run of nodes up to the next one with cut links: its full
+            // nodes are interior (one branch-free pass); any other material
+            // node of the run goes through the checks below (which reject it:
+            // it lacks a cut link towards a void or outside neighbour)
+            const int32_t xl = (p < L.size() && L[p]->node < row0 + nx)
+                                   ? (int32_t)(L[p]->node - row0) : nx;
+            if (x < xl) {
+                const uint8_t *__restrict__ fr = full.data();
+                uint8_t *__restrict__ cr = crow;
+                uint32_t cnt = 0;
+                for (int32_t q = x; q < xl; ++q) {
+                    cr[q] = fr[q];
+                    cnt += fr[q];
+                }
+                t->interior += cnt;
+                int32_t bad = xl;
+                for (int32_t q = x; q < xl; ++q)
+                    if (!full[q] && d.node_type[row0 + q]) {
+                        bad = q;
+                        break;
+                    }
+                if (bad == xl) {
+                    x = xl - 1;
+                    continue;
+                }
+                x = bad;
+                crow[x] = kVoid;
+            }
+            const int64_t node = row0 + x;
             const lbm_link *mine[kQ] = {nullptr};
             uint16_t cut = 0;
             while (p < L.size() && L[p]->node == node) {
@@ -415,6 +475,7 @@ lbm_status classify(const lbm_desc &d, const Units &u, Tables *t) {
             t->bnodes.push_back(bn);
             for (int i = 0; i < 8; ++i) t->blinks.push_back(slots[i]);
         }
+    }
     return LBM_OK;
 }
 
