@@ -40,19 +40,31 @@ METRIC = "GLUPS (giga lattice updates per second, whole job)"
 # FP32 operations of one lattice update in the temporally blocked kernel (FMA =
 # 2): raw moments 24, relaxation 26, populations 30, displacement update 11
 FLOPS_PER_UPDATE = 91
+# with lambda != mu the blocked kernel also forms each node's density (8) and
+# the source from the density gradient (10)
+FLOPS_PER_UPDATE_GRAD = 109
 # the kernel sources each kernel's recorded DRAM traffic depends on
 KERNEL_SOURCES = {"k_interior": ("lbm_kernels.cu", "lbm_device.cuh"),
                   "k_wave": ("lbm_wave.cu", "lbm_device.cuh")}
 WORKLOADS = ("crack", "plate", "batch", "serve")
 
 
-def _workload(name):
+def _workload(name, material="poisson"):
+    """The workload; material "paper" takes the paper's lambda != mu solid (the
+    crack's c_s^2/c_d^2 = 0.3611, nu = 0.2174; the plate's c_d^2/c_s^2 = 2.8)."""
+    import dataclasses
     from paper_2208_04088_gb300 import workloads as W
     if name == "crack":
-        return W.CONFIG3
-    if name == "plate":
-        return W.CONFIG2
-    raise SystemExit(f"unknown workload {name}")
+        wl = W.CONFIG3
+        lm = W.CRACK_PAPER_LAM_OVER_MU
+    elif name == "plate":
+        wl = W.CONFIG2
+        lm = W.PLATE_NONPOISSON_LAM_OVER_MU
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if material == "paper":
+        wl = dataclasses.replace(wl, lam_over_mu=lm)
+    return wl
 
 
 def _peaks():
@@ -165,7 +177,7 @@ def _cpu_baseline(wl, seconds=12.0):
 
 def run_reference(args):
     world, rank, _ = _dist()
-    wl = _workload(args.workload)
+    wl = _workload(args.workload, args.material)
     if rank != 0:
         return 0
     import oracle
@@ -231,7 +243,7 @@ def run_profile(args):
     from paper_2208_04088_gb300 import _native as N
     import torch
     torch.cuda.set_device(0)
-    wl = _workload(args.workload)
+    wl = _workload(args.workload, args.material)
     s = N.Solver(N.desc_from_workload(wl, storage=args.storage,
                                       wall_node=args.wall_values == "node",
                                       time_block=args.time_block))
@@ -418,7 +430,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     N.load(build_if_missing=False)
-    wl = _workload(args.workload)
+    wl = _workload(args.workload, args.material)
     stream = torch.cuda.Stream(device=dev)
 
     wall_node = args.wall_values == "node"
@@ -498,14 +510,15 @@ def run_gpu(args):
         n_launch = max(1, tim["steps"] // tblock)
         mean_launch_ms = tim["interior_ms"] / n_launch
         lu_per_launch = nodes * tblock
-        achieved = lu_per_launch * FLOPS_PER_UPDATE / (mean_launch_ms * 1e-3) / 1e12
+        fpu = FLOPS_PER_UPDATE if wl.lam_over_mu == 1.0 else FLOPS_PER_UPDATE_GRAD
+        achieved = lu_per_launch * fpu / (mean_launch_ms * 1e-3) / 1e12
         sm_mhz = clk.get("sm_mhz") or 2070.0
         alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak,
                     "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage, "k_wave"),
                     "kernel": "k_wave", "steps_per_launch": tblock,
-                    "flops_per_update": FLOPS_PER_UPDATE, "updates_per_launch": lu_per_launch,
+                    "flops_per_update": fpu, "updates_per_launch": lu_per_launch,
                     "mean_launch_ms": mean_launch_ms,
                     "peak_kind": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured)",
                     "hbm_algorithmic_gbs": nodes * info0["bytes_per_update"] / (mean_launch_ms * 1e-3) / 1e9,
@@ -586,6 +599,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
             "data": "synthetic",
             "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "time_steps": wl.steps,
+                       "lambda_over_mu": wl.lam_over_mu,
                        "material_nodes": nodes, "storage": args.storage + " deviations",
                        "wall_values": args.wall_values,
                        "parallelism": f"replicas x{world}",
@@ -614,6 +628,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="crack", choices=WORKLOADS)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--material", default="poisson", choices=["poisson", "paper"],
+                    help="poisson: lambda = mu (nu = 1/4); paper: the paper's lambda != mu "
+                         "solid of the workload (crack nu = 0.2174, plate c_d^2/c_s^2 = 2.8)")
     ap.add_argument("--wall-values", default="node", choices=["extrapolate", "node"],
                     help="Neumann wall values: the boundary node's own (default) or the "
                          "paper's extrapolation along the link, whose density mode grows "

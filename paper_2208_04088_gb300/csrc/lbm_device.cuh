@@ -548,21 +548,44 @@ __device__ __forceinline__ float boundary8_collide(float fk, float g0, int kdir,
     return mine;
 }
 
-// Source S = F + (mu - lambda)/rho grad rho at an interior node (central
-// differences).  `drho` holds density deviations rho - rho0, so the differences
-// do not cancel against rho0.
+// Density deviation rho - rho0 of nine populations, summed as raw_moments
+// forms m00 (so it equals moments(f).dr bit for bit).
+__device__ __forceinline__ float density_of(const float f[9]) {
+    const float a0 = (f[7] + f[4]) + f[8];
+    const float b0 = (f[3] + f[0]) + f[1];
+    const float c0 = (f[6] + f[2]) + f[5];
+    return (a0 + b0) + c0;
+}
+
+// Source S = F + (mu - lambda)/rho grad rho (Eq. sourceterm) from the density
+// deviations of the node (r0) and of its axis neighbours: central differences,
+// one-sided where one neighbour of an axis is across a wall (open flags false),
+// zero where both are.  Deviations, so the differences do not cancel against
+// rho0.  Explicitly rounded, so every kernel forms the same S.
+__device__ __forceinline__ void grad_source(float r0, float rxp, float rxm, float ryp, float rym,
+                                            bool xp, bool xm, bool yp, bool ym, const Lattice &L,
+                                            float &sx, float &sy) {
+    float gx = 0.0f, gy = 0.0f;
+    if (xp && xm) gx = rmul(0.5f, rsub(rxp, rxm));
+    else if (xp) gx = rsub(rxp, r0);
+    else if (xm) gx = rsub(r0, rxm);
+    if (yp && ym) gy = rmul(0.5f, rsub(ryp, rym));
+    else if (yp) gy = rsub(ryp, r0);
+    else if (ym) gy = rsub(r0, rym);
+    const float c = __fdiv_rn(L.mu_m_lam, radd(L.rho0, r0));
+    sx = rfma(c, gx, L.fx);
+    sy = rfma(c, gy, L.fy);
+}
+
+// Source at an interior node from a dense array of density deviations.
 __device__ __forceinline__ void source_interior(const float *__restrict__ drho, int64_t k, int pitch,
                                                 float drho_k, const Lattice &L, float &sx,
                                                 float &sy) {
     sx = L.fx;
     sy = L.fy;
-    if (L.grad) {
-        const float gx = 0.5f * (__ldg(drho + k + 1) - __ldg(drho + k - 1));
-        const float gy = 0.5f * (__ldg(drho + k + pitch) - __ldg(drho + k - pitch));
-        const float c = L.mu_m_lam / (L.rho0 + drho_k);
-        sx += c * gx;
-        sy += c * gy;
-    }
+    if (L.grad)
+        grad_source(drho_k, __ldg(drho + k + 1), __ldg(drho + k - 1), __ldg(drho + k + pitch),
+                    __ldg(drho + k - pitch), true, true, true, true, L, sx, sy);
 }
 
 // Same at a boundary node: one-sided where a neighbour is across a wall.
@@ -574,19 +597,10 @@ __device__ __forceinline__ void source_boundary(const float *__restrict__ rho, c
     if (!L.grad) return;
     const bool xp = !(b.cut & (1u << 1)), xm = !(b.cut & (1u << 3));
     const bool yp = !(b.cut & (1u << 2)), ym = !(b.cut & (1u << 4));
-    const float r0 = rho[k];
-    float gx = 0.0f, gy = 0.0f;
-    if (xp && xm) gx = 0.5f * (rho[k + 1] - rho[k - 1]);
-    else if (xp) gx = rho[k + 1] - r0;
-    else if (xm) gx = r0 - rho[k - 1];
-    if (yp && ym) gy = 0.5f * (rho[k + L.pitch] - rho[k - L.pitch]);
-    else if (yp) gy = rho[k + L.pitch] - r0;
-    else if (ym) gy = r0 - rho[k - L.pitch];
-    const float c = L.mu_m_lam / (L.rho0 + drho_k);
-    sx += c * gx;
-    sy += c * gy;
+    const float rxp = xp ? rho[k + 1] : 0.0f, rxm = xm ? rho[k - 1] : 0.0f;
+    const float ryp = yp ? rho[k + L.pitch] : 0.0f, rym = ym ? rho[k - L.pitch] : 0.0f;
+    grad_source(drho_k, rxp, rxm, ryp, rym, xp, xm, yp, ym, L, sx, sy);
 }
-
 
 // Density deviation at time t of material node k: from the boundary pass for a
 // boundary node (rho holds it), the sum of the pulled populations otherwise.
@@ -599,6 +613,15 @@ __device__ __forceinline__ float node_drho(const T *__restrict__ src,
     float f[9];
     pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
     return moments(f).dr;
+}
+
+// The nine incoming populations of a boundary node held one per lane (group
+// of eight lanes, direction k on lane k - 1; g0 = f_0), on every lane.
+__device__ __forceinline__ void gather8(float fk, float g0, float f[9]) {
+    const int base = threadIdx.x & 24;  // first lane of the group within the warp
+    f[0] = g0;
+#pragma unroll
+    for (int m = 1; m < 9; ++m) f[m] = __shfl_sync(0xffffffffu, fk, base + m - 1);
 }
 
 // Source S = F + (mu - lambda)/rho grad rho (Eq. sourceterm) at a boundary node,
@@ -625,17 +648,7 @@ __device__ __forceinline__ void source_boundary8(const T *__restrict__ src,
     const float rym = __shfl_sync(0xffffffffu, mine, base + 3);
     const bool xp = !((b.cut >> 1) & 1u), yp = !((b.cut >> 2) & 1u);
     const bool xm = !((b.cut >> 3) & 1u), ym = !((b.cut >> 4) & 1u);
-    const float r0 = rho[kn];
-    float gx = 0.0f, gy = 0.0f;
-    if (xp && xm) gx = 0.5f * (rxp - rxm);
-    else if (xp) gx = rxp - r0;
-    else if (xm) gx = r0 - rxm;
-    if (yp && ym) gy = 0.5f * (ryp - rym);
-    else if (yp) gy = ryp - r0;
-    else if (ym) gy = r0 - rym;
-    const float c = L.mu_m_lam / (L.rho0 + r0);
-    sx += c * gx;
-    sy += c * gy;
+    grad_source(rho[kn], rxp, rxm, ryp, rym, xp, xm, yp, ym, L, sx, sy);
 }
 
 // ---------------------------------------------------------------------------

@@ -120,10 +120,9 @@ __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict_
     __syncthreads();
     if (!live) return;
     // interior nodes have all four axis neighbours: central differences
-    const float gxr = 0.5f * (rs[ty + 1][tx + 2] - rs[ty + 1][tx]);
-    const float gyr = 0.5f * (rs[ty + 2][tx + 1] - rs[ty][tx + 1]);
-    const float cc = L.mu_m_lam / (L.rho0 + own);
-    const float sx = L.fx + cc * gxr, sy = L.fy + cc * gyr;
+    float sx, sy;
+    grad_source(own, rs[ty + 1][tx + 2], rs[ty + 1][tx], rs[ty + 2][tx + 1], rs[ty][tx + 1], true,
+                true, true, true, L, sx, sy);
     float dr, jx, jy;
     collide(f, sx, sy, L, dr, jx, jy);
 #pragma unroll
