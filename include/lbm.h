@@ -142,10 +142,11 @@ typedef struct {
                             0  library default (LBM_TIME_BLOCK where supported, else 1)
                             1  one launch per step (bulk and boundary-list kernels)
                             LBM_TIME_BLOCK  temporal blocking: each launch carries
-                               LBM_TIME_BLOCK steps of a strip of the lattice in
-                               shared memory, so the populations cross HBM once per
-                               LBM_TIME_BLOCK steps; needs FP32 storage, lambda = mu
-                               and nx >= 128 (LBM_ERR_ARG otherwise).  Every stored
+                               LBM_TIME_BLOCK steps (4 when lambda != mu, whose
+                               source needs the density gradient) of a strip of
+                               the lattice in shared memory, so the populations
+                               cross HBM once per launch; needs FP32 storage and
+                               nx >= 128 (LBM_ERR_ARG otherwise).  Every stored
                                value is bit-identical to time_block = 1. */
 } lbm_desc;
 
@@ -162,7 +163,8 @@ typedef struct {
     float storage_scale;    /* power-of-two scale of the 16-bit forms, 1 for FP32 */
     float bytes_per_update; /* algorithmic HBM bytes per interior lattice update */
     int64_t kernel_launches; /* kernels this handle has launched so far */
-    int32_t time_block;      /* steps per launch in use (1 or LBM_TIME_BLOCK) */
+    int32_t time_block;      /* steps per launch in use: 1, LBM_TIME_BLOCK, or 4
+                                (temporal blocking with lambda != mu) */
     int32_t reserved;        /* 0 */
 } lbm_info;
 

@@ -30,14 +30,15 @@ struct Layout {
 };
 
 // Steps per launch for a description: the temporally blocked kernel needs FP32
-// storage, lambda = mu and a lattice at least one strip wide.  Returns 0 if
+// storage and a lattice at least one strip wide (8 steps per launch, 4 when
+// lambda != mu).  Returns 0 if
 // the description asks for blocking that this lattice cannot have.
 int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
-    const bool ok = d.storage == LBM_F32 && u.lam == u.mu && t.nx >= kWaveC &&
-                    t.bnodes.size() < (size_t(1) << 28);
+    const bool ok = d.storage == LBM_F32 && t.nx >= kWaveC && t.bnodes.size() < (size_t(1) << 28);
+    const int k = u.lam == u.mu ? kWaveK : kWaveGradK;
     if (d.time_block == 1) return 1;
-    if (d.time_block == LBM_TIME_BLOCK) return ok ? kWaveK : 0;
-    return ok ? kWaveK : 1;  // the library default: blocked where it applies
+    if (d.time_block == LBM_TIME_BLOCK) return ok ? k : 0;
+    return ok ? k : 1;  // the library default: blocked where it applies
 }
 
 Layout layout(const Tables &t, int storage, bool grad, int block) {
@@ -126,7 +127,8 @@ void destroy_graphs(lbm_solver *h) {
 // with the boundary kernel on a side branch beside the interior kernel, or
 // kGraphChunk / kWaveK temporally blocked launches (an even number, so the
 // chunk ends in the buffer it started from either way).
-static_assert(kGraphChunk % (2 * kWaveK) == 0, "graph chunk and time block");
+static_assert(kGraphChunk % (2 * kWaveK) == 0 && kGraphChunk % (2 * kWaveGradK) == 0,
+              "graph chunk and time block");
 
 lbm_status build_graph(lbm_solver *h, int start) {
     cudaGraph_t g = nullptr;
@@ -170,7 +172,7 @@ extern "C" lbm_status lbm_workspace_size(const lbm_desc *desc, uint64_t *bytes) 
     if (st != LBM_OK) return st;
     const int block = steps_per_launch(*desc, t, u);
     if (block == 0) {
-        set_error("lbm_workspace_size: time_block = LBM_TIME_BLOCK needs FP32 storage, lambda = mu and nx >= 128");
+        set_error("lbm_workspace_size: time_block = LBM_TIME_BLOCK needs FP32 storage and nx >= 128");
         return LBM_ERR_ARG;
     }
     *bytes = layout(t, desc->storage, u.lam != u.mu, block).total;
@@ -197,7 +199,7 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
     h->L.wall_node = desc->wall_values == LBM_WALL_NODE ? 1 : 0;
     h->block = steps_per_launch(*desc, h->tab, h->units);
     if (h->block == 0) {
-        set_error("lbm_create: time_block = LBM_TIME_BLOCK needs FP32 storage, lambda = mu and nx >= 128");
+        set_error("lbm_create: time_block = LBM_TIME_BLOCK needs FP32 storage and nx >= 128");
         delete h;
         return LBM_ERR_ARG;
     }

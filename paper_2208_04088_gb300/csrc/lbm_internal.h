@@ -153,6 +153,9 @@ struct WaveMaps {
 };
 
 bool wave_supported(const Lattice &L);
+// Steps carried by one temporally blocked launch: kWaveK, or kWaveGradK when
+// the source needs the density gradient (lambda != mu).
+constexpr int kWaveGradK = 4;
 size_t wave_smem_bytes();
 // Upper bound of the blocks of one launch (entries of S.wave_tab).
 size_t wave_table_entries(int nx, int ny);

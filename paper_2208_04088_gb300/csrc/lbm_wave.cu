@@ -1,6 +1,7 @@
 // lbm_wave.cu -- temporally blocked time stepping: kWaveK steps of the solid
 // LBM (Eqs. stream, moments, fieq, coll and the boundary rules of Sec. 4) per
-// kernel launch, FP32 storage, lambda = mu (no density gradient in the source).
+// kernel launch, FP32 storage, lambda = mu (k_wave); kGradK steps per launch
+// when lambda != mu and the source needs the density gradient (k_wave_grad).
 //
 // One step reads and writes every population once, so the one-step kernels
 // are bound by HBM at 104 B per lattice update.  Here a block owns a strip of
@@ -443,6 +444,277 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// lambda != mu: the source S = F + (mu - lambda)/rho grad rho needs the
+// densities of the four axis neighbours at the same time level.  Each level l
+// therefore runs two tasks per sweep step, on two sets of warps: the density of
+// row y + 2 (from the pulled, or rule-given, populations of level l - 1, into a
+// four-row density ring of its own) and the collision of row y (pulled
+// populations, the densities of rows y - 1 .. y + 1, Eq. sourceterm, Eq. coll).
+// Row y + 2 of level l - 1 must be complete a step earlier, so the levels run
+// four rows apart; the level rings hold eight rows, and the halo shrinks by two
+// nodes per level.  With kGradK = 4 levels the core is the same 112 columns.
+constexpr int kGradK = kWaveGradK;        // time steps per launch
+constexpr int kGradSkew = 4;              // rows between consecutive levels
+constexpr int kGradNI = 8, kGradD = 3;    // level-0 ring rows; rows issued ahead
+constexpr int kGradNL = 8, kGradND = 4;   // level ring rows; density ring rows
+constexpr int kGradNU = 19;               // node-word and displacement ring rows
+constexpr int kGradThreads = 2 * kGradK * kC;  // collision warps, then density warps
+constexpr size_t kGOffIn = 0;
+constexpr size_t kGOffLev = kGOffIn + (size_t)kGradNI * kFRowBytes;
+constexpr size_t kGOffDen = kGOffLev + (size_t)(kGradK - 1) * kGradNL * kFRowBytes;
+constexpr size_t kGOffU = kGOffDen + (size_t)kGradK * kGradND * kC * 4;
+constexpr size_t kGOffNw = kGOffU + (size_t)kGradNU * kURowBytes;
+constexpr size_t kGOffBar = kGOffNw + (size_t)kGradNU * kNwRowBytes;
+constexpr size_t kGSmem = kGOffBar + (size_t)kGradNI * 8;
+static_assert(kGSmem <= 232448, "shared memory of one block");
+static_assert(kGradThreads <= 1024, "block shape");
+static_assert(kC - 4 * kGradK == kW, "the same strips as the lambda = mu kernel");
+static_assert(kGOffLev % 128 == 0 && kGOffDen % 128 == 0 && kGOffU % 128 == 0 &&
+                  kGOffNw % 128 == 0,
+              "TMA destinations 128-byte aligned");
+
+// The incoming populations of an interior node from three ring rows.
+__device__ __forceinline__ void pull_rows(const float *rm, const float *r0, const float *rp,
+                                          int c, float f[9]) {
+    f[0] = r0[c];
+    f[1] = r0[kC + c - 1];
+    f[2] = rm[2 * kC + c];
+    f[3] = r0[3 * kC + c + 1];
+    f[4] = rp[4 * kC + c];
+    f[5] = rm[5 * kC + c - 1];
+    f[6] = rm[6 * kC + c + 1];
+    f[7] = rp[7 * kC + c + 1];
+    f[8] = rp[8 * kC + c - 1];
+}
+
+// Axis directions 1..4 open (not cut) from a node word's cut mask.
+__device__ __forceinline__ void open_axes(uint64_t nw, bool &xp, bool &yp, bool &xm, bool &ym) {
+    const uint32_t cut = nw_mask(nw, 2);
+    xp = !((cut >> 1) & 1u);
+    yp = !((cut >> 2) & 1u);
+    xm = !((cut >> 3) & 1u);
+    ym = !((cut >> 4) & 1u);
+}
+
+// One launch: kGradK steps of every material node, lambda != mu.  Blocks and
+// regions are those of k_wave.  Warps 0..15 run the collisions, warps 16..31
+// the densities; within each set warp 4 l' + s takes level l' + 1 and column
+// chunk (s - l') mod 4, as in k_wave.
+__global__ void __launch_bounds__(kGradThreads, 1)
+    k_wave_grad(const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tnw,
+                const __grid_constant__ CUtensorMap tu, float *__restrict__ dst,
+                float4 *__restrict__ uc, const BLink *__restrict__ blinks,
+                const BCDev *__restrict__ bcs, Lattice L, const int64_t *__restrict__ time,
+                int toff, const int4 *__restrict__ tab, uint32_t *__restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float *in = reinterpret_cast<float *>(sm + kGOffIn);
+    float *lev = reinterpret_cast<float *>(sm + kGOffLev);
+    float *den = reinterpret_cast<float *>(sm + kGOffDen);
+    float4 *ur = reinterpret_cast<float4 *>(sm + kGOffU);
+    const uint64_t *nwr = reinterpret_cast<const uint64_t *>(sm + kGOffNw);
+    const uint32_t bar0 = smem_addr(sm + kGOffBar);
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const bool density_warp = (tid >> 5) >= 4 * kGradK;  // warp-uniform
+    const int w = (tid >> 5) & (4 * kGradK - 1);
+    const int lv = (w >> 2) + 1;  // time level of this thread (warp-uniform)
+    const int c = ((((w & 3) - (w >> 2)) & 3) << 5) | lane;
+    const int4 region = tab[blockIdx.x];
+    const int X0 = region.x, Y0 = region.y, Hs = region.z;
+    const int xin = X0 - 2 * kGradK;    // lattice column of ring column 0
+    const int y_in0 = Y0 - 2 * kGradK;  // lattice row of input row index 0
+    const int j_last = Hs + 4 * kGradK - 1;
+    const int nsweep = Hs + 6 * kGradK - 3;
+    const float tb = (float)(*time + toff + lv - 2);  // boundary data at the time of f^col
+
+    auto issue = [&](int j) {
+        const uint32_t bar = bar0 + 8u * (uint32_t)(j & (kGradNI - 1));
+        const int y = y_in0 + j;
+        mbar_expect_tx(bar, kTxBytes);
+        tma_load_3d(smem_addr(in + (size_t)(j & (kGradNI - 1)) * kRowF), &tf, xin, y, 0, bar);
+        tma_load_2d(smem_addr(sm + kGOffNw + (size_t)(j % kGradNU) * kNwRowBytes), &tnw, xin, y,
+                    bar);
+        tma_load_3d(smem_addr(sm + kGOffU + (size_t)(j % kGradNU) * kURowBytes), &tu, 0, X0, y,
+                    bar);
+    };
+    auto wait_row = [&](int j) {
+        return mbar_wait(bar0 + 8u * (uint32_t)(j & (kGradNI - 1)),
+                         (uint32_t)((j / kGradNI) & 1));
+    };
+
+    bool ok = true;        // thread 0: every wait so far completed
+    int j_issued = -1;     // thread 0: last input row issued
+    int last_waited = -1;  // thread 0: last input row known to have landed
+    if (tid == 0) {
+        for (int q = 0; q < kGradNI; ++q) mbar_init(bar0 + 8u * q, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int j = 0; j <= kGradD + 1 && j <= j_last; ++j) {
+            issue(j);
+            j_issued = j;
+        }
+        for (int j = 0; j <= 2 && j <= j_last && ok; ++j) {
+            ok = wait_row(j);
+            last_waited = ok ? j : j - 1;
+        }
+    }
+    __syncthreads();
+
+    const bool col_c = c >= 2 * lv && c < kC - 2 * lv;          // collision columns
+    const bool col_d = c >= 2 * lv - 1 && c < kC - 2 * lv + 1;  // density columns
+    const int lo = Y0 - 2 * (kGradK - lv), hi = Y0 + Hs - 1 + 2 * (kGradK - lv);
+    const float *prev_base = lv == 1 ? in : lev + (size_t)(lv - 2) * kGradNL * kRowF;
+    float *own_base = lev + (size_t)(lv - 1) * kGradNL * kRowF;  // unused by the last level
+    float *den_base = den + (size_t)(lv - 1) * kGradND * kC;
+    const int grp = lane >> 3, kdir = (lane & 7) + 1;
+
+    for (int n = 0; n < nsweep; ++n) {
+        if (tid == 0 && n + kGradD + 2 <= j_last && ok) {
+            // order the block's earlier shared-memory accesses before the copy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(n + kGradD + 2);
+            j_issued = n + kGradD + 2;
+        }
+        const int y = y_in0 - 1 + n - kGradSkew * (lv - 1);
+        const int j = y - y_in0;
+        if (density_warp) {
+            // density deviation of row y + 2 at this level
+            if (y + 2 >= lo - 1 && y + 2 <= hi + 1) {
+                const int jd = j + 2;
+                const uint64_t nw = col_d ? nwr[(jd % kGradNU) * kC + c] : 0ull;
+                const uint32_t cl = (uint32_t)(nw & 3u);
+                const float *rm = prev_base + ((jd - 1) & (kGradNL - 1)) * kRowF;
+                const float *r0 = prev_base + (jd & (kGradNL - 1)) * kRowF;
+                const float *rp = prev_base + ((jd + 1) & (kGradNL - 1)) * kRowF;
+                float *drow = den_base + (jd & (kGradND - 1)) * kC;
+                const bool simple_b = cl == kBoundary && ((nw >> 34) & 1u);
+                if (cl == kInterior || simple_b) {
+                    float f[9];
+                    if (cl == kInterior) pull_rows(rm, r0, rp, c, f);
+                    else simple_pull(Rows{rm, r0, rp, c}, nw, bcs, tb, L, f);
+                    drow[c] = density_of(f);
+                }
+                unsigned rem = __ballot_sync(0xffffffffu, cl == kBoundary && !simple_b);
+                while (rem) {  // other boundary nodes: eight lanes each, four per pass
+                    unsigned r = rem;
+                    for (int q = 0; q < grp; ++q) r &= r - 1;
+                    const bool live = r != 0;
+                    const int src = __ffs(live ? r : rem) - 1;
+                    for (int q = 0; q < 4; ++q) rem &= rem - 1;
+                    const uint64_t wb = __shfl_sync(0xffffffffu, nw, src);
+                    const int cb = (c & ~31) + src;
+                    const BLink *lrec = blinks + (int64_t)(uint32_t)(wb >> 35) * 8;
+                    auto link = [&](int i) { return lrec[i - 1]; };
+                    float g0, f[9];
+                    const float fk = boundary8_pull(Rows{rm, r0, rp, cb}, nw_mask(wb, 2),
+                                                    nw_mask(wb, 10), nw_mask(wb, 18),
+                                                    nw_mask(wb, 26), kdir, link, bcs, tb, L, g0);
+                    gather8(fk, g0, f);
+                    if (live && kdir == 1) drow[cb] = density_of(f);
+                }
+            }
+        } else if (y >= lo && y <= hi) {
+            // collision of row y at this level
+            const int ju = j % kGradNU;
+            const uint64_t nw = col_c ? nwr[ju * kC + c] : 0ull;
+            const uint32_t cl = (uint32_t)(nw & 3u);
+            const float *rm = prev_base + ((j - 1) & (kGradNL - 1)) * kRowF;
+            const float *r0 = prev_base + (j & (kGradNL - 1)) * kRowF;
+            const float *rp = prev_base + ((j + 1) & (kGradNL - 1)) * kRowF;
+            const float *dm = den_base + ((j - 1) & (kGradND - 1)) * kC;
+            const float *d0 = den_base + (j & (kGradND - 1)) * kC;
+            const float *dp = den_base + ((j + 1) & (kGradND - 1)) * kC;
+            float *own = own_base + (j & (kGradNL - 1)) * kRowF;
+            const int64_t krow = (int64_t)y * L.pitch + xin;  // lattice index of ring column 0
+            const bool core_row = y >= Y0 && y < Y0 + Hs;
+            float4 *urow = ur + ju * kW;
+            auto store = [&](int col, int k, float v) {
+                if (lv < kGradK) own[k * kC + col] = v;
+                else dst[k * L.plane + krow + col] = v;
+            };
+            auto advance_u = [&](int col, float jx, float jy, float dr) {
+                if (!core_row || col < 2 * kGradK || col >= kC - 2 * kGradK) return;
+                float4 *up = urow + (col - 2 * kGradK);
+                float4 wu = *up;
+                integrate_u_value(wu, jx, jy, L.rho0 + dr);
+                if (lv < kGradK) {
+                    *up = wu;
+                } else {
+                    uc[krow + col] = wu;
+                    flag_nonfinite(status, dr, jx, jy);
+                }
+            };
+            const bool simple_b = cl == kBoundary && ((nw >> 34) & 1u);
+            if (cl == kInterior || simple_b) {
+                float f[9];
+                bool xp = true, yp = true, xm = true, ym = true;
+                if (cl == kInterior) {
+                    pull_rows(rm, r0, rp, c, f);
+                } else {
+                    simple_pull(Rows{rm, r0, rp, c}, nw, bcs, tb, L, f);
+                    open_axes(nw, xp, yp, xm, ym);
+                }
+                float sx, sy, dr, jx, jy;
+                grad_source(density_of(f), d0[c + 1], d0[c - 1], dp[c], dm[c], xp, xm, yp, ym, L,
+                            sx, sy);
+                collide(f, sx, sy, L, dr, jx, jy);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) store(c, i, f[i]);
+                advance_u(c, jx, jy, dr);
+            }
+            unsigned rem = __ballot_sync(0xffffffffu, cl == kBoundary && !simple_b);
+            while (rem) {  // other boundary nodes: eight lanes each, four per pass
+                unsigned r = rem;
+                for (int q = 0; q < grp; ++q) r &= r - 1;
+                const bool live = r != 0;
+                const int src = __ffs(live ? r : rem) - 1;
+                for (int q = 0; q < 4; ++q) rem &= rem - 1;
+                const uint64_t wb = __shfl_sync(0xffffffffu, nw, src);
+                const int cb = (c & ~31) + src;
+                const BLink *lrec = blinks + (int64_t)(uint32_t)(wb >> 35) * 8;
+                auto link = [&](int i) { return lrec[i - 1]; };
+                float g0, f[9];
+                const float fk = boundary8_pull(Rows{rm, r0, rp, cb}, nw_mask(wb, 2),
+                                                nw_mask(wb, 10), nw_mask(wb, 18),
+                                                nw_mask(wb, 26), kdir, link, bcs, tb, L, g0);
+                gather8(fk, g0, f);
+                bool xp, yp, xm, ym;
+                open_axes(wb, xp, yp, xm, ym);
+                float sx, sy, dr, jx, jy;
+                grad_source(density_of(f), d0[cb + 1], d0[cb - 1], dp[cb], dm[cb], xp, xm, yp, ym,
+                            L, sx, sy);
+                collide(f, sx, sy, L, dr, jx, jy);
+                float mine = f[1];
+#pragma unroll
+                for (int q = 2; q < 9; ++q)
+                    if (kdir == q) mine = f[q];
+                if (!live) continue;
+                store(cb, kdir, mine);
+                if (kdir == 1) {
+                    store(cb, 0, f[0]);
+                    advance_u(cb, jx, jy, dr);
+                }
+            }
+        }
+        if (tid == 0 && n + 3 <= j_last && ok) {
+            ok = wait_row(n + 3);
+            if (!ok) last_waited = n + 2;
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && !ok) {
+        // a copy did not land in time: flag it, and give the copies still in
+        // flight a bounded chance to land before the block's shared memory goes
+        atomicOr(status, 2u);
+        for (int j = last_waited + 1; j <= j_issued; ++j)
+            if (!wait_row(j)) break;
+    }
+}
+
 // Node words: the class of every node, then the boundary records.
 __global__ void k_nw_fill(const uint8_t *__restrict__ cls, uint64_t *__restrict__ nw, int64_t n) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -630,7 +902,7 @@ std::vector<int4> wave_plan(const Tables &t, int sms) {
 size_t wave_smem_bytes() { return kSmem; }
 
 bool wave_supported(const Lattice &L) {
-    return L.nx >= kC && L.ny >= 1 && L.nb < (1 << 28) && !L.grad && encoder() != nullptr;
+    return L.nx >= kC && L.ny >= 1 && L.nb < (1 << 28) && encoder() != nullptr;
 }
 
 cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, WaveMaps *m,
@@ -657,7 +929,10 @@ cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, W
     const cuuint32_t ubox[3] = {4, (cuuint32_t)kW, 1};
     if (!encode(&m->u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S.ucomp, udims, ustr, ubox))
         return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(k_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    e = L.grad ? cudaFuncSetAttribute(k_wave_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kGSmem)
+               : cudaFuncSetAttribute(k_wave, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kSmem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess)
@@ -673,9 +948,14 @@ cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, W
 
 cudaError_t launch_wave(const Lattice &L, const DevState &S, const WaveMaps &m, int cur, int toff,
                         cudaStream_t s) {
-    k_wave<<<(unsigned)m.nblocks, kThreads, kSmem, s>>>(
-        m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]), S.ucomp, S.blinks, S.bcs, L,
-        S.time, toff, S.wave_tab, S.status);
+    if (L.grad)
+        k_wave_grad<<<(unsigned)m.nblocks, kGradThreads, kGSmem, s>>>(
+            m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]), S.ucomp, S.blinks, S.bcs, L,
+            S.time, toff, S.wave_tab, S.status);
+    else
+        k_wave<<<(unsigned)m.nblocks, kThreads, kSmem, s>>>(
+            m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]), S.ucomp, S.blinks, S.bcs, L,
+            S.time, toff, S.wave_tab, S.status);
     return cudaGetLastError();
 }
 

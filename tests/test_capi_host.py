@@ -107,7 +107,7 @@ def test_physical_units_are_accepted():
 
 def test_time_block_selection_and_validation():
     """lbm_desc.time_block: 0 (default: blocked where supported), 1 (one step per launch) or
-    LBM_TIME_BLOCK (temporal blocking, FP32 storage, lambda = mu, nx >= 128);
+    LBM_TIME_BLOCK (temporal blocking, FP32 storage, nx >= 128);
     the blocked form adds the 8-byte node words and its block table to the
     workspace."""
     wl = W.hole_plate(256, 128, 16.0, 0)
@@ -129,9 +129,10 @@ def test_time_block_selection_and_validation():
             N.lbm_workspace_size(_desc(wl, time_block=bad))
     with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
         N.lbm_workspace_size(_desc(wl, storage="bf16", time_block=N.LBM_TIME_BLOCK))
+    # lambda != mu is blocked too (4 steps per launch): the same extra tables
     nonpoisson = W.hole_plate(256, 128, 16.0, 0, lam_over_mu=0.8)
-    with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
-        N.lbm_workspace_size(_desc(nonpoisson, time_block=N.LBM_TIME_BLOCK))
+    assert N.lbm_workspace_size(_desc(nonpoisson, time_block=N.LBM_TIME_BLOCK)) - \
+        N.lbm_workspace_size(_desc(nonpoisson, time_block=1)) == blk - one
     narrow = W.square_plate(64, 0)
     with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
         N.lbm_workspace_size(_desc(narrow, time_block=N.LBM_TIME_BLOCK))

@@ -110,3 +110,55 @@ def test_blocked_reports_non_finite():
         with pytest.raises(N.LbmError, match="LBM_ERR_UNSTABLE"):
             s.sync()
         s.close()
+
+
+# lambda != mu: the source needs grad rho; the blocked kernel carries 4 steps
+# per launch (densities of each level formed two rows ahead)
+PAPER = W.CRACK_PAPER_LAM_OVER_MU
+
+
+def _moving_wall_plate_nonpoisson():
+    wl = _moving_wall_plate()
+    wl.lam_over_mu = W.PLATE_NONPOISSON_LAM_OVER_MU
+    wl.name = "moving_wall_160_nonpoisson"
+    return wl
+
+
+GRAD_CASES = [
+    _with(W.hole_plate(256, 128, 16.0, 0, lam_over_mu=0.8), name="hole_256x128_nonpoisson"),
+    _with(W.hole_plate(256, 128, 16.0, 0, lam_over_mu=0.8), wall_node=True,
+          name="hole_256x128_nonpoisson_node"),
+    _with(W.edge_crack(256, 64, 0, lam_over_mu=PAPER), name="edge_crack_256_L64_paper"),
+    _with(W.centre_crack(32, 0, lam_over_mu=PAPER), name="centre_crack_128_L32_paper"),
+    _moving_wall_plate_nonpoisson(),
+]
+
+
+@pytest.mark.parametrize("steps", [4, 37, 77])
+@pytest.mark.parametrize("wl", GRAD_CASES, ids=lambda w: w.name)
+def test_blocked_nonpoisson_bit_identical_to_one_step(wl, steps):
+    a = run_gpu(wl, steps, time_block=1)
+    b = run_gpu(wl, steps, time_block=TB)
+    assert a["info"]["time_block"] == 1 and b["info"]["time_block"] == 4
+    for k in ("u", "v", "sigma"):
+        assert np.array_equal(a[k], b[k]), (k, float(np.abs(a[k] - b[k]).max()))
+
+
+@pytest.mark.parametrize("wl,steps", [(W.hole_plate(256, 128, 16.0, 0, lam_over_mu=0.8), 300),
+                                      (_with(W.edge_crack(256, 64, 0, lam_over_mu=PAPER),
+                                             wall_node=True), 300)],
+                         ids=["hole_256x128_nonpoisson", "edge_crack_256_paper_node"])
+def test_blocked_nonpoisson_parity_with_oracle(oracle_mod, wl, steps):
+    gpu = run_gpu(wl, steps, time_block=TB)
+    assert gpu["info"]["time_block"] == 4
+    err = compare(gpu, run_oracle(oracle_mod, wl, steps))
+    assert all(e <= 1e-5 for e in err.values()), err
+
+
+def test_blocked_nonpoisson_full_size_crack_bit_identical():
+    # the 2048^2 edge crack in the paper's material (nu = 0.2174) over 1500 steps
+    wl = _with(W.CONFIG3, wall_node=True, lam_over_mu=PAPER)
+    a = run_gpu(wl, wl.steps, time_block=1)
+    b = run_gpu(wl, wl.steps, time_block=TB)
+    for k in ("u", "v", "sigma"):
+        assert np.array_equal(a[k], b[k]), k
