@@ -139,7 +139,8 @@ typedef struct {
     int32_t storage;   /* lbm_storage */
     int32_t wall_values; /* lbm_wall_values */
     int32_t time_block;  /* time steps fused into one kernel launch:
-                            0  library default (LBM_TIME_BLOCK where supported, else 1)
+                            0  library default (LBM_TIME_BLOCK where supported and
+                               lambda = mu, where it is the faster form; else 1)
                             1  one launch per step (bulk and boundary-list kernels)
                             LBM_TIME_BLOCK  temporal blocking: each launch carries
                                LBM_TIME_BLOCK steps (4 when lambda != mu, whose

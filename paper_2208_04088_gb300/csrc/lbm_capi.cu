@@ -38,7 +38,10 @@ int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
     const int k = u.lam == u.mu ? kWaveK : kWaveGradK;
     if (d.time_block == 1) return 1;
     if (d.time_block == LBM_TIME_BLOCK) return ok ? k : 0;
-    return ok ? k : 1;  // the library default: blocked where it applies
+    // the library default: blocked where that is faster (lambda = mu); with
+    // lambda != mu the blocked kernel advances half as many warps per row step
+    // and measured slower than one step per launch (34 vs 45 GLUPS, 2048^2 crack)
+    return ok && u.lam == u.mu ? k : 1;
 }
 
 Layout layout(const Tables &t, int storage, bool grad, int block) {

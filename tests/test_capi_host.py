@@ -133,6 +133,9 @@ def test_time_block_selection_and_validation():
     nonpoisson = W.hole_plate(256, 128, 16.0, 0, lam_over_mu=0.8)
     assert N.lbm_workspace_size(_desc(nonpoisson, time_block=N.LBM_TIME_BLOCK)) - \
         N.lbm_workspace_size(_desc(nonpoisson, time_block=1)) == blk - one
+    # ... but its default is one step per launch (the faster form there)
+    assert N.lbm_workspace_size(_desc(nonpoisson)) == \
+        N.lbm_workspace_size(_desc(nonpoisson, time_block=1))
     narrow = W.square_plate(64, 0)
     with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
         N.lbm_workspace_size(_desc(narrow, time_block=N.LBM_TIME_BLOCK))
