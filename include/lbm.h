@@ -139,8 +139,10 @@ typedef struct {
     int32_t storage;   /* lbm_storage */
     int32_t wall_values; /* lbm_wall_values */
     int32_t time_block;  /* time steps fused into one kernel launch:
-                            0  library default (LBM_TIME_BLOCK where supported and
-                               lambda = mu, where it is the faster form; else 1)
+                            0  library default: LBM_TIME_BLOCK where it is the
+                               faster form (supported, lambda = mu, at least 2^21
+                               nodes, at most one boundary node per 4096 nodes that
+                               is not on a box edge or crack face); else 1
                             1  one launch per step (bulk and boundary-list kernels)
                             LBM_TIME_BLOCK  temporal blocking: each launch carries
                                LBM_TIME_BLOCK steps (4 when lambda != mu, whose

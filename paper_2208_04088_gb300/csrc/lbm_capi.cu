@@ -33,15 +33,51 @@ struct Layout {
 // storage and a lattice at least one strip wide (8 steps per launch, 4 when
 // lambda != mu).  Returns 0 if
 // the description asks for blocking that this lattice cannot have.
+// Boundary nodes that the blocked kernel updates eight lanes to a node: all but
+// the "simple" ones (every cut link a mid-link wall of one BC and one
+// axis-aligned normal: box edges and crack faces).
+int64_t complex_boundary_nodes(const Tables &t) {
+    int64_t n = 0;
+    for (size_t g = 0; g < t.bnodes.size(); ++g) {
+        const BNode &b = t.bnodes[g];
+        bool simple = b.corner == 0;
+        int bc = -1;
+        float n0 = 0.0f, n1 = 0.0f;
+        for (int i = 1; i < kQ && simple; ++i) {
+            if (!((b.cut >> i) & 1u)) continue;
+            const BLink &lk = t.blinks[g * 8 + i - 1];
+            const bool axis = (lk.n0 == 0.0f && (lk.n1 == 1.0f || lk.n1 == -1.0f)) ||
+                              (lk.n1 == 0.0f && (lk.n0 == 1.0f || lk.n0 == -1.0f));
+            if (lk.q != 0.5f || lk.bc != lk.bc2 || !axis) simple = false;
+            if (bc < 0) {
+                bc = lk.bc;
+                n0 = lk.n0;
+                n1 = lk.n1;
+            } else if (lk.bc != bc || lk.n0 != n0 || lk.n1 != n1) {
+                simple = false;
+            }
+        }
+        n += simple ? 0 : 1;
+    }
+    return n;
+}
+
 int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
     const bool ok = d.storage == LBM_F32 && t.nx >= kWaveC && t.bnodes.size() < (size_t(1) << 28);
     const int k = u.lam == u.mu ? kWaveK : kWaveGradK;
     if (d.time_block == 1) return 1;
     if (d.time_block == LBM_TIME_BLOCK) return ok ? k : 0;
-    // the library default: blocked where that is faster (lambda = mu); with
-    // lambda != mu the blocked kernel advances half as many warps per row step
-    // and measured slower than one step per launch (34 vs 45 GLUPS, 2048^2 crack)
-    return ok && u.lam == u.mu ? k : 1;
+    // The library default: blocked where that measured faster on GB300 --
+    // lambda = mu (with lambda != mu the blocked kernel advances half as many
+    // warps per row step: 34 vs 45 GLUPS on the 2048^2 crack), lattices of at
+    // least 2^21 nodes (below, the fill of each block's row pipeline dominates:
+    // 1024^2 plate 29 vs 80 GLUPS), and few boundary nodes off box edges and
+    // crack faces, which the blocked kernel updates eight lanes to a node in
+    // every row they occupy (2048^2 plate with a hole of radius 256: 37 vs 62).
+    const int64_t nodes = (int64_t)t.nx * t.ny;
+    const bool faster = u.lam == u.mu && nodes >= ((int64_t)1 << 21) &&
+                        complex_boundary_nodes(t) * 4096 <= nodes;
+    return ok && faster ? k : 1;
 }
 
 Layout layout(const Tables &t, int storage, bool grad, int block) {

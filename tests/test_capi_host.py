@@ -106,7 +106,7 @@ def test_physical_units_are_accepted():
 
 
 def test_time_block_selection_and_validation():
-    """lbm_desc.time_block: 0 (default: blocked where supported), 1 (one step per launch) or
+    """lbm_desc.time_block: 0 (default: blocked where faster), 1 (one step per launch) or
     LBM_TIME_BLOCK (temporal blocking, FP32 storage, nx >= 128);
     the blocked form adds the 8-byte node words and its block table to the
     workspace."""
@@ -120,7 +120,15 @@ def test_time_block_selection_and_validation():
     strips = (256 + 111) // 112
     table = (max(strips, 4096) + strips) * 16
     assert blk - one == (8 * plane + 255) // 256 * 256 + (table + 255) // 256 * 256
-    assert dflt == blk
+    # the default is blocked only where that is the faster form: at least 2^21
+    # nodes, lambda = mu and few boundary nodes off box edges and crack faces
+    assert dflt == one
+    crack = W.edge_crack(2048, 512, 0)
+    assert N.lbm_workspace_size(_desc(crack)) == \
+        N.lbm_workspace_size(_desc(crack, time_block=N.LBM_TIME_BLOCK))
+    big_hole = W.hole_plate(2048, 2048, 256.0, 0)
+    assert N.lbm_workspace_size(_desc(big_hole)) == \
+        N.lbm_workspace_size(_desc(big_hole, time_block=1))
     # the default falls back to one step per launch where blocking is unsupported
     assert N.lbm_workspace_size(_desc(wl, storage="f16")) == \
         N.lbm_workspace_size(_desc(wl, storage="f16", time_block=1))
