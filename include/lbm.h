@@ -141,7 +141,7 @@ typedef struct {
     int32_t time_block;  /* time steps fused into one kernel launch:
                             0  library default: LBM_TIME_BLOCK where it is the
                                faster form (supported, lambda = mu, at least 2^21
-                               nodes, at most one boundary node per 4096 nodes that
+                               nodes, at most one boundary node per 1536 nodes that
                                is not on a box edge or crack face); else 1
                             1  one launch per step (bulk and boundary-list kernels)
                             LBM_TIME_BLOCK  temporal blocking: each launch carries

@@ -38,27 +38,7 @@ struct Layout {
 // axis-aligned normal: box edges and crack faces).
 int64_t complex_boundary_nodes(const Tables &t) {
     int64_t n = 0;
-    for (size_t g = 0; g < t.bnodes.size(); ++g) {
-        const BNode &b = t.bnodes[g];
-        bool simple = b.corner == 0;
-        int bc = -1;
-        float n0 = 0.0f, n1 = 0.0f;
-        for (int i = 1; i < kQ && simple; ++i) {
-            if (!((b.cut >> i) & 1u)) continue;
-            const BLink &lk = t.blinks[g * 8 + i - 1];
-            const bool axis = (lk.n0 == 0.0f && (lk.n1 == 1.0f || lk.n1 == -1.0f)) ||
-                              (lk.n1 == 0.0f && (lk.n0 == 1.0f || lk.n0 == -1.0f));
-            if (lk.q != 0.5f || lk.bc != lk.bc2 || !axis) simple = false;
-            if (bc < 0) {
-                bc = lk.bc;
-                n0 = lk.n0;
-                n1 = lk.n1;
-            } else if (lk.bc != bc || lk.n0 != n0 || lk.n1 != n1) {
-                simple = false;
-            }
-        }
-        n += simple ? 0 : 1;
-    }
+    for (size_t g = 0; g < t.bnodes.size(); ++g) n += complex_boundary_node(t, g) ? 1 : 0;
     return n;
 }
 
@@ -71,12 +51,13 @@ int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
     // lambda = mu (with lambda != mu the blocked kernel advances half as many
     // warps per row step: 34 vs 45 GLUPS on the 2048^2 crack), lattices of at
     // least 2^21 nodes (below, the fill of each block's row pipeline dominates:
-    // 1024^2 plate 29 vs 80 GLUPS), and few boundary nodes off box edges and
-    // crack faces, which the blocked kernel updates eight lanes to a node in
-    // every row they occupy (2048^2 plate with a hole of radius 256: 37 vs 62).
+    // 1024^2 plate 29 vs 80 GLUPS), and at most one boundary node off box edges
+    // and crack faces per 1536 nodes: the blocked kernel updates those eight
+    // lanes to a node at every level (2048^2 plates with a hole: radius 256,
+    // one per 2040 nodes, 84 vs 62 GLUPS; radius 512, one per 1022, 55 vs 59).
     const int64_t nodes = (int64_t)t.nx * t.ny;
     const bool faster = u.lam == u.mu && nodes >= ((int64_t)1 << 21) &&
-                        complex_boundary_nodes(t) * 4096 <= nodes;
+                        complex_boundary_nodes(t) * 1536 <= nodes;
     return ok && faster ? k : 1;
 }
 

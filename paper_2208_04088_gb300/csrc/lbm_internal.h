@@ -159,6 +159,10 @@ constexpr int kWaveGradK = 4;
 size_t wave_smem_bytes();
 // Upper bound of the blocks of one launch (entries of S.wave_tab).
 size_t wave_table_entries(int nx, int ny);
+// Whether boundary node g takes the blocked kernel's eight-lane update (curved
+// walls, corners, crack mouth) rather than the one-lane update of a mid-link
+// wall with one BC and one axis-aligned normal.
+bool complex_boundary_node(const Tables &t, size_t g);
 // The blocks of one launch for a device with `sms` SMs: (X0, Y0, rows, has_boundary).
 std::vector<int4> wave_plan(const Tables &t, int sms);
 // Builds the node words from the class and boundary tables, the TMA

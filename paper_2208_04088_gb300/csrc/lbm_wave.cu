@@ -807,13 +807,42 @@ size_t wave_table_entries(int nx, int ny) {
 //     that wall is updated in every row and level);
 //   - a row in which at least a quarter of the region's columns are boundary
 //     nodes (a wall along the row: box edge, crack face) adds kWallRowPenalty,
-//     counted also when it lies in the segment's halo.
+//     counted also when it lies in the segment's halo;
+//   - curved-wall, corner and crack-mouth nodes (the 8-lane update, four
+//     nodes per pass in each 32-column chunk) add kComplexPassCost per pass
+//     of the row's busiest chunk.
 // Segments are cut greedily against a target cost, and the smallest target for
 // which all blocks fit one wave on `sms` SMs (one block per SM) is found by
 // bisection.  Each entry also says whether a boundary node lies in the
 // block's region or halo.
 constexpr double kWallRowCost = 2.3;
 constexpr double kWallRowPenalty = 65.0;
+constexpr double kComplexPassCost = 4.0;
+
+// A boundary node the blocked kernel updates eight lanes to a node (curved
+// walls, corners, crack mouth): not every cut link is a mid-link wall of one
+// BC and one axis-aligned normal (the node words' "simple" flag).
+bool complex_boundary_node(const Tables &t, size_t g) {
+    const BNode &b = t.bnodes[g];
+    if (b.corner) return true;
+    int bc = -1;
+    float n0 = 0.0f, n1 = 0.0f;
+    for (int i = 1; i < kQ; ++i) {
+        if (!((b.cut >> i) & 1u)) continue;
+        const BLink &lk = t.blinks[g * 8 + i - 1];
+        const bool axis = (lk.n0 == 0.0f && (lk.n1 == 1.0f || lk.n1 == -1.0f)) ||
+                          (lk.n1 == 0.0f && (lk.n0 == 1.0f || lk.n0 == -1.0f));
+        if (lk.q != 0.5f || lk.bc != lk.bc2 || !axis) return true;
+        if (bc < 0) {
+            bc = lk.bc;
+            n0 = lk.n0;
+            n1 = lk.n1;
+        } else if (lk.bc != bc || lk.n0 != n0 || lk.n1 != n1) {
+            return true;
+        }
+    }
+    return bc < 0;
+}
 
 std::vector<int4> wave_plan(const Tables &t, int sms) {
     const int nx = t.nx, ny = t.ny;
@@ -821,12 +850,39 @@ std::vector<int4> wave_plan(const Tables &t, int sms) {
     std::vector<int64_t> per_strip(nstrips, 0);
     // boundary rows seen by each strip's region (core and halo columns)
     std::vector<std::vector<int>> rows(nstrips);
-    for (const BNode &b : t.bnodes) {
+    // complex nodes as (row, 32-column chunk of the region) keys per strip
+    std::vector<std::vector<int64_t>> ckeys(nstrips);
+    for (size_t g = 0; g < t.bnodes.size(); ++g) {
+        const BNode &b = t.bnodes[g];
         per_strip[b.x / kW] += 1;
+        const bool cx = complex_boundary_node(t, g);
         const int s_lo = std::max(0, (b.x - kK) / kW), s_hi = std::min(nstrips - 1, (b.x + kK) / kW);
         for (int sx = s_lo; sx <= s_hi; ++sx) {
             const int X0 = sx * kW;
-            if (b.x >= X0 - kK && b.x < X0 + kW + kK) rows[sx].push_back(b.y);
+            if (b.x >= X0 - kK && b.x < X0 + kW + kK) {
+                rows[sx].push_back(b.y);
+                if (cx) ckeys[sx].push_back((int64_t)b.y * 4 + (b.x - X0 + kK) / 32);
+            }
+        }
+    }
+    // passes of the busiest chunk per row, as sorted rows and prefix sums
+    std::vector<std::vector<int>> crow(nstrips);
+    std::vector<std::vector<double>> cpre(nstrips);
+    for (int sx = 0; sx < nstrips; ++sx) {
+        auto &k = ckeys[sx];
+        std::sort(k.begin(), k.end());
+        cpre[sx].push_back(0.0);
+        for (size_t a = 0; a < k.size();) {
+            const int64_t y = k[a] / 4;
+            int passes = 0;
+            while (a < k.size() && k[a] / 4 == y) {
+                size_t b = a;
+                while (b < k.size() && k[b] == k[a]) ++b;
+                passes = std::max(passes, (int)(b - a + 3) / 4);
+                a = b;
+            }
+            crow[sx].push_back((int)y);
+            cpre[sx].push_back(cpre[sx].back() + passes);
         }
     }
     std::vector<double> row_cost(nstrips);
@@ -847,7 +903,11 @@ std::vector<int4> wave_plan(const Tables &t, int sms) {
         const auto &d = dense[sx];
         const auto lo = std::lower_bound(d.begin(), d.end(), a - kK);
         const auto hi = std::lower_bound(d.begin(), d.end(), b + kK);
-        return row_cost[sx] * (b - a + 3 * kK - 3) + kWallRowPenalty * (double)(hi - lo);
+        const auto &cr = crow[sx];
+        const size_t clo = std::lower_bound(cr.begin(), cr.end(), a - kK) - cr.begin();
+        const size_t chi = std::lower_bound(cr.begin(), cr.end(), b + kK) - cr.begin();
+        return row_cost[sx] * (b - a + 3 * kK - 3) + kWallRowPenalty * (double)(hi - lo) +
+               kComplexPassCost * (cpre[sx][chi] - cpre[sx][clo]);
     };
     // greedy cut of strip sx against target T (every segment at least one row)
     auto cut = [&](int sx, double T, std::vector<int> *ends) {

@@ -121,12 +121,18 @@ def test_time_block_selection_and_validation():
     table = (max(strips, 4096) + strips) * 16
     assert blk - one == (8 * plane + 255) // 256 * 256 + (table + 255) // 256 * 256
     # the default is blocked only where that is the faster form: at least 2^21
-    # nodes, lambda = mu and few boundary nodes off box edges and crack faces
+    # nodes, lambda = mu and at most one boundary node off box edges and crack
+    # faces per 1536 nodes
     assert dflt == one
     crack = W.edge_crack(2048, 512, 0)
     assert N.lbm_workspace_size(_desc(crack)) == \
         N.lbm_workspace_size(_desc(crack, time_block=N.LBM_TIME_BLOCK))
-    big_hole = W.hole_plate(2048, 2048, 256.0, 0)
+    # a hole of radius 256 in a 2048^2 plate: about one curved-wall node per
+    # 2040 nodes, blocked; radius 512 (one per 1022): one step per launch
+    hole = W.hole_plate(2048, 2048, 256.0, 0)
+    assert N.lbm_workspace_size(_desc(hole)) == \
+        N.lbm_workspace_size(_desc(hole, time_block=N.LBM_TIME_BLOCK))
+    big_hole = W.hole_plate(2048, 2048, 512.0, 0)
     assert N.lbm_workspace_size(_desc(big_hole)) == \
         N.lbm_workspace_size(_desc(big_hole, time_block=1))
     # the default falls back to one step per launch where blocking is unsupported
