@@ -71,48 +71,94 @@ __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// The same operations on the values of two lattice nodes at once: an f32x2
+// register pair, one instruction for both (each half rounded to nearest, so
+// a pair gives, half by half, what the scalar operation gives).
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 f2(float lo, float hi) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_split(F2 x, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x.v));
+}
+__device__ __forceinline__ F2 rmul(F2 a, F2 b) {
+    F2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 radd(F2 a, F2 b) {
+    F2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 rsub(F2 a, F2 b) {
+    F2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 rfma(F2 a, F2 b, F2 c) {
+    F2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+// A constant in either form.
+template <class V> __device__ __forceinline__ V splat(float c);
+template <> __device__ __forceinline__ float splat<float>(float c) { return c; }
+template <> __device__ __forceinline__ F2 splat<F2>(float c) { return f2(c, c); }
+
 // ---------------------------------------------------------------------------
 // Raw moments m_pq = sum_i f_i c_ix^p c_iy^q (p, q in 0..2) of the nine
 // populations.  D2Q9 is the tensor product of {-1, 0, 1} in x and y, so the
 // transform is two passes of the 1-D map (a-, a0, a+) -> (a- + a0 + a+,
 // a+ - a-, a+ + a-), whose inverse has only the coefficients 1 and 1/2: the
 // round trip adds nothing but additions to the rounding.
-struct Raw {
-    float m00, m10, m01, m20, m02, m11, m21, m12, m22;
+template <class V> struct RawT {
+    V m00, m10, m01, m20, m02, m11, m21, m12, m22;
 };
+using Raw = RawT<float>;
 
-__device__ __forceinline__ Raw raw_moments(const float f[9]) {
+template <class V> __device__ __forceinline__ RawT<V> raw_moments(const V f[9]) {
     // rows c_y = -1: (f7, f4, f8); c_y = 0: (f3, f0, f1); c_y = +1: (f6, f2, f5)
-    const float a0 = (f[7] + f[4]) + f[8], a1 = f[8] - f[7], a2 = f[8] + f[7];
-    const float b0 = (f[3] + f[0]) + f[1], b1 = f[1] - f[3], b2 = f[1] + f[3];
-    const float c0 = (f[6] + f[2]) + f[5], c1 = f[5] - f[6], c2 = f[5] + f[6];
-    Raw m;
-    m.m00 = (a0 + b0) + c0;
-    m.m01 = c0 - a0;
-    m.m02 = c0 + a0;
-    m.m10 = (a1 + b1) + c1;
-    m.m11 = c1 - a1;
-    m.m12 = c1 + a1;
-    m.m20 = (a2 + b2) + c2;
-    m.m21 = c2 - a2;
-    m.m22 = c2 + a2;
+    const V a0 = radd(radd(f[7], f[4]), f[8]), a1 = rsub(f[8], f[7]), a2 = radd(f[8], f[7]);
+    const V b0 = radd(radd(f[3], f[0]), f[1]), b1 = rsub(f[1], f[3]), b2 = radd(f[1], f[3]);
+    const V c0 = radd(radd(f[6], f[2]), f[5]), c1 = rsub(f[5], f[6]), c2 = radd(f[5], f[6]);
+    RawT<V> m;
+    m.m00 = radd(radd(a0, b0), c0);
+    m.m01 = rsub(c0, a0);
+    m.m02 = radd(c0, a0);
+    m.m10 = radd(radd(a1, b1), c1);
+    m.m11 = rsub(c1, a1);
+    m.m12 = radd(c1, a1);
+    m.m20 = radd(radd(a2, b2), c2);
+    m.m21 = rsub(c2, a2);
+    m.m22 = radd(c2, a2);
     return m;
 }
 
-__device__ __forceinline__ void populations(const Raw &m, float f[9]) {
+// Inverse of the 1-D map: (s, d, p) -> (a-, a0, a+) = ((p - d)/2, s - p,
+// (p + d)/2), with (p -/+ d)/2 formed as fma(-/+1/2, d, p/2): halving is exact,
+// so this is the correctly rounded half of p -/+ d.
+template <class V>
+__device__ __forceinline__ void inverse3(V s, V d, V p, V &am, V &a0, V &ap) {
+    const V h = rmul(splat<V>(0.5f), p);
+    am = rfma(splat<V>(-0.5f), d, h);
+    a0 = rsub(s, p);
+    ap = rfma(splat<V>(0.5f), d, h);
+}
+
+template <class V> __device__ __forceinline__ void populations(const RawT<V> &m, V f[9]) {
     // inverse in y for each x-order p, then inverse in x for each row
-    const float a0 = 0.5f * (m.m02 - m.m01), b0 = m.m00 - m.m02, c0 = 0.5f * (m.m02 + m.m01);
-    const float a1 = 0.5f * (m.m12 - m.m11), b1 = m.m10 - m.m12, c1 = 0.5f * (m.m12 + m.m11);
-    const float a2 = 0.5f * (m.m22 - m.m21), b2 = m.m20 - m.m22, c2 = 0.5f * (m.m22 + m.m21);
-    f[7] = 0.5f * (a2 - a1);
-    f[4] = a0 - a2;
-    f[8] = 0.5f * (a2 + a1);
-    f[3] = 0.5f * (b2 - b1);
-    f[0] = b0 - b2;
-    f[1] = 0.5f * (b2 + b1);
-    f[6] = 0.5f * (c2 - c1);
-    f[2] = c0 - c2;
-    f[5] = 0.5f * (c2 + c1);
+    V a0, b0, c0, a1, b1, c1, a2, b2, c2;
+    inverse3(m.m00, m.m01, m.m02, a0, b0, c0);
+    inverse3(m.m10, m.m11, m.m12, a1, b1, c1);
+    inverse3(m.m20, m.m21, m.m22, a2, b2, c2);
+    inverse3(a0, a1, a2, f[7], f[4], f[8]);
+    inverse3(b0, b1, b2, f[3], f[0], f[1]);
+    inverse3(c0, c1, c2, f[6], f[2], f[5]);
 }
 
 // Moments of Eq. (moments) in deviation form: drho, m = sum f c (without S/2), P.
@@ -134,29 +180,38 @@ __device__ __forceinline__ Mom moments(const float f[9]) {
 // and those of psi_i = 3 w_i c_i.S are S in the first and S/3 in the third
 // moments.  rho and P pass through untouched and j gains exactly S, so the
 // collision invariants are not disturbed by the rounding of 1/3 and 1/9.
-// On return f holds f^col, jx/jy the momentum j = m + S/2, dr the density deviation.
-// The relaxation of Eq. (coll) on the raw moments (see collide); returns the
-// momentum j = m + S/2 in jx, jy.
-__device__ __forceinline__ void relax_raw(Raw &m, float sx, float sy, const Lattice &L, float &jx,
-                                          float &jy) {
-    jx = rfma(0.5f, sx, m.m10);
-    jy = rfma(0.5f, sy, m.m01);
-    const float w = L.omega;
-    const float s3 = rmul(L.src, 1.0f / 3.0f);
+// The relaxation on the raw moments; w = omega, s3 = (1 - 1/(2 tau))/3.
+// Returns the momentum j = m + S/2 in jx, jy.  omega (f^eq - f) is formed as
+// (-omega)(f - f^eq), which rounds to the same value.
+template <class V>
+__device__ __forceinline__ void relax_raw(RawT<V> &m, V sx, V sy, V w, V s3, V &jx, V &jy) {
+    const V half = splat<V>(0.5f), third = splat<V>(1.0f / 3.0f);
+    const V mthird = splat<V>(-1.0f / 3.0f), mninth = splat<V>(-1.0f / 9.0f);
+    const V mw = rsub(splat<V>(0.0f), w);
+    jx = rfma(half, sx, m.m10);
+    jy = rfma(half, sy, m.m01);
     m.m10 = radd(m.m10, sx);
     m.m01 = radd(m.m01, sy);
-    m.m21 = radd(m.m21, rfma(s3, sy, rmul(w, rfma(jy, 1.0f / 3.0f, -m.m21))));
-    m.m12 = radd(m.m12, rfma(s3, sx, rmul(w, rfma(jx, 1.0f / 3.0f, -m.m12))));
-    const float e = rfma(-m.m00, 1.0f / 9.0f, rmul(radd(m.m20, m.m02), 1.0f / 3.0f));
+    m.m21 = radd(m.m21, rfma(s3, sy, rmul(mw, rfma(jy, mthird, m.m21))));
+    m.m12 = radd(m.m12, rfma(s3, sx, rmul(mw, rfma(jx, mthird, m.m12))));
+    const V e = rfma(m.m00, mninth, rmul(radd(m.m20, m.m02), third));
     m.m22 = rfma(w, rsub(e, m.m22), m.m22);
+}
+
+// On return f holds f^col, jx/jy the momentum j = m + S/2, dr the density
+// deviation; the same for one node (float) or two (F2).
+template <class V>
+__device__ __forceinline__ void collide_v(V f[9], V sx, V sy, V w, V s3, V &dr_out, V &jx_out,
+                                          V &jy_out) {
+    RawT<V> m = raw_moments(f);
+    relax_raw(m, sx, sy, w, s3, jx_out, jy_out);
+    dr_out = m.m00;
+    populations(m, f);
 }
 
 __device__ __forceinline__ void collide(float f[9], float sx, float sy, const Lattice &L,
                                         float &dr_out, float &jx_out, float &jy_out) {
-    Raw m = raw_moments(f);
-    relax_raw(m, sx, sy, L, jx_out, jy_out);
-    dr_out = m.m00;
-    populations(m, f);
+    collide_v<float>(f, sx, sy, L.omega, rmul(L.src, 1.0f / 3.0f), dr_out, jx_out, jy_out);
 }
 
 // u(t+1) = u(t) + j/rho with Kahan compensation per component; w holds

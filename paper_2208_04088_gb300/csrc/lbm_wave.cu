@@ -44,7 +44,7 @@ constexpr int kC = kWaveC, kK = kWaveK, kW = kWaveW;
 constexpr int kNI = 8;                // rows of the level-0 ring (and mbarriers)
 constexpr int kD = kNI - 3;           // rows issued ahead of the row level 1 needs
 constexpr int kNU = 2 * kK + kD;      // rows of the node-word and displacement rings
-constexpr int kThreads = kK * kC;
+constexpr int kThreads = kK * kC / 2;  // two columns per thread
 constexpr int kRowF = 9 * kC;         // floats per ring row (nine planes of kC)
 constexpr uint32_t kFRowBytes = kRowF * 4;
 constexpr uint32_t kNwRowBytes = kC * 8;
@@ -220,11 +220,27 @@ __device__ __forceinline__ void simple_pull(const Rows &ld, uint64_t nw,
     }
 }
 
+// Stores the post-collision populations of a lane's two nodes (columns c and
+// c + 32; plane stride `stride`), those that were updated.
+__device__ __forceinline__ void store_pair(float *out, int64_t stride, const F2 f[9], bool a,
+                                           bool b) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        float va, vb;
+        f2_split(f[i], va, vb);
+        if (a) out[i * stride] = va;
+        if (b) out[i * stride + 32] = vb;
+    }
+}
+
 // One launch: kWaveK steps of every material node.  Block b handles the
 // region tab[b] = (X0, Y0, rows, has_boundary): core columns [X0, X0 +
 // kWaveW), core rows [Y0, Y0 + rows); has_boundary says whether a boundary
 // node lies in the region or its halo.  Each warp computes one level of one
-// 32-column chunk of the ring (ring column c is lattice column X0 - kWaveK + c).
+// 64-column half of the ring, two columns per lane, c and c + 32 (ring column c
+// is lattice column X0 - kWaveK + c): their collisions run as one stream of
+// paired (f32x2) operations, and every shared-memory access of a warp stays on
+// consecutive words.
 __global__ void __launch_bounds__(kThreads, 1)
     k_wave(const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tnw,
            const __grid_constant__ CUtensorMap tu, float *__restrict__ dst,
@@ -238,17 +254,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t *nwr = reinterpret_cast<const uint64_t *>(sm + kOffNw);
     const uint32_t bar0 = smem_addr(sm + kOffBar);
 
-    // Warp w runs on sub-partition w % 4 of the SM.  Warp w = 4 l' + s takes
-    // level l' + 1 and column chunk (s - l') mod 4: the warps of one level, and
-    // the warps of one column chunk across the levels, are spread over the four
-    // sub-partitions, so neither a wall row (boundary nodes in every chunk of
-    // a level) nor a wall column (one chunk, every level) piles its boundary
-    // updates onto one of them.
-    static_assert(kC == 128, "four column chunks of 32");
+    // Warp w runs on sub-partition w % 4 of the SM.  Warp w = 2 l' + h' takes
+    // level l' + 1 and half h = h' xor (l' / 2) % 2: the two halves of a level
+    // sit on two sub-partitions, and one half across the levels on all four,
+    // so neither a wall row nor a wall column piles its boundary updates onto
+    // one of them.
+    static_assert(kC == 128 && kThreads == kK * 64, "two halves of 64 columns per level");
     const int tid = threadIdx.x;
-    const int warp = tid >> 5;
-    const int lv = (warp >> 2) + 1;  // time level of this thread (warp-uniform)
-    const int c = ((((warp & 3) - (warp >> 2)) & 3) << 5) | (tid & 31);
+    const int warp = tid >> 5, lane = tid & 31;
+    const int lv = (warp >> 1) + 1;  // time level of this thread (warp-uniform)
+    const int half = (warp ^ (warp >> 2)) & 1;
+    const int c = (half << 6) | lane;  // the lane's columns c, c + 32
     const int4 region = tab[blockIdx.x];
     const int X0 = region.x, Y0 = region.y, Hs = region.z;
     const int xin = X0 - kK;     // lattice column of ring column 0
@@ -256,6 +272,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int j_last = Hs - 1 + 2 * kK;
     const int nsweep = Hs + 3 * kK - 3;
     const float tb = (float)(*time + toff + lv - 2);  // boundary data at the time of f^col
+    const F2 sx2 = f2(L.fx, L.fx), sy2 = f2(L.fy, L.fy);
+    const F2 w2 = splat<F2>(L.omega), s32 = splat<F2>(rmul(L.src, 1.0f / 3.0f));
 
     auto issue = [&](int j) {
         const uint32_t bar = bar0 + 8u * (uint32_t)(j & (kNI - 1));
@@ -289,11 +307,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
 
-    const bool col_live = c >= lv && c < kC - lv;
+    const bool live_a = c >= lv && c < kC - lv;
+    const bool live_b = c + 32 >= lv && c + 32 < kC - lv;
     const int lo = Y0 - (kK - lv), hi = Y0 + Hs - 1 + (kK - lv);
     const float *prev_base = lv == 1 ? in : lev + (size_t)(lv - 2) * 4 * kRowF;
     const int pmask = lv == 1 ? kNI - 1 : 3;
     float *own_base = lev + (size_t)(lv - 1) * 4 * kRowF;  // unused by level kWaveK
+    const bool core_a = c >= kK && c < kC - kK, core_b = c + 32 >= kK && c + 32 < kC - kK;
 
     // The sweep, compiled twice: with the boundary updates, and without them
     // for regions that hold no boundary node (their interior update is then
@@ -315,111 +335,159 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ju = ju_next;
             ju_next = ju + 1 == kNU ? 0 : ju + 1;
             if (y >= lo && y <= hi) {  // warp-uniform: one level per warp
-                const uint64_t nw = col_live ? nwr[ju * kC + c] : 0ull;
-                const uint32_t cl = (uint32_t)(nw & 3u);
-                const float *rm = prev_base + ((j - 1) & pmask) * kRowF;
-                const float *r0 = prev_base + (j & pmask) * kRowF;
-                const float *rp = prev_base + ((j + 1) & pmask) * kRowF;
-                float *own = own_base + (j & 3) * kRowF;
+                const uint64_t nwa = live_a ? nwr[ju * kC + c] : 0ull;
+                const uint64_t nwb = live_b ? nwr[ju * kC + c + 32] : 0ull;
+                const uint32_t cla = (uint32_t)(nwa & 3u), clb = (uint32_t)(nwb & 3u);
+                const float *rm = prev_base + ((j - 1) & pmask) * kRowF + c;
+                const float *r0 = prev_base + (j & pmask) * kRowF + c;
+                const float *rp = prev_base + ((j + 1) & pmask) * kRowF + c;
+                float *own = own_base + (j & 3) * kRowF + c;
                 const bool core_row = y >= Y0 && y < Y0 + Hs;
+                const int64_t grow = (int64_t)y * L.pitch + xin + c;  // lattice index of column c
                 // the row's update, compiled with and without the boundary
                 // updates; a warp takes the second unless its row holds a
                 // boundary node, so rows inside the material run the plain
                 // interior update
                 auto row = [&](auto with_boundary_row) {
                     constexpr bool kR = decltype(with_boundary_row)::value;
-                    const bool simple_b = kR && cl == kBoundary && ((nw >> 34) & 1u);
-                    if (cl == kInterior || simple_b) {
-                        float f[9];
-                        float dr, jx, jy;
-                        if (!kR || cl == kInterior) {
-                            f[0] = r0[c];
-                            f[1] = r0[kC + c - 1];
-                            f[2] = rm[2 * kC + c];
-                            f[3] = r0[3 * kC + c + 1];
-                            f[4] = rp[4 * kC + c];
-                            f[5] = rm[5 * kC + c - 1];
-                            f[6] = rm[6 * kC + c + 1];
-                            f[7] = rp[7 * kC + c + 1];
-                            f[8] = rp[8 * kC + c - 1];
+                    const bool sim_a = kR && cla == kBoundary && ((nwa >> 34) & 1u);
+                    const bool sim_b = kR && clb == kBoundary && ((nwb >> 34) & 1u);
+                    const bool do_a = cla == kInterior || sim_a, do_b = clb == kInterior || sim_b;
+                    if (do_a || do_b) {
+                        F2 f[9];
+                        if (!kR || (cla == kInterior && clb == kInterior)) {
+                            // pulls of both nodes (a node of the pair that is not
+                            // updated reads in-bounds values it never stores)
+                            auto ld2 = [](const float *r) { return f2(r[0], r[32]); };
+                            f[0] = ld2(r0);
+                            f[1] = ld2(r0 + kC - 1);
+                            f[2] = ld2(rm + 2 * kC);
+                            f[3] = ld2(r0 + 3 * kC + 1);
+                            f[4] = ld2(rp + 4 * kC);
+                            f[5] = ld2(rm + 5 * kC - 1);
+                            f[6] = ld2(rm + 6 * kC + 1);
+                            f[7] = ld2(rp + 7 * kC + 1);
+                            f[8] = ld2(rp + 8 * kC - 1);
                         } else {
-                            simple_pull(Rows{rm, r0, rp, c}, nw, bcs, tb, L, f);
-                        }
-                        collide(f, L.fx, L.fy, L, dr, jx, jy);
-                        if (lv < kK) {
-        #pragma unroll
-                            for (int i = 0; i < 9; ++i) own[i * kC + c] = f[i];
-                        } else {
-        #pragma unroll
-                            for (int i = 0; i < 9; ++i) dst[i * L.plane + ((int64_t)y * L.pitch + xin) + c] = f[i];
-                        }
-                        if (core_row && c >= kK && c < kC - kK) {
-                            float4 *up = ur + ju * kW + (c - kK);
-                            float4 w = *up;
-                            integrate_u_value(w, jx, jy, L.rho0 + dr);
-                            if (lv < kK) {
-                                *up = w;
-                            } else {
-                                uc[(int64_t)y * L.pitch + xin + c] = w;
-                                flag_nonfinite(status, dr, jx, jy);
+                            // one of the pair is a simple boundary node: each node
+                            // pulled on its own (one copy of the code), then the
+                            // pair collides together
+#pragma unroll
+                            for (int i = 0; i < 9; ++i) f[i] = f2(0.0f, 0.0f);
+#pragma unroll 1
+                            for (int h = 0; h < 2; ++h) {
+                                float g[9];
+                                const int dc = h << 5;
+                                if (h ? sim_b : sim_a) {
+                                    simple_pull(Rows{rm - c, r0 - c, rp - c, c + dc}, h ? nwb : nwa,
+                                                bcs, tb, L, g);
+                                } else {
+                                    g[0] = r0[dc];
+                                    g[1] = r0[kC + dc - 1];
+                                    g[2] = rm[2 * kC + dc];
+                                    g[3] = r0[3 * kC + dc + 1];
+                                    g[4] = rp[4 * kC + dc];
+                                    g[5] = rm[5 * kC + dc - 1];
+                                    g[6] = rm[6 * kC + dc + 1];
+                                    g[7] = rp[7 * kC + dc + 1];
+                                    g[8] = rp[8 * kC + dc - 1];
+                                }
+#pragma unroll
+                                for (int i = 0; i < 9; ++i) {
+                                    float va, vb;
+                                    f2_split(f[i], va, vb);
+                                    f[i] = h ? f2(va, g[i]) : f2(g[i], vb);
+                                }
                             }
+                        }
+                        F2 dr, jx, jy;
+                        collide_v(f, sx2, sy2, w2, s32, dr, jx, jy);
+                        if (lv < kK)
+                            store_pair(own, kC, f, do_a, do_b);
+                        else
+                            store_pair(dst + grow, L.plane, f, do_a, do_b);
+                        if (core_row) {
+                            float dra, drb, jxa, jxb, jya, jyb;
+                            f2_split(dr, dra, drb);
+                            f2_split(jx, jxa, jxb);
+                            f2_split(jy, jya, jyb);
+                            auto u_one = [&](int dc, float d, float mx, float my) {
+                                float4 *up = ur + ju * kW + (c + dc - kK);
+                                float4 w = *up;
+                                integrate_u_value(w, mx, my, L.rho0 + d);
+                                if (lv < kK) {
+                                    *up = w;
+                                } else {
+                                    uc[grow + dc] = w;
+                                    flag_nonfinite(status, d, mx, my);
+                                }
+                            };
+                            if (do_a && core_a) u_one(0, dra, jxa, jya);
+                            if (do_b && core_b) u_one(32, drb, jxb, jyb);
                         }
                     }
                     // the other boundary nodes of the warp (curved walls, corners): eight
                     // lanes each, the update of the cooperative boundary kernel (four
-                    // nodes per pass)
-                    const unsigned bmask =
-                        kR ? __ballot_sync(0xffffffffu, cl == kBoundary && !simple_b) : 0u;
-                    if (kR && bmask) {  // warp-uniform
-                        const int lane = tid & 31, grp = lane >> 3, kdir = (lane & 7) + 1;
-                        const bool lane0 = kdir == 1;  // lane 0 of the group stores f_0 and u
-                        unsigned rem = bmask;
-                        while (rem) {
-                            // group g takes the g-th remaining node; spare groups redo the
-                            // first one and store nothing
-                            unsigned r = rem;
-                            for (int q = 0; q < grp; ++q) r &= r - 1;
-                            const bool live = r != 0;
-                            const int src = __ffs(live ? r : rem) - 1;
-                            for (int q = 0; q < 4; ++q) rem &= rem - 1;
-                            const uint64_t wb = __shfl_sync(0xffffffffu, nw, src);
-                            const int cb = (c & ~31) + src;
-                            const bool simple = (wb >> 34) & 1u;
-                            const uint32_t hi = (uint32_t)(wb >> 35);
-                            const BLink sl = simple_link(hi);
-                            const BLink *lrec = blinks + (int64_t)hi * 8;
-                            auto link = [&](int i) { return simple ? sl : lrec[i - 1]; };
-                            float f0;
-                            const float fk = boundary8_pull(Rows{rm, r0, rp, cb}, nw_mask(wb, 2),
-                                                            nw_mask(wb, 10), nw_mask(wb, 18),
-                                                            nw_mask(wb, 26), kdir, link, bcs, tb, L, f0);
-                            float fr, jx, jy, m00;
-                            const float mine =
-                                boundary8_collide(fk, f0, kdir, L.fx, L.fy, L, fr, jx, jy, m00);
-                            if (live) {
-                                if (lv < kK) {
-                                    own[kdir * kC + cb] = mine;
-                                    if (lane0) own[cb] = fr;
-                                } else {
-                                    dst[kdir * L.plane + ((int64_t)y * L.pitch + xin) + cb] = mine;
-                                    if (lane0) dst[(int64_t)y * L.pitch + xin + cb] = fr;
-                                }
-                                if (lane0 && core_row && cb >= kK && cb < kC - kK) {
-                                    float4 *up = ur + ju * kW + (cb - kK);
-                                    float4 w = *up;
-                                    integrate_u_value(w, jx, jy, L.rho0 + m00);
+                    // nodes per pass); node m of the 64 is column m of the half
+                    if (kR) {
+                        const bool cx_a = cla == kBoundary && !sim_a, cx_b = clb == kBoundary && !sim_b;
+                        const unsigned ma = __ballot_sync(0xffffffffu, cx_a);
+                        const unsigned mb = __ballot_sync(0xffffffffu, cx_b);
+                        if (ma | mb) {  // warp-uniform
+                            const int grp = lane >> 3, kdir = (lane & 7) + 1;
+                            const bool lane0 = kdir == 1;  // lane 0 of the group stores f_0 and u
+                            unsigned long long rem = ((unsigned long long)mb << 32) | ma;
+                            while (rem) {
+                                // group g takes the g-th remaining node; spare groups redo
+                                // the first one and store nothing
+                                unsigned long long r = rem;
+                                for (int q = 0; q < grp; ++q) r &= r - 1;
+                                const bool live = r != 0;
+                                const int m = __ffsll((long long)(live ? r : rem)) - 1;
+                                for (int q = 0; q < 4; ++q) rem &= rem - 1;
+                                const int src = m & 31, hb = m >> 5;
+                                const uint64_t wa = __shfl_sync(0xffffffffu, nwa, src);
+                                const uint64_t wbb = __shfl_sync(0xffffffffu, nwb, src);
+                                const uint64_t wb = hb ? wbb : wa;
+                                const int cb = (half << 6) + m;
+                                const bool simple = (wb >> 34) & 1u;
+                                const uint32_t bh = (uint32_t)(wb >> 35);
+                                const BLink sl = simple_link(bh);
+                                const BLink *lrec = blinks + (int64_t)bh * 8;
+                                auto link = [&](int i) { return simple ? sl : lrec[i - 1]; };
+                                float f0;
+                                const float fk = boundary8_pull(
+                                    Rows{rm - c, r0 - c, rp - c, cb}, nw_mask(wb, 2), nw_mask(wb, 10),
+                                    nw_mask(wb, 18), nw_mask(wb, 26), kdir, link, bcs, tb, L, f0);
+                                float fr, jx, jy, m00;
+                                const float mine =
+                                    boundary8_collide(fk, f0, kdir, L.fx, L.fy, L, fr, jx, jy, m00);
+                                if (live) {
+                                    const int64_t gb = (int64_t)y * L.pitch + xin + cb;
                                     if (lv < kK) {
-                                        *up = w;
+                                        own[kdir * kC + cb - c] = mine;
+                                        if (lane0) own[cb - c] = fr;
                                     } else {
-                                        uc[(int64_t)y * L.pitch + xin + cb] = w;
-                                        flag_nonfinite(status, m00, jx, jy);
+                                        dst[kdir * L.plane + gb] = mine;
+                                        if (lane0) dst[gb] = fr;
+                                    }
+                                    if (lane0 && core_row && cb >= kK && cb < kC - kK) {
+                                        float4 *up = ur + ju * kW + (cb - kK);
+                                        float4 w = *up;
+                                        integrate_u_value(w, jx, jy, L.rho0 + m00);
+                                        if (lv < kK) {
+                                            *up = w;
+                                        } else {
+                                            uc[gb] = w;
+                                            flag_nonfinite(status, m00, jx, jy);
+                                        }
                                     }
                                 }
                             }
                         }
                     }
                 };
-                if (kB && __ballot_sync(0xffffffffu, cl == kBoundary))
+                if (kB && __ballot_sync(0xffffffffu, cla == kBoundary || clb == kBoundary))
                     row(std::true_type{});
                 else
                     row(std::false_type{});
