@@ -141,7 +141,7 @@ typedef struct {
     int32_t time_block;  /* time steps fused into one kernel launch:
                             0  library default: LBM_TIME_BLOCK where it is the
                                faster form (supported, lambda = mu, at least 2^21
-                               nodes, at most one boundary node per 1536 nodes that
+                               nodes, at most one boundary node per 800 nodes that
                                is not on a box edge or crack face); else 1
                             1  one launch per step (bulk and boundary-list kernels)
                             LBM_TIME_BLOCK  temporal blocking: each launch carries
@@ -202,7 +202,10 @@ lbm_status lbm_workspace_size(const lbm_desc *desc, uint64_t *bytes);
  * lbm_workspace_size() bytes, 256-byte aligned, owned by the caller and kept
  * alive until lbm_destroy; otherwise the library allocates with cudaMalloc.
  * The caller keeps ownership of every host array; none is referenced after
- * return.  Synchronises the stream before returning. */
+ * return.  With temporal blocking, three blocked launches on the zero state
+ * measure the SM cycles of every block and the strips are re-cut to balance
+ * them (a launch plan with the smallest measured maximum is kept); the state
+ * is then reset.  Synchronises the stream before returning. */
 lbm_status lbm_create(const lbm_desc *desc, void *stream, void *workspace,
                       uint64_t workspace_bytes, lbm_handle *out);
 

@@ -52,12 +52,12 @@ int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
     // warps per row step: 34 vs 45 GLUPS on the 2048^2 crack), lattices of at
     // least 2^21 nodes (below, the fill of each block's row pipeline dominates:
     // 1024^2 plate 29 vs 80 GLUPS), and at most one boundary node off box edges
-    // and crack faces per 1536 nodes: the blocked kernel updates those eight
-    // lanes to a node at every level (2048^2 plates with a hole: radius 256,
-    // one per 2040 nodes, 84 vs 62 GLUPS; radius 512, one per 1022, 55 vs 59).
+    // and crack faces per 800 nodes: the blocked kernel updates those eight
+    // lanes to a node at every level (2048^2 plates with a hole: radius 512,
+    // one per 1022 nodes, 74 vs 59 GLUPS; radius 900, one per 582, 34 vs 48).
     const int64_t nodes = (int64_t)t.nx * t.ny;
     const bool faster = u.lam == u.mu && nodes >= ((int64_t)1 << 21) &&
-                        complex_boundary_nodes(t) * 1536 <= nodes;
+                        complex_boundary_nodes(t) * 800 <= nodes;
     return ok && faster ? k : 1;
 }
 
@@ -86,7 +86,8 @@ Layout layout(const Tables &t, int storage, bool grad, int block) {
     l.probe = take(7 * (size_t)kMaxProbe * sizeof(float));
     l.probe_idx = take((size_t)kMaxProbe * sizeof(int32_t));
     l.nw = block > 1 ? take(plane * sizeof(uint64_t)) : 0;
-    l.wave_tab = block > 1 ? take(wave_table_entries(t.nx, t.ny) * sizeof(int4)) : 0;
+    l.wave_tab =
+        block > 1 ? take(wave_table_entries(t.nx, t.ny) * (sizeof(int4) + sizeof(long long))) : 0;
     l.total = o;
     return l;
 }
@@ -272,6 +273,9 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
     S.probe_idx = reinterpret_cast<int32_t *>(b + lay.probe_idx);
     S.nw = h->block > 1 ? reinterpret_cast<uint64_t *>(b + lay.nw) : nullptr;
     S.wave_tab = h->block > 1 ? reinterpret_cast<int4 *>(b + lay.wave_tab) : nullptr;
+    S.wave_cyc = h->block > 1 ? reinterpret_cast<long long *>(
+                                    b + lay.wave_tab + wave_table_entries(h->tab.nx, h->tab.ny) * sizeof(int4))
+                              : nullptr;
 
     auto fail = [&](cudaError_t err, const char *where) {
         lbm_status s = cuda_fail(err, where);
@@ -300,6 +304,8 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
             h->block = 1;  // default: fall back to one step per launch
         } else {
             e = wave_prepare(h->tab, h->L, S, &h->wave, h->stream);
+            if (e == cudaSuccess) e = wave_calibrate(h->tab, h->L, S, &h->wave, h->stream);
+            if (e == cudaSuccess) e = launch_reset(h->storage, h->L, S, h->stream);
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -113,6 +113,7 @@ struct DevState {
     int32_t *probe_idx = nullptr;
     uint64_t *nw = nullptr;           // per-node words of the temporally blocked kernel
     int4 *wave_tab = nullptr;         // blocks of a temporally blocked launch
+    long long *wave_cyc = nullptr;    // per-block SM cycles of a calibration launch
 };
 
 constexpr int kMaxProbe = 4096;
@@ -157,7 +158,7 @@ bool wave_supported(const Lattice &L);
 // the source needs the density gradient (lambda != mu).
 constexpr int kWaveGradK = 4;
 size_t wave_smem_bytes();
-// Upper bound of the blocks of one launch (entries of S.wave_tab).
+// Upper bound of the blocks of one launch (entries of S.wave_tab and S.wave_cyc).
 size_t wave_table_entries(int nx, int ny);
 // Whether boundary node g takes the blocked kernel's eight-lane update (curved
 // walls, corners, crack mouth) rather than the one-lane update of a mid-link
@@ -170,10 +171,19 @@ std::vector<int4> wave_plan(const Tables &t, int sms);
 // plane) and S.wave_tab must be allocated.
 cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, WaveMaps *m,
                          cudaStream_t s);
+// Balances the blocks of a launch by measurement: blocked launches from
+// buffer 0 record each block's SM cycles, the modelled cost of every row is
+// scaled by its block's measured/modelled ratio and the strips are cut again
+// (twice); the plan with the smallest measured maximum is kept in
+// S.wave_tab.  Leaves f[1], the displacements and the status word modified:
+// the caller resets the state.
+cudaError_t wave_calibrate(const Tables &t, const Lattice &L, const DevState &S, WaveMaps *m,
+                           cudaStream_t s);
 // kWaveK steps from buffer `cur` into buffer cur ^ 1; the first of them is
-// step `toff` after *S.time.
+// step `toff` after *S.time.  With `cycles`, block b stores its SM cycles in
+// cycles[b].
 cudaError_t launch_wave(const Lattice &L, const DevState &S, const WaveMaps &m, int cur, int toff,
-                        cudaStream_t s);
+                        cudaStream_t s, long long *cycles = nullptr);
 
 }  // namespace lbm
 

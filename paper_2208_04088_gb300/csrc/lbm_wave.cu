@@ -246,8 +246,10 @@ __global__ void __launch_bounds__(kThreads, 1)
            const __grid_constant__ CUtensorMap tu, float *__restrict__ dst,
            float4 *__restrict__ uc, const BLink *__restrict__ blinks,
            const BCDev *__restrict__ bcs, Lattice L, const int64_t *__restrict__ time, int toff,
-           const int4 *__restrict__ tab, uint32_t *__restrict__ status) {
+           const int4 *__restrict__ tab, uint32_t *__restrict__ status,
+           long long *__restrict__ cycles) {
     extern __shared__ __align__(1024) unsigned char sm[];
+    const long long t_start = clock64();
     float *in = reinterpret_cast<float *>(sm + kOffIn);
     float *lev = reinterpret_cast<float *>(sm + kOffLev);
     float4 *ur = reinterpret_cast<float4 *>(sm + kOffU);
@@ -353,6 +355,68 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const bool sim_a = kR && cla == kBoundary && ((nwa >> 34) & 1u);
                     const bool sim_b = kR && clb == kBoundary && ((nwb >> 34) & 1u);
                     const bool do_a = cla == kInterior || sim_a, do_b = clb == kInterior || sim_b;
+                    // the other boundary nodes of the warp (curved walls, corners): eight
+                    // lanes each, the update of the cooperative boundary kernel (four
+                    // nodes per pass); node m of the 64 is column m of the half.  They
+                    // go first: their long dependent chains then overlap the other
+                    // warps' updates instead of delaying the row's barrier.
+                    if (kR) {
+                        const bool cx_a = cla == kBoundary && !sim_a, cx_b = clb == kBoundary && !sim_b;
+                        const unsigned ma = __ballot_sync(0xffffffffu, cx_a);
+                        const unsigned mb = __ballot_sync(0xffffffffu, cx_b);
+                        if (ma | mb) {  // warp-uniform
+                            const int grp = lane >> 3, kdir = (lane & 7) + 1;
+                            const bool lane0 = kdir == 1;  // lane 0 of the group stores f_0 and u
+                            unsigned long long rem = ((unsigned long long)mb << 32) | ma;
+                            while (rem) {
+                                // group g takes the g-th remaining node; spare groups redo
+                                // the first one and store nothing
+                                unsigned long long r = rem;
+                                for (int q = 0; q < grp; ++q) r &= r - 1;
+                                const bool live = r != 0;
+                                const int m = __ffsll((long long)(live ? r : rem)) - 1;
+                                for (int q = 0; q < 4; ++q) rem &= rem - 1;
+                                const int src = m & 31, hb = m >> 5;
+                                const uint64_t wa = __shfl_sync(0xffffffffu, nwa, src);
+                                const uint64_t wbb = __shfl_sync(0xffffffffu, nwb, src);
+                                const uint64_t wb = hb ? wbb : wa;
+                                const int cb = (half << 6) + m;
+                                const bool simple = (wb >> 34) & 1u;
+                                const uint32_t bh = (uint32_t)(wb >> 35);
+                                const BLink sl = simple_link(bh);
+                                const BLink *lrec = blinks + (int64_t)bh * 8;
+                                auto link = [&](int i) { return simple ? sl : lrec[i - 1]; };
+                                float f0;
+                                const float fk = boundary8_pull(
+                                    Rows{rm - c, r0 - c, rp - c, cb}, nw_mask(wb, 2), nw_mask(wb, 10),
+                                    nw_mask(wb, 18), nw_mask(wb, 26), kdir, link, bcs, tb, L, f0);
+                                float fr, jx, jy, m00;
+                                const float mine =
+                                    boundary8_collide(fk, f0, kdir, L.fx, L.fy, L, fr, jx, jy, m00);
+                                if (live) {
+                                    const int64_t gb = (int64_t)y * L.pitch + xin + cb;
+                                    if (lv < kK) {
+                                        own[kdir * kC + cb - c] = mine;
+                                        if (lane0) own[cb - c] = fr;
+                                    } else {
+                                        dst[kdir * L.plane + gb] = mine;
+                                        if (lane0) dst[gb] = fr;
+                                    }
+                                    if (lane0 && core_row && cb >= kK && cb < kC - kK) {
+                                        float4 *up = ur + ju * kW + (cb - kK);
+                                        float4 w = *up;
+                                        integrate_u_value(w, jx, jy, L.rho0 + m00);
+                                        if (lv < kK) {
+                                            *up = w;
+                                        } else {
+                                            uc[gb] = w;
+                                            flag_nonfinite(status, m00, jx, jy);
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    }
                     if (do_a || do_b) {
                         F2 f[9];
                         if (!kR || (cla == kInterior && clb == kInterior)) {
@@ -426,66 +490,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (do_b && core_b) u_one(32, drb, jxb, jyb);
                         }
                     }
-                    // the other boundary nodes of the warp (curved walls, corners): eight
-                    // lanes each, the update of the cooperative boundary kernel (four
-                    // nodes per pass); node m of the 64 is column m of the half
-                    if (kR) {
-                        const bool cx_a = cla == kBoundary && !sim_a, cx_b = clb == kBoundary && !sim_b;
-                        const unsigned ma = __ballot_sync(0xffffffffu, cx_a);
-                        const unsigned mb = __ballot_sync(0xffffffffu, cx_b);
-                        if (ma | mb) {  // warp-uniform
-                            const int grp = lane >> 3, kdir = (lane & 7) + 1;
-                            const bool lane0 = kdir == 1;  // lane 0 of the group stores f_0 and u
-                            unsigned long long rem = ((unsigned long long)mb << 32) | ma;
-                            while (rem) {
-                                // group g takes the g-th remaining node; spare groups redo
-                                // the first one and store nothing
-                                unsigned long long r = rem;
-                                for (int q = 0; q < grp; ++q) r &= r - 1;
-                                const bool live = r != 0;
-                                const int m = __ffsll((long long)(live ? r : rem)) - 1;
-                                for (int q = 0; q < 4; ++q) rem &= rem - 1;
-                                const int src = m & 31, hb = m >> 5;
-                                const uint64_t wa = __shfl_sync(0xffffffffu, nwa, src);
-                                const uint64_t wbb = __shfl_sync(0xffffffffu, nwb, src);
-                                const uint64_t wb = hb ? wbb : wa;
-                                const int cb = (half << 6) + m;
-                                const bool simple = (wb >> 34) & 1u;
-                                const uint32_t bh = (uint32_t)(wb >> 35);
-                                const BLink sl = simple_link(bh);
-                                const BLink *lrec = blinks + (int64_t)bh * 8;
-                                auto link = [&](int i) { return simple ? sl : lrec[i - 1]; };
-                                float f0;
-                                const float fk = boundary8_pull(
-                                    Rows{rm - c, r0 - c, rp - c, cb}, nw_mask(wb, 2), nw_mask(wb, 10),
-                                    nw_mask(wb, 18), nw_mask(wb, 26), kdir, link, bcs, tb, L, f0);
-                                float fr, jx, jy, m00;
-                                const float mine =
-                                    boundary8_collide(fk, f0, kdir, L.fx, L.fy, L, fr, jx, jy, m00);
-                                if (live) {
-                                    const int64_t gb = (int64_t)y * L.pitch + xin + cb;
-                                    if (lv < kK) {
-                                        own[kdir * kC + cb - c] = mine;
-                                        if (lane0) own[cb - c] = fr;
-                                    } else {
-                                        dst[kdir * L.plane + gb] = mine;
-                                        if (lane0) dst[gb] = fr;
-                                    }
-                                    if (lane0 && core_row && cb >= kK && cb < kC - kK) {
-                                        float4 *up = ur + ju * kW + (cb - kK);
-                                        float4 w = *up;
-                                        integrate_u_value(w, jx, jy, L.rho0 + m00);
-                                        if (lv < kK) {
-                                            *up = w;
-                                        } else {
-                                            uc[gb] = w;
-                                            flag_nonfinite(status, m00, jx, jy);
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                    }
                 };
                 if (kB && __ballot_sync(0xffffffffu, cla == kBoundary || clb == kBoundary))
                     row(std::true_type{});
@@ -503,6 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         sweep(std::true_type{});
     else
         sweep(std::false_type{});
+    if (cycles && tid == 0) cycles[blockIdx.x] = clock64() - t_start;
     if (tid == 0 && !ok) {
         // a copy did not land in time: flag it, and give the copies still in
         // flight a bounded chance to land before the block's shared memory goes
@@ -574,8 +579,10 @@ __global__ void __launch_bounds__(kGradThreads, 1)
                 const __grid_constant__ CUtensorMap tu, float *__restrict__ dst,
                 float4 *__restrict__ uc, const BLink *__restrict__ blinks,
                 const BCDev *__restrict__ bcs, Lattice L, const int64_t *__restrict__ time,
-                int toff, const int4 *__restrict__ tab, uint32_t *__restrict__ status) {
+                int toff, const int4 *__restrict__ tab, uint32_t *__restrict__ status,
+           long long *__restrict__ cycles) {
     extern __shared__ __align__(1024) unsigned char sm[];
+    const long long t_start = clock64();
     float *in = reinterpret_cast<float *>(sm + kGOffIn);
     float *lev = reinterpret_cast<float *>(sm + kGOffLev);
     float *den = reinterpret_cast<float *>(sm + kGOffDen);
@@ -774,6 +781,7 @@ __global__ void __launch_bounds__(kGradThreads, 1)
         }
         __syncthreads();
     }
+    if (cycles && tid == 0) cycles[blockIdx.x] = clock64() - t_start;
     if (tid == 0 && !ok) {
         // a copy did not land in time: flag it, and give the copies still in
         // flight a bounded chance to land before the block's shared memory goes
@@ -869,23 +877,21 @@ size_t wave_table_entries(int nx, int ny) {
 
 // The blocks of one launch.  Every strip of kWaveW columns is cut into row
 // segments; a segment sweeps 3 kWaveK - 3 rows more than it owns.  The cost of
-// a block is modelled in row sweeps, measured on GB300 (2048^2 crack):
-//   - a row costs 1, or kWallRowCost in a strip that a wall column runs
-//     through (boundary nodes in at least half of its rows, e.g. a box edge:
-//     that wall is updated in every row and level);
-//   - a row in which at least a quarter of the region's columns are boundary
-//     nodes (a wall along the row: box edge, crack face) adds kWallRowPenalty,
-//     counted also when it lies in the segment's halo;
-//   - curved-wall, corner and crack-mouth nodes (the 8-lane update, four
-//     nodes per pass in each 32-column chunk) add kComplexPassCost per pass
-//     of the row's busiest chunk.
+// a block is modelled in row sweeps, from per-block cycle counts measured on
+// GB300 (edge and centre cracks, plates with holes of radius 64 to 512):
+//   - each row of the sweep costs 1, and the block kBlockCost more;
+//   - a row's 64-column half of the region (one warp per level) that holds a
+//     boundary node takes the boundary update: kHalfRowCost, counted also in
+//     the segment's halo rows;
+//   - curved-wall, corner and crack-mouth nodes (the 8-lane update, four nodes
+//     per pass in each half) add kPassCost per pass.
 // Segments are cut greedily against a target cost, and the smallest target for
 // which all blocks fit one wave on `sms` SMs (one block per SM) is found by
 // bisection.  Each entry also says whether a boundary node lies in the
 // block's region or halo.
-constexpr double kWallRowCost = 2.3;
-constexpr double kWallRowPenalty = 65.0;
-constexpr double kComplexPassCost = 4.0;
+constexpr double kBlockCost = 6.0;
+constexpr double kHalfRowCost = 1.0;
+constexpr double kPassCost = 5.5;
 
 // A boundary node the blocked kernel updates eight lanes to a node (curved
 // walls, corners, crack mouth): not every cut link is a mid-link wall of one
@@ -912,72 +918,58 @@ bool complex_boundary_node(const Tables &t, size_t g) {
     return bc < 0;
 }
 
-std::vector<int4> wave_plan(const Tables &t, int sms) {
-    const int nx = t.nx, ny = t.ny;
-    const int nstrips = (nx + kW - 1) / kW;
-    std::vector<int64_t> per_strip(nstrips, 0);
-    // boundary rows seen by each strip's region (core and halo columns)
-    std::vector<std::vector<int>> rows(nstrips);
-    // complex nodes as (row, 32-column chunk of the region) keys per strip
-    std::vector<std::vector<int64_t>> ckeys(nstrips);
+namespace {
+
+// Modelled extra cost (row sweeps) of each row of every strip: the boundary
+// update of each 64-column half holding a boundary node, and the passes of
+// the 8-lane update.  Rows sorted, with prefix sums.
+struct StripRows {
+    std::vector<std::vector<int>> row;
+    std::vector<std::vector<double>> pre;
+};
+
+StripRows strip_rows(const Tables &t, int nstrips) {
+    // boundary nodes seen by each strip's region (core and halo columns), as
+    // keys row * 4 + half * 2 + curved
+    std::vector<std::vector<int64_t>> keys(nstrips);
     for (size_t g = 0; g < t.bnodes.size(); ++g) {
         const BNode &b = t.bnodes[g];
-        per_strip[b.x / kW] += 1;
-        const bool cx = complex_boundary_node(t, g);
+        const int64_t cx = complex_boundary_node(t, g) ? 1 : 0;
         const int s_lo = std::max(0, (b.x - kK) / kW), s_hi = std::min(nstrips - 1, (b.x + kK) / kW);
         for (int sx = s_lo; sx <= s_hi; ++sx) {
             const int X0 = sx * kW;
-            if (b.x >= X0 - kK && b.x < X0 + kW + kK) {
-                rows[sx].push_back(b.y);
-                if (cx) ckeys[sx].push_back((int64_t)b.y * 4 + (b.x - X0 + kK) / 32);
-            }
+            if (b.x >= X0 - kK && b.x < X0 + kW + kK)
+                keys[sx].push_back((int64_t)b.y * 4 + ((b.x - X0 + kK) >> 6) * 2 + cx);
         }
     }
-    // passes of the busiest chunk per row, as sorted rows and prefix sums
-    std::vector<std::vector<int>> crow(nstrips);
-    std::vector<std::vector<double>> cpre(nstrips);
+    StripRows r;
+    r.row.resize(nstrips);
+    r.pre.resize(nstrips);
     for (int sx = 0; sx < nstrips; ++sx) {
-        auto &k = ckeys[sx];
+        auto &k = keys[sx];
         std::sort(k.begin(), k.end());
-        cpre[sx].push_back(0.0);
+        r.pre[sx].push_back(0.0);
         for (size_t a = 0; a < k.size();) {
-            const int64_t y = k[a] / 4;
-            int passes = 0;
-            while (a < k.size() && k[a] / 4 == y) {
-                size_t b = a;
-                while (b < k.size() && k[b] == k[a]) ++b;
-                passes = std::max(passes, (int)(b - a + 3) / 4);
-                a = b;
+            const int64_t y = k[a] >> 2;
+            double extra = 0.0;
+            while (a < k.size() && (k[a] >> 2) == y) {  // one half of row y
+                const int64_t hk = k[a] >> 1;
+                int curved = 0;
+                for (; a < k.size() && (k[a] >> 1) == hk; ++a) curved += (int)(k[a] & 1);
+                extra += kHalfRowCost + kPassCost * (double)((curved + 3) / 4);
             }
-            crow[sx].push_back((int)y);
-            cpre[sx].push_back(cpre[sx].back() + passes);
+            r.row[sx].push_back((int)y);
+            r.pre[sx].push_back(r.pre[sx].back() + extra);
         }
     }
-    std::vector<double> row_cost(nstrips);
-    std::vector<std::vector<int>> dense(nstrips);  // rows with a wall along them, sorted
-    for (int sx = 0; sx < nstrips; ++sx) {
-        auto &r = rows[sx];
-        std::sort(r.begin(), r.end());
-        for (size_t a = 0; a < r.size();) {
-            size_t b = a;
-            while (b < r.size() && r[b] == r[a]) ++b;
-            if ((int)(b - a) * 4 >= kC) dense[sx].push_back(r[a]);
-            a = b;
-        }
-        row_cost[sx] = 2 * per_strip[sx] >= ny ? kWallRowCost : 1.0;
-    }
-    // cost of the block owning rows [a, b) of strip sx
-    auto cost = [&](int sx, int a, int b) {
-        const auto &d = dense[sx];
-        const auto lo = std::lower_bound(d.begin(), d.end(), a - kK);
-        const auto hi = std::lower_bound(d.begin(), d.end(), b + kK);
-        const auto &cr = crow[sx];
-        const size_t clo = std::lower_bound(cr.begin(), cr.end(), a - kK) - cr.begin();
-        const size_t chi = std::lower_bound(cr.begin(), cr.end(), b + kK) - cr.begin();
-        return row_cost[sx] * (b - a + 3 * kK - 3) + kWallRowPenalty * (double)(hi - lo) +
-               kComplexPassCost * (cpre[sx][chi] - cpre[sx][clo]);
-    };
-    // greedy cut of strip sx against target T (every segment at least one row)
+    return r;
+}
+
+// Cuts every strip into segments greedily against a target cost (cost(sx, a,
+// b) of the segment owning rows [a, b)); the smallest target for which the
+// blocks fit `budget` is found by bisection.
+template <class Cost>
+std::vector<int4> cut_strips(const StripRows &br, int nstrips, int ny, int budget, Cost cost) {
     auto cut = [&](int sx, double T, std::vector<int> *ends) {
         int count = 0;
         for (int a = 0; a < ny;) {
@@ -1000,7 +992,6 @@ std::vector<int4> wave_plan(const Tables &t, int sms) {
         for (int sx = 0; sx < nstrips; ++sx) n += cut(sx, T, nullptr);
         return n;
     };
-    const int budget = std::max(sms, nstrips);
     double hi_T = 0.0, lo_T = 0.0;
     for (int sx = 0; sx < nstrips; ++sx) hi_T = std::max(hi_T, cost(sx, 0, ny));
     for (int it = 0; it < 48; ++it) {
@@ -1015,7 +1006,7 @@ std::vector<int4> wave_plan(const Tables &t, int sms) {
         int Y0 = 0;
         for (int e : ends) {
             const int Hs = e - Y0;
-            const auto &r = rows[sx];
+            const auto &r = br.row[sx];
             const auto it = std::lower_bound(r.begin(), r.end(), Y0 - kK);
             const int has = (it != r.end() && *it < Y0 + Hs + kK) ? 1 : 0;
             out.push_back(make_int4(sx * kW, Y0, Hs, has));
@@ -1025,6 +1016,106 @@ std::vector<int4> wave_plan(const Tables &t, int sms) {
     // heavy blocks first
     std::stable_sort(out.begin(), out.end(), [](const int4 &a, const int4 &b) { return a.w > b.w; });
     return out;
+}
+
+int device_sms() {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    return sms;
+}
+
+}  // namespace
+
+std::vector<int4> wave_plan(const Tables &t, int sms) {
+    const int nx = t.nx, ny = t.ny;
+    const int nstrips = (nx + kW - 1) / kW;
+    const StripRows br = strip_rows(t, nstrips);
+    auto cost = [&](int sx, int a, int b) {
+        const auto &r = br.row[sx];
+        const size_t lo = std::lower_bound(r.begin(), r.end(), a - kK) - r.begin();
+        const size_t hi = std::lower_bound(r.begin(), r.end(), b + kK) - r.begin();
+        return (double)(b - a + 3 * kK - 3) + kBlockCost + (br.pre[sx][hi] - br.pre[sx][lo]);
+    };
+    return cut_strips(br, nstrips, ny, std::max(sms, nstrips), cost);
+}
+
+cudaError_t wave_calibrate(const Tables &t, const Lattice &L, const DevState &S, WaveMaps *m,
+                           cudaStream_t s) {
+    const int nx = t.nx, ny = t.ny;
+    const int nstrips = (nx + kW - 1) / kW;
+    const int budget = std::max(device_sms(), nstrips);
+    const StripRows br = strip_rows(t, nstrips);
+    // per strip and row: the modelled extra cost, and the measured/modelled
+    // ratio of the block that owned the row (1 before any measurement)
+    std::vector<std::vector<double>> extra(nstrips, std::vector<double>(ny, 0.0));
+    for (int sx = 0; sx < nstrips; ++sx)
+        for (size_t i = 0; i < br.row[sx].size(); ++i) {
+            const int y = br.row[sx][i];
+            if (y >= 0 && y < ny) extra[sx][y] = br.pre[sx][i + 1] - br.pre[sx][i];
+        }
+    std::vector<std::vector<double>> ratio(nstrips, std::vector<double>(ny, 1.0));
+    std::vector<std::vector<double>> p1(nstrips), pe(nstrips);
+    auto prefix = [&]() {
+        for (int sx = 0; sx < nstrips; ++sx) {
+            p1[sx].assign(ny + 1, 0.0);
+            pe[sx].assign(ny + 1, 0.0);
+            for (int y = 0; y < ny; ++y) {
+                p1[sx][y + 1] = p1[sx][y] + ratio[sx][y];
+                pe[sx][y + 1] = pe[sx][y] + extra[sx][y] * ratio[sx][y];
+            }
+        }
+    };
+    // the modelled cost of a segment with every row scaled by its ratio (the
+    // fixed sweep of 3 kWaveK - 3 rows and kBlockCost by the segment's mean)
+    auto cost = [&](int sx, int a, int b) {
+        const double rows = p1[sx][b] - p1[sx][a];
+        const double halo = pe[sx][std::min(ny, b + kK)] - pe[sx][std::max(0, a - kK)];
+        return rows + halo + (3 * kK - 3 + kBlockCost) * rows / (double)(b - a);
+    };
+    std::vector<long long> cyc;
+    auto measure = [&](const std::vector<int4> &plan) -> cudaError_t {
+        if (plan.empty() || plan.size() > wave_table_entries(nx, ny)) return cudaErrorInvalidValue;
+        m->nblocks = (int)plan.size();
+        cudaError_t e = cudaMemcpyAsync(S.wave_tab, plan.data(), plan.size() * sizeof(int4),
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_wave(L, S, *m, 0, 0, s, S.wave_cyc);
+        cyc.assign(plan.size(), 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cyc.data(), S.wave_cyc, plan.size() * sizeof(long long),
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e;
+    };
+    prefix();
+    std::vector<int4> plan = cut_strips(br, nstrips, ny, budget, cost);
+    std::vector<int4> best;
+    long long best_max = 0;
+    for (int round = 0; round < 3; ++round) {
+        cudaError_t e = measure(plan);
+        if (e != cudaSuccess) return e;
+        const long long mx = *std::max_element(cyc.begin(), cyc.end());
+        if (best.empty() || mx < best_max) {
+            best = plan;
+            best_max = mx;
+        }
+        if (round == 2) break;
+        // scale the rows of every block by its measured/modelled ratio
+        for (size_t b = 0; b < plan.size(); ++b) {
+            const int sx = plan[b].x / kW, a = plan[b].y, e2 = plan[b].y + plan[b].z;
+            const double modelled = cost(sx, a, e2);
+            if (!(modelled > 0.0) || cyc[b] <= 0) continue;
+            const double f = (double)cyc[b] / modelled;
+            for (int y = a; y < e2; ++y) ratio[sx][y] *= f;
+        }
+        prefix();
+        plan = cut_strips(br, nstrips, ny, budget, cost);
+    }
+    m->nblocks = (int)best.size();
+    // pageable source: the copy is staged before the call returns
+    return cudaMemcpyAsync(S.wave_tab, best.data(), best.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice, s);
 }
 
 size_t wave_smem_bytes() { return kSmem; }
@@ -1062,11 +1153,7 @@ cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, W
                : cudaFuncSetAttribute(k_wave, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kSmem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 148;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaGetLastError();
-    const std::vector<int4> plan = wave_plan(t, sms);
+    const std::vector<int4> plan = wave_plan(t, device_sms());
     m->nblocks = (int)plan.size();
     if (plan.empty() || plan.size() > wave_table_entries(t.nx, t.ny)) return cudaErrorInvalidValue;
     // pageable source: the copy is staged before the call returns
@@ -1075,15 +1162,15 @@ cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, W
 }
 
 cudaError_t launch_wave(const Lattice &L, const DevState &S, const WaveMaps &m, int cur, int toff,
-                        cudaStream_t s) {
+                        cudaStream_t s, long long *cycles) {
     if (L.grad)
         k_wave_grad<<<(unsigned)m.nblocks, kGradThreads, kGSmem, s>>>(
             m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]), S.ucomp, S.blinks, S.bcs, L,
-            S.time, toff, S.wave_tab, S.status);
+            S.time, toff, S.wave_tab, S.status, cycles);
     else
         k_wave<<<(unsigned)m.nblocks, kThreads, kSmem, s>>>(
             m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]), S.ucomp, S.blinks, S.bcs, L,
-            S.time, toff, S.wave_tab, S.status);
+            S.time, toff, S.wave_tab, S.status, cycles);
     return cudaGetLastError();
 }
 

@@ -115,24 +115,25 @@ def test_time_block_selection_and_validation():
     one = N.lbm_workspace_size(_desc(wl, time_block=1))
     blk = N.lbm_workspace_size(_desc(wl, time_block=N.LBM_TIME_BLOCK))
     dflt = N.lbm_workspace_size(_desc(wl))
-    # node words (8 bytes per node) and the block table (16 bytes per block;
-    # at most max(strips, 4096) + strips blocks of 112-column strips)
+    # node words (8 bytes per node) and the block table (16 bytes per block and
+    # 8 for its measured cycles; at most max(strips, 4096) + strips blocks of
+    # 112-column strips)
     strips = (256 + 111) // 112
-    table = (max(strips, 4096) + strips) * 16
+    table = (max(strips, 4096) + strips) * 24
     assert blk - one == (8 * plane + 255) // 256 * 256 + (table + 255) // 256 * 256
     # the default is blocked only where that is the faster form: at least 2^21
     # nodes, lambda = mu and at most one boundary node off box edges and crack
-    # faces per 1536 nodes
+    # faces per 800 nodes
     assert dflt == one
     crack = W.edge_crack(2048, 512, 0)
     assert N.lbm_workspace_size(_desc(crack)) == \
         N.lbm_workspace_size(_desc(crack, time_block=N.LBM_TIME_BLOCK))
-    # a hole of radius 256 in a 2048^2 plate: about one curved-wall node per
-    # 2040 nodes, blocked; radius 512 (one per 1022): one step per launch
-    hole = W.hole_plate(2048, 2048, 256.0, 0)
+    # a hole of radius 512 in a 2048^2 plate: about one curved-wall node per
+    # 1022 nodes, blocked; radius 900 (one per 582): one step per launch
+    hole = W.hole_plate(2048, 2048, 512.0, 0)
     assert N.lbm_workspace_size(_desc(hole)) == \
         N.lbm_workspace_size(_desc(hole, time_block=N.LBM_TIME_BLOCK))
-    big_hole = W.hole_plate(2048, 2048, 512.0, 0)
+    big_hole = W.hole_plate(2048, 2048, 900.0, 0)
     assert N.lbm_workspace_size(_desc(big_hole)) == \
         N.lbm_workspace_size(_desc(big_hole, time_block=1))
     # the default falls back to one step per launch where blocking is unsupported
