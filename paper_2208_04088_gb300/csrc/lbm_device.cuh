@@ -604,12 +604,24 @@ __device__ __forceinline__ float boundary8_collide(float fk, float g0, int kdir,
 }
 
 // Density deviation rho - rho0 of nine populations, summed as raw_moments
-// forms m00 (so it equals moments(f).dr bit for bit).
-__device__ __forceinline__ float density_of(const float f[9]) {
-    const float a0 = (f[7] + f[4]) + f[8];
-    const float b0 = (f[3] + f[0]) + f[1];
-    const float c0 = (f[6] + f[2]) + f[5];
-    return (a0 + b0) + c0;
+// forms m00 (so it equals moments(f).dr bit for bit); one node or two.
+template <class V> __device__ __forceinline__ V density_of(const V f[9]) {
+    const V a0 = radd(radd(f[7], f[4]), f[8]);
+    const V b0 = radd(radd(f[3], f[0]), f[1]);
+    const V c0 = radd(radd(f[6], f[2]), f[5]);
+    return radd(radd(a0, b0), c0);
+}
+
+// The source coefficient (mu - lambda)/rho = (mu - lambda) times an
+// approximate reciprocal of rho0 + drho (relative error about 1e-7; the same
+// value in every kernel).
+__device__ __forceinline__ float source_coef(float r0, const Lattice &L) {
+    return rmul(L.mu_m_lam, __fdividef(1.0f, radd(L.rho0, r0)));
+}
+__device__ __forceinline__ F2 source_coef(F2 r0, const Lattice &L) {
+    float a, b;
+    f2_split(radd(splat<F2>(L.rho0), r0), a, b);
+    return rmul(splat<F2>(L.mu_m_lam), f2(__fdividef(1.0f, a), __fdividef(1.0f, b)));
 }
 
 // Source S = F + (mu - lambda)/rho grad rho (Eq. sourceterm) from the density
@@ -627,9 +639,20 @@ __device__ __forceinline__ void grad_source(float r0, float rxp, float rxm, floa
     if (yp && ym) gy = rmul(0.5f, rsub(ryp, rym));
     else if (yp) gy = rsub(ryp, r0);
     else if (ym) gy = rsub(r0, rym);
-    const float c = __fdiv_rn(L.mu_m_lam, radd(L.rho0, r0));
+    const float c = source_coef(r0, L);
     sx = rfma(c, gx, L.fx);
     sy = rfma(c, gy, L.fy);
+}
+
+// The same for two nodes whose four axis neighbours are all material: the
+// operations of grad_source with every flag set, paired.
+__device__ __forceinline__ void grad_source_open(F2 r0, F2 rxp, F2 rxm, F2 ryp, F2 rym,
+                                                 const Lattice &L, F2 &sx, F2 &sy) {
+    const F2 half = splat<F2>(0.5f);
+    const F2 gx = rmul(half, rsub(rxp, rxm)), gy = rmul(half, rsub(ryp, rym));
+    const F2 c = source_coef(r0, L);
+    sx = rfma(c, gx, splat<F2>(L.fx));
+    sy = rfma(c, gy, splat<F2>(L.fy));
 }
 
 // Source at an interior node from a dense array of density deviations.

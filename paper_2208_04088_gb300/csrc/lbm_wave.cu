@@ -532,7 +532,7 @@ constexpr int kGradSkew = 4;              // rows between consecutive levels
 constexpr int kGradNI = 8, kGradD = 3;    // level-0 ring rows; rows issued ahead
 constexpr int kGradNL = 8, kGradND = 4;   // level ring rows; density ring rows
 constexpr int kGradNU = 19;               // node-word and displacement ring rows
-constexpr int kGradThreads = 2 * kGradK * kC;  // collision warps, then density warps
+constexpr int kGradThreads = 2 * kGradK * kC / 2;  // collision warps, then density warps
 constexpr size_t kGOffIn = 0;
 constexpr size_t kGOffLev = kGOffIn + (size_t)kGradNI * kFRowBytes;
 constexpr size_t kGOffDen = kGOffLev + (size_t)(kGradK - 1) * kGradNL * kFRowBytes;
@@ -547,18 +547,19 @@ static_assert(kGOffLev % 128 == 0 && kGOffDen % 128 == 0 && kGOffU % 128 == 0 &&
                   kGOffNw % 128 == 0,
               "TMA destinations 128-byte aligned");
 
-// The incoming populations of an interior node from three ring rows.
+// The incoming populations of an interior node from three ring rows, column
+// dc of rows rm, r0, rp.
 __device__ __forceinline__ void pull_rows(const float *rm, const float *r0, const float *rp,
-                                          int c, float f[9]) {
-    f[0] = r0[c];
-    f[1] = r0[kC + c - 1];
-    f[2] = rm[2 * kC + c];
-    f[3] = r0[3 * kC + c + 1];
-    f[4] = rp[4 * kC + c];
-    f[5] = rm[5 * kC + c - 1];
-    f[6] = rm[6 * kC + c + 1];
-    f[7] = rp[7 * kC + c + 1];
-    f[8] = rp[8 * kC + c - 1];
+                                          int dc, float f[9]) {
+    f[0] = r0[dc];
+    f[1] = r0[kC + dc - 1];
+    f[2] = rm[2 * kC + dc];
+    f[3] = r0[3 * kC + dc + 1];
+    f[4] = rp[4 * kC + dc];
+    f[5] = rm[5 * kC + dc - 1];
+    f[6] = rm[6 * kC + dc + 1];
+    f[7] = rp[7 * kC + dc + 1];
+    f[8] = rp[8 * kC + dc - 1];
 }
 
 // Axis directions 1..4 open (not cut) from a node word's cut mask.
@@ -571,16 +572,17 @@ __device__ __forceinline__ void open_axes(uint64_t nw, bool &xp, bool &yp, bool 
 }
 
 // One launch: kGradK steps of every material node, lambda != mu.  Blocks and
-// regions are those of k_wave.  Warps 0..15 run the collisions, warps 16..31
-// the densities; within each set warp 4 l' + s takes level l' + 1 and column
-// chunk (s - l') mod 4, as in k_wave.
+// regions are those of k_wave.  Warps 0..7 run the collisions, warps 8..15
+// the densities; within each set warp 2 l' + h' takes level l' + 1 and the
+// 64-column half h' xor (l' / 2) % 2, and lane t its columns c = 64 h + t and
+// c + 32, as in k_wave.  Each sub-partition holds two warps of each set.
 __global__ void __launch_bounds__(kGradThreads, 1)
     k_wave_grad(const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tnw,
                 const __grid_constant__ CUtensorMap tu, float *__restrict__ dst,
                 float4 *__restrict__ uc, const BLink *__restrict__ blinks,
                 const BCDev *__restrict__ bcs, Lattice L, const int64_t *__restrict__ time,
                 int toff, const int4 *__restrict__ tab, uint32_t *__restrict__ status,
-           long long *__restrict__ cycles) {
+                long long *__restrict__ cycles) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const long long t_start = clock64();
     float *in = reinterpret_cast<float *>(sm + kGOffIn);
@@ -590,12 +592,14 @@ __global__ void __launch_bounds__(kGradThreads, 1)
     const uint64_t *nwr = reinterpret_cast<const uint64_t *>(sm + kGOffNw);
     const uint32_t bar0 = smem_addr(sm + kGOffBar);
 
+    static_assert(kGradThreads == 2 * kGradK * 64, "two sets of warps, two columns per lane");
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const bool density_warp = (tid >> 5) >= 4 * kGradK;  // warp-uniform
-    const int w = (tid >> 5) & (4 * kGradK - 1);
-    const int lv = (w >> 2) + 1;  // time level of this thread (warp-uniform)
-    const int c = ((((w & 3) - (w >> 2)) & 3) << 5) | lane;
+    const bool density_warp = (tid >> 5) >= 2 * kGradK;  // warp-uniform
+    const int w = (tid >> 5) & (2 * kGradK - 1);
+    const int lv = (w >> 1) + 1;  // time level of this thread (warp-uniform)
+    const int half = (w ^ (w >> 2)) & 1;
+    const int c = (half << 6) | lane;  // the lane's columns c, c + 32
     const int4 region = tab[blockIdx.x];
     const int X0 = region.x, Y0 = region.y, Hs = region.z;
     const int xin = X0 - 2 * kGradK;    // lattice column of ring column 0
@@ -603,6 +607,7 @@ __global__ void __launch_bounds__(kGradThreads, 1)
     const int j_last = Hs + 4 * kGradK - 1;
     const int nsweep = Hs + 6 * kGradK - 3;
     const float tb = (float)(*time + toff + lv - 2);  // boundary data at the time of f^col
+    const F2 w2 = splat<F2>(L.omega), s32 = splat<F2>(rmul(L.src, 1.0f / 3.0f));
 
     auto issue = [&](int j) {
         const uint32_t bar = bar0 + 8u * (uint32_t)(j & (kGradNI - 1));
@@ -639,148 +644,257 @@ __global__ void __launch_bounds__(kGradThreads, 1)
     }
     __syncthreads();
 
-    const bool col_c = c >= 2 * lv && c < kC - 2 * lv;          // collision columns
-    const bool col_d = c >= 2 * lv - 1 && c < kC - 2 * lv + 1;  // density columns
+    // collision columns shrink by two per level, density columns by one less
+    const int m0 = density_warp ? 2 * lv - 1 : 2 * lv;
+    const bool live_a = c >= m0 && c < kC - m0, live_b = c + 32 >= m0 && c + 32 < kC - m0;
+    const bool core_a = c >= 2 * kGradK && c < kC - 2 * kGradK;
+    const bool core_b = c + 32 >= 2 * kGradK && c + 32 < kC - 2 * kGradK;
     const int lo = Y0 - 2 * (kGradK - lv), hi = Y0 + Hs - 1 + 2 * (kGradK - lv);
     const float *prev_base = lv == 1 ? in : lev + (size_t)(lv - 2) * kGradNL * kRowF;
     float *own_base = lev + (size_t)(lv - 1) * kGradNL * kRowF;  // unused by the last level
     float *den_base = den + (size_t)(lv - 1) * kGradND * kC;
     const int grp = lane >> 3, kdir = (lane & 7) + 1;
 
-    for (int n = 0; n < nsweep; ++n) {
-        if (tid == 0 && n + kGradD + 2 <= j_last && ok) {
-            // order the block's earlier shared-memory accesses before the copy
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(n + kGradD + 2);
-            j_issued = n + kGradD + 2;
+    // Populations of the lane's two nodes pulled from ring rows rm, r0, rp
+    // (offset to column c): paired loads when both are interior (or when the
+    // row holds no boundary node), else each node on its own, a simple
+    // boundary node by its rules (one copy of the code).
+    auto pull_pair = [&](auto with_boundary_row, const float *rm, const float *r0, const float *rp,
+                         uint32_t cla, uint32_t clb, bool sim_a, bool sim_b, uint64_t nwa,
+                         uint64_t nwb, F2 f[9]) {
+        constexpr bool kR = decltype(with_boundary_row)::value;
+        if (!kR || (cla == kInterior && clb == kInterior)) {
+            auto ld2 = [](const float *r) { return f2(r[0], r[32]); };
+            f[0] = ld2(r0);
+            f[1] = ld2(r0 + kC - 1);
+            f[2] = ld2(rm + 2 * kC);
+            f[3] = ld2(r0 + 3 * kC + 1);
+            f[4] = ld2(rp + 4 * kC);
+            f[5] = ld2(rm + 5 * kC - 1);
+            f[6] = ld2(rm + 6 * kC + 1);
+            f[7] = ld2(rp + 7 * kC + 1);
+            f[8] = ld2(rp + 8 * kC - 1);
+            return;
         }
-        const int y = y_in0 - 1 + n - kGradSkew * (lv - 1);
-        const int j = y - y_in0;
-        if (density_warp) {
-            // density deviation of row y + 2 at this level
-            if (y + 2 >= lo - 1 && y + 2 <= hi + 1) {
-                const int jd = j + 2;
-                const uint64_t nw = col_d ? nwr[(jd % kGradNU) * kC + c] : 0ull;
-                const uint32_t cl = (uint32_t)(nw & 3u);
-                const float *rm = prev_base + ((jd - 1) & (kGradNL - 1)) * kRowF;
-                const float *r0 = prev_base + (jd & (kGradNL - 1)) * kRowF;
-                const float *rp = prev_base + ((jd + 1) & (kGradNL - 1)) * kRowF;
-                float *drow = den_base + (jd & (kGradND - 1)) * kC;
-                const bool simple_b = cl == kBoundary && ((nw >> 34) & 1u);
-                if (cl == kInterior || simple_b) {
-                    float f[9];
-                    if (cl == kInterior) pull_rows(rm, r0, rp, c, f);
-                    else simple_pull(Rows{rm, r0, rp, c}, nw, bcs, tb, L, f);
-                    drow[c] = density_of(f);
-                }
-                unsigned rem = __ballot_sync(0xffffffffu, cl == kBoundary && !simple_b);
-                while (rem) {  // other boundary nodes: eight lanes each, four per pass
-                    unsigned r = rem;
-                    for (int q = 0; q < grp; ++q) r &= r - 1;
-                    const bool live = r != 0;
-                    const int src = __ffs(live ? r : rem) - 1;
-                    for (int q = 0; q < 4; ++q) rem &= rem - 1;
-                    const uint64_t wb = __shfl_sync(0xffffffffu, nw, src);
-                    const int cb = (c & ~31) + src;
-                    const BLink *lrec = blinks + (int64_t)(uint32_t)(wb >> 35) * 8;
-                    auto link = [&](int i) { return lrec[i - 1]; };
-                    float g0, f[9];
-                    const float fk = boundary8_pull(Rows{rm, r0, rp, cb}, nw_mask(wb, 2),
-                                                    nw_mask(wb, 10), nw_mask(wb, 18),
-                                                    nw_mask(wb, 26), kdir, link, bcs, tb, L, g0);
-                    gather8(fk, g0, f);
-                    if (live && kdir == 1) drow[cb] = density_of(f);
-                }
-            }
-        } else if (y >= lo && y <= hi) {
-            // collision of row y at this level
-            const int ju = j % kGradNU;
-            const uint64_t nw = col_c ? nwr[ju * kC + c] : 0ull;
-            const uint32_t cl = (uint32_t)(nw & 3u);
-            const float *rm = prev_base + ((j - 1) & (kGradNL - 1)) * kRowF;
-            const float *r0 = prev_base + (j & (kGradNL - 1)) * kRowF;
-            const float *rp = prev_base + ((j + 1) & (kGradNL - 1)) * kRowF;
-            const float *dm = den_base + ((j - 1) & (kGradND - 1)) * kC;
-            const float *d0 = den_base + (j & (kGradND - 1)) * kC;
-            const float *dp = den_base + ((j + 1) & (kGradND - 1)) * kC;
-            float *own = own_base + (j & (kGradNL - 1)) * kRowF;
-            const int64_t krow = (int64_t)y * L.pitch + xin;  // lattice index of ring column 0
-            const bool core_row = y >= Y0 && y < Y0 + Hs;
-            float4 *urow = ur + ju * kW;
-            auto store = [&](int col, int k, float v) {
-                if (lv < kGradK) own[k * kC + col] = v;
-                else dst[k * L.plane + krow + col] = v;
-            };
-            auto advance_u = [&](int col, float jx, float jy, float dr) {
-                if (!core_row || col < 2 * kGradK || col >= kC - 2 * kGradK) return;
-                float4 *up = urow + (col - 2 * kGradK);
-                float4 wu = *up;
-                integrate_u_value(wu, jx, jy, L.rho0 + dr);
-                if (lv < kGradK) {
-                    *up = wu;
-                } else {
-                    uc[krow + col] = wu;
-                    flag_nonfinite(status, dr, jx, jy);
-                }
-            };
-            const bool simple_b = cl == kBoundary && ((nw >> 34) & 1u);
-            if (cl == kInterior || simple_b) {
-                float f[9];
-                bool xp = true, yp = true, xm = true, ym = true;
-                if (cl == kInterior) {
-                    pull_rows(rm, r0, rp, c, f);
-                } else {
-                    simple_pull(Rows{rm, r0, rp, c}, nw, bcs, tb, L, f);
-                    open_axes(nw, xp, yp, xm, ym);
-                }
-                float sx, sy, dr, jx, jy;
-                grad_source(density_of(f), d0[c + 1], d0[c - 1], dp[c], dm[c], xp, xm, yp, ym, L,
-                            sx, sy);
-                collide(f, sx, sy, L, dr, jx, jy);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) store(c, i, f[i]);
-                advance_u(c, jx, jy, dr);
-            }
-            unsigned rem = __ballot_sync(0xffffffffu, cl == kBoundary && !simple_b);
-            while (rem) {  // other boundary nodes: eight lanes each, four per pass
-                unsigned r = rem;
-                for (int q = 0; q < grp; ++q) r &= r - 1;
-                const bool live = r != 0;
-                const int src = __ffs(live ? r : rem) - 1;
-                for (int q = 0; q < 4; ++q) rem &= rem - 1;
-                const uint64_t wb = __shfl_sync(0xffffffffu, nw, src);
-                const int cb = (c & ~31) + src;
-                const BLink *lrec = blinks + (int64_t)(uint32_t)(wb >> 35) * 8;
-                auto link = [&](int i) { return lrec[i - 1]; };
-                float g0, f[9];
-                const float fk = boundary8_pull(Rows{rm, r0, rp, cb}, nw_mask(wb, 2),
-                                                nw_mask(wb, 10), nw_mask(wb, 18),
-                                                nw_mask(wb, 26), kdir, link, bcs, tb, L, g0);
-                gather8(fk, g0, f);
-                bool xp, yp, xm, ym;
-                open_axes(wb, xp, yp, xm, ym);
-                float sx, sy, dr, jx, jy;
-                grad_source(density_of(f), d0[cb + 1], d0[cb - 1], dp[cb], dm[cb], xp, xm, yp, ym,
-                            L, sx, sy);
-                collide(f, sx, sy, L, dr, jx, jy);
-                float mine = f[1];
+        for (int i = 0; i < 9; ++i) f[i] = f2(0.0f, 0.0f);
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            float g[9];
+            const int dc = h << 5;
+            if (h ? sim_b : sim_a) simple_pull(Rows{rm - c, r0 - c, rp - c, c + dc}, h ? nwb : nwa, bcs, tb, L, g);
+            else pull_rows(rm, r0, rp, dc, g);
 #pragma unroll
-                for (int q = 2; q < 9; ++q)
-                    if (kdir == q) mine = f[q];
-                if (!live) continue;
-                store(cb, kdir, mine);
-                if (kdir == 1) {
-                    store(cb, 0, f[0]);
-                    advance_u(cb, jx, jy, dr);
-                }
+            for (int i = 0; i < 9; ++i) {
+                float va, vb;
+                f2_split(f[i], va, vb);
+                f[i] = h ? f2(va, g[i]) : f2(g[i], vb);
             }
         }
-        if (tid == 0 && n + 3 <= j_last && ok) {
-            ok = wait_row(n + 3);
-            if (!ok) last_waited = n + 2;
+    };
+    // The 8-lane passes over the row's other boundary nodes (node m of the 64
+    // is column m of the half): `use` gets the gathered populations of the
+    // group's node, its column and word, and whether the group holds a node.
+    auto passes = [&](const float *rm, const float *r0, const float *rp, bool cx_a, bool cx_b,
+                      uint64_t nwa, uint64_t nwb, auto use) {
+        const unsigned ma = __ballot_sync(0xffffffffu, cx_a);
+        const unsigned mb = __ballot_sync(0xffffffffu, cx_b);
+        unsigned long long rem = ((unsigned long long)mb << 32) | ma;
+        while (rem) {  // warp-uniform
+            unsigned long long r = rem;
+            for (int q = 0; q < grp; ++q) r &= r - 1;
+            const bool live = r != 0;
+            const int m = __ffsll((long long)(live ? r : rem)) - 1;
+            for (int q = 0; q < 4; ++q) rem &= rem - 1;
+            const int src = m & 31;
+            const uint64_t wa = __shfl_sync(0xffffffffu, nwa, src);
+            const uint64_t wbb = __shfl_sync(0xffffffffu, nwb, src);
+            const uint64_t wb = (m >> 5) ? wbb : wa;
+            const int cb = (half << 6) + m;
+            const BLink *lrec = blinks + (int64_t)(uint32_t)(wb >> 35) * 8;
+            auto link = [&](int i) { return lrec[i - 1]; };
+            float g0, f[9];
+            const float fk = boundary8_pull(Rows{rm - c, r0 - c, rp - c, cb}, nw_mask(wb, 2),
+                                            nw_mask(wb, 10), nw_mask(wb, 18), nw_mask(wb, 26),
+                                            kdir, link, bcs, tb, L, g0);
+            gather8(fk, g0, f);
+            use(f, cb, wb, live);
         }
-        __syncthreads();
-    }
+    };
+
+    auto sweep = [&](auto with_boundary) {
+        constexpr bool kB = decltype(with_boundary)::value;
+        for (int n = 0; n < nsweep; ++n) {
+            if (tid == 0 && n + kGradD + 2 <= j_last && ok) {
+                // order the block's earlier shared-memory accesses before the copy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(n + kGradD + 2);
+                j_issued = n + kGradD + 2;
+            }
+            const int y = y_in0 - 1 + n - kGradSkew * (lv - 1);
+            const int j = y - y_in0;
+            if (density_warp) {
+                // density deviations of row y + 2 at this level
+                if (y + 2 >= lo - 1 && y + 2 <= hi + 1) {
+                    const int jd = j + 2;
+                    const int ju = jd % kGradNU;
+                    const uint64_t nwa = live_a ? nwr[ju * kC + c] : 0ull;
+                    const uint64_t nwb = live_b ? nwr[ju * kC + c + 32] : 0ull;
+                    const uint32_t cla = (uint32_t)(nwa & 3u), clb = (uint32_t)(nwb & 3u);
+                    const float *rm = prev_base + ((jd - 1) & (kGradNL - 1)) * kRowF + c;
+                    const float *r0 = prev_base + (jd & (kGradNL - 1)) * kRowF + c;
+                    const float *rp = prev_base + ((jd + 1) & (kGradNL - 1)) * kRowF + c;
+                    float *drow = den_base + (jd & (kGradND - 1)) * kC;
+                    auto row = [&](auto with_boundary_row) {
+                        constexpr bool kR = decltype(with_boundary_row)::value;
+                        const bool sim_a = kR && cla == kBoundary && ((nwa >> 34) & 1u);
+                        const bool sim_b = kR && clb == kBoundary && ((nwb >> 34) & 1u);
+                        if (kR)
+                            passes(rm, r0, rp, cla == kBoundary && !sim_a, clb == kBoundary && !sim_b,
+                                   nwa, nwb, [&](const float *f, int cb, uint64_t, bool live) {
+                                       if (live && kdir == 1) drow[cb] = density_of(f);
+                                   });
+                        const bool do_a = cla == kInterior || sim_a, do_b = clb == kInterior || sim_b;
+                        if (do_a || do_b) {
+                            F2 f[9];
+                            pull_pair(with_boundary_row, rm, r0, rp, cla, clb, sim_a, sim_b, nwa,
+                                      nwb, f);
+                            float da, db;
+                            f2_split(density_of(f), da, db);
+                            if (do_a) drow[c] = da;
+                            if (do_b) drow[c + 32] = db;
+                        }
+                    };
+                    if (kB && __ballot_sync(0xffffffffu, cla == kBoundary || clb == kBoundary))
+                        row(std::true_type{});
+                    else
+                        row(std::false_type{});
+                }
+            } else if (y >= lo && y <= hi) {
+                // collision of row y at this level
+                const int ju = j % kGradNU;
+                const uint64_t nwa = live_a ? nwr[ju * kC + c] : 0ull;
+                const uint64_t nwb = live_b ? nwr[ju * kC + c + 32] : 0ull;
+                const uint32_t cla = (uint32_t)(nwa & 3u), clb = (uint32_t)(nwb & 3u);
+                const float *rm = prev_base + ((j - 1) & (kGradNL - 1)) * kRowF + c;
+                const float *r0 = prev_base + (j & (kGradNL - 1)) * kRowF + c;
+                const float *rp = prev_base + ((j + 1) & (kGradNL - 1)) * kRowF + c;
+                const float *dm = den_base + ((j - 1) & (kGradND - 1)) * kC;
+                const float *d0 = den_base + (j & (kGradND - 1)) * kC;
+                const float *dp = den_base + ((j + 1) & (kGradND - 1)) * kC;
+                float *own = own_base + (j & (kGradNL - 1)) * kRowF;
+                const int64_t krow = (int64_t)y * L.pitch + xin;  // lattice index of ring column 0
+                const bool core_row = y >= Y0 && y < Y0 + Hs;
+                float4 *urow = ur + ju * kW;
+                auto advance_u = [&](int col, float jx, float jy, float dr) {
+                    float4 *up = urow + (col - 2 * kGradK);
+                    float4 wu = *up;
+                    integrate_u_value(wu, jx, jy, L.rho0 + dr);
+                    if (lv < kGradK) {
+                        *up = wu;
+                    } else {
+                        uc[krow + col] = wu;
+                        flag_nonfinite(status, dr, jx, jy);
+                    }
+                };
+                // the scalar source of one node of the pair from its pulled populations
+                auto source_one = [&](const float *g, int col, uint64_t nw, bool open, float &sx,
+                                      float &sy) {
+                    bool xp = true, yp = true, xm = true, ym = true;
+                    if (!open) open_axes(nw, xp, yp, xm, ym);
+                    grad_source(density_of(g), d0[col + 1], d0[col - 1], dp[col], dm[col], xp, xm,
+                                yp, ym, L, sx, sy);
+                };
+                auto row = [&](auto with_boundary_row) {
+                    constexpr bool kR = decltype(with_boundary_row)::value;
+                    const bool sim_a = kR && cla == kBoundary && ((nwa >> 34) & 1u);
+                    const bool sim_b = kR && clb == kBoundary && ((nwb >> 34) & 1u);
+                    if (kR)
+                        passes(rm, r0, rp, cla == kBoundary && !sim_a, clb == kBoundary && !sim_b,
+                               nwa, nwb, [&](float *f, int cb, uint64_t wb, bool live) {
+                                   float sx, sy, dr, jx, jy;
+                                   source_one(f, cb, wb, false, sx, sy);
+                                   collide(f, sx, sy, L, dr, jx, jy);
+                                   float mine = f[1];
+#pragma unroll
+                                   for (int q = 2; q < 9; ++q)
+                                       if (kdir == q) mine = f[q];
+                                   if (!live) return;
+                                   if (lv < kGradK) own[kdir * kC + cb] = mine;
+                                   else dst[kdir * L.plane + krow + cb] = mine;
+                                   if (kdir == 1) {
+                                       if (lv < kGradK) own[cb] = f[0];
+                                       else dst[krow + cb] = f[0];
+                                       if (core_row && cb >= 2 * kGradK && cb < kC - 2 * kGradK)
+                                           advance_u(cb, jx, jy, dr);
+                                   }
+                               });
+                    const bool do_a = cla == kInterior || sim_a, do_b = clb == kInterior || sim_b;
+                    if (do_a || do_b) {
+                        F2 f[9];
+                        pull_pair(with_boundary_row, rm, r0, rp, cla, clb, sim_a, sim_b, nwa, nwb, f);
+                        F2 sx, sy;
+                        if (!kR || (cla == kInterior && clb == kInterior)) {
+                            const float *d0c = d0 + c, *dpc = dp + c, *dmc = dm + c;
+                            grad_source_open(density_of(f), f2(d0c[1], d0c[33]), f2(d0c[-1], d0c[31]),
+                                             f2(dpc[0], dpc[32]), f2(dmc[0], dmc[32]), L, sx, sy);
+                        } else {
+                            float sxa = 0.0f, sya = 0.0f, sxb = 0.0f, syb = 0.0f;
+#pragma unroll 1
+                            for (int h = 0; h < 2; ++h) {
+                                float g[9];
+#pragma unroll
+                                for (int i = 0; i < 9; ++i) {
+                                    float va, vb;
+                                    f2_split(f[i], va, vb);
+                                    g[i] = h ? vb : va;
+                                }
+                                float hx, hy;
+                                source_one(g, c + (h << 5), h ? nwb : nwa, (h ? clb : cla) == kInterior,
+                                           hx, hy);
+                                if (h) {
+                                    sxb = hx;
+                                    syb = hy;
+                                } else {
+                                    sxa = hx;
+                                    sya = hy;
+                                }
+                            }
+                            sx = f2(sxa, sxb);
+                            sy = f2(sya, syb);
+                        }
+                        F2 dr, jx, jy;
+                        collide_v(f, sx, sy, w2, s32, dr, jx, jy);
+                        if (lv < kGradK)
+                            store_pair(own + c, kC, f, do_a, do_b);
+                        else
+                            store_pair(dst + krow + c, L.plane, f, do_a, do_b);
+                        if (core_row) {
+                            float dra, drb, jxa, jxb, jya, jyb;
+                            f2_split(dr, dra, drb);
+                            f2_split(jx, jxa, jxb);
+                            f2_split(jy, jya, jyb);
+                            if (do_a && core_a) advance_u(c, jxa, jya, dra);
+                            if (do_b && core_b) advance_u(c + 32, jxb, jyb, drb);
+                        }
+                    }
+                };
+                if (kB && __ballot_sync(0xffffffffu, cla == kBoundary || clb == kBoundary))
+                    row(std::true_type{});
+                else
+                    row(std::false_type{});
+            }
+            if (tid == 0 && n + 3 <= j_last && ok) {
+                ok = wait_row(n + 3);
+                if (!ok) last_waited = n + 2;
+            }
+            __syncthreads();
+        }
+    };
+    if (region.w)
+        sweep(std::true_type{});
+    else
+        sweep(std::false_type{});
     if (cycles && tid == 0) cycles[blockIdx.x] = clock64() - t_start;
     if (tid == 0 && !ok) {
         // a copy did not land in time: flag it, and give the copies still in
