@@ -45,7 +45,9 @@ FLOPS_PER_UPDATE = 91
 FLOPS_PER_UPDATE_GRAD = 109
 # the kernel sources each kernel's recorded DRAM traffic depends on
 KERNEL_SOURCES = {"k_interior": ("lbm_kernels.cu", "lbm_device.cuh"),
-                  "k_wave": ("lbm_wave.cu", "lbm_device.cuh")}
+                  "k_interior_grad": ("lbm_kernels.cu", "lbm_device.cuh"),
+                  "k_wave": ("lbm_wave.cu", "lbm_device.cuh"),
+                  "k_wave_grad": ("lbm_wave.cu", "lbm_device.cuh")}
 WORKLOADS = ("crack", "plate", "batch", "serve")
 
 
@@ -511,13 +513,14 @@ def run_gpu(args):
         mean_launch_ms = tim["interior_ms"] / n_launch
         lu_per_launch = nodes * tblock
         fpu = FLOPS_PER_UPDATE if wl.lam_over_mu == 1.0 else FLOPS_PER_UPDATE_GRAD
+        kname = "k_wave" if wl.lam_over_mu == 1.0 else "k_wave_grad"
         achieved = lu_per_launch * fpu / (mean_launch_ms * 1e-3) / 1e12
         sm_mhz = clk.get("sm_mhz") or 2070.0
         alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak,
-                    "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage, "k_wave"),
-                    "kernel": "k_wave", "steps_per_launch": tblock,
+                    "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage, kname),
+                    "kernel": kname, "steps_per_launch": tblock,
                     "flops_per_update": fpu, "updates_per_launch": lu_per_launch,
                     "mean_launch_ms": mean_launch_ms,
                     "peak_kind": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured)",
@@ -535,10 +538,11 @@ def run_gpu(args):
         interior = info0["interior_nodes"]
         mean_interior_ms = tim["interior_ms"] / max(1, tim["steps"])
         achieved_gbs = interior * bpu / (mean_interior_ms * 1e-3) / 1e9
+        kname = "k_interior" if wl.lam_over_mu == 1.0 else "k_interior_grad"
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak,
                     "unit": "GB/s", "frac": achieved_gbs / peak,
-                    "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage, "k_interior"),
-                    "kernel": "k_interior",
+                    "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage, kname),
+                    "kernel": kname,
                     "bytes_per_update": bpu, "updates_per_launch": interior,
                     "mean_launch_ms": mean_interior_ms, "peak_kind": peak_kind,
                     "boundary_kernel_ms_per_step": tim["boundary_ms"] / max(1, tim["steps"]),
