@@ -46,6 +46,7 @@ FLOPS_PER_UPDATE_GRAD = 109
 # the kernel sources each kernel's recorded DRAM traffic depends on
 KERNEL_SOURCES = {"k_interior": ("lbm_kernels.cu", "lbm_device.cuh"),
                   "k_interior_grad": ("lbm_kernels.cu", "lbm_device.cuh"),
+                  "k_interior_aa": ("lbm_kernels.cu", "lbm_device.cuh"),
                   "k_wave": ("lbm_wave.cu", "lbm_device.cuh"),
                   "k_wave_grad": ("lbm_wave.cu", "lbm_device.cuh")}
 WORKLOADS = ("crack", "plate", "batch", "serve")
@@ -246,7 +247,7 @@ def run_profile(args):
     import torch
     torch.cuda.set_device(0)
     wl = _workload(args.workload, args.material)
-    s = N.Solver(N.desc_from_workload(wl, storage=args.storage,
+    s = N.Solver(N.desc_from_workload(wl, storage=args.storage, in_place=args.streaming == "in-place",
                                       wall_node=args.wall_values == "node",
                                       time_block=args.time_block))
     s.step(args.profile)  # as a solve does: replayed graphs, then direct launches
@@ -437,7 +438,7 @@ def run_gpu(args):
 
     wall_node = args.wall_values == "node"
     desc = N.desc_from_workload(wl, storage=args.storage, wall_node=wall_node,
-                                time_block=args.time_block)
+                                time_block=args.time_block, in_place=args.streaming == "in-place")
     nodes = int(desc.node_type.sum())
     solver = N.Solver(desc, stream=stream, device=dev)
     info0 = solver.info()
@@ -538,7 +539,8 @@ def run_gpu(args):
         interior = info0["interior_nodes"]
         mean_interior_ms = tim["interior_ms"] / max(1, tim["steps"])
         achieved_gbs = interior * bpu / (mean_interior_ms * 1e-3) / 1e9
-        kname = "k_interior" if wl.lam_over_mu == 1.0 else "k_interior_grad"
+        kname = ("k_interior_grad" if wl.lam_over_mu != 1.0 else
+                 "k_interior_aa" if args.streaming == "in-place" else "k_interior")
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak,
                     "unit": "GB/s", "frac": achieved_gbs / peak,
                     "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage, kname),
@@ -564,7 +566,8 @@ def run_gpu(args):
         def e2e_solve():
             nonlocal h2d
             d = N.desc_from_workload(wl, storage=args.storage, wall_node=wall_node,
-                                     time_block=args.time_block)
+                                     time_block=args.time_block,
+                                     in_place=args.streaming == "in-place")
             h = N.lbm_create(d, stream.cuda_stream, 0, 0)
             inf = N.lbm_get_info(h)
             h2d = (inf["pitch"] * wl.ny + 16 * inf["boundary_nodes"] +
@@ -596,6 +599,7 @@ def run_gpu(args):
     solver.close()
     if rank == 0:
         esz = 4 if args.storage == "f32" else 2
+        nbuf = 1 if args.streaming == "in-place" else 2  # population buffers
         line = {
             "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -605,11 +609,11 @@ def run_gpu(args):
             "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "time_steps": wl.steps,
                        "lambda_over_mu": wl.lam_over_mu,
                        "material_nodes": nodes, "storage": args.storage + " deviations",
-                       "wall_values": args.wall_values,
+                       "wall_values": args.wall_values, "streaming": args.streaming,
                        "parallelism": f"replicas x{world}",
                        "l2": ("inputs larger than L2 (working set "
-                              f"{(2 * 9 * esz + 16) * wl.nx * wl.ny / 1e6:.0f} MB)"
-                              if (2 * 9 * esz + 16) * wl.nx * wl.ny > 129e6 else
+                              f"{(nbuf * 9 * esz + 16) * wl.nx * wl.ny / 1e6:.0f} MB)"
+                              if (nbuf * 9 * esz + 16) * wl.nx * wl.ny > 129e6 else
                               "working set fits in L2; no flush inside a solve")},
             "roofline": roofline,
             "time_block": tblock,
@@ -657,6 +661,9 @@ def main():
     ap.add_argument("--time-block", type=int, default=0,
                     help="steps per launch: 0 library default, 1 one-step kernels, "
                          "8 temporally blocked kernel")
+    ap.add_argument("--streaming", choices=("two-buffers", "in-place"), default="two-buffers",
+                    help="population streaming: two buffers, or one buffer in place (AA pattern, "
+                         "one step per launch)")
     ap.add_argument("--profile", type=int, default=0,
                     help="run this many direct-launch steps of the workload and exit (for ncu)")
     ap.add_argument("--traffic", type=float, default=None,

@@ -69,6 +69,16 @@ typedef enum { LBM_F32 = 0, LBM_F16_DEV = 1, LBM_BF16_DEV = 2 } lbm_storage;
  * straight edges. */
 typedef enum { LBM_WALL_EXTRAPOLATE = 0, LBM_WALL_NODE = 1 } lbm_wall_values;
 
+/* How the populations are streamed (lbm_desc.streaming).  LBM_STREAM_TWO_BUFFERS
+ * pulls f_i(x, t) = f_i^col(x - c_i, t-1) (Eq. stream) from one buffer into
+ * the other.  LBM_STREAM_IN_PLACE keeps one buffer and updates it in place in
+ * the AA pattern: even steps read and write each node's own slots (reversed),
+ * odd steps the slots of its neighbours, so every node reads and writes the
+ * same nine locations.  It halves the population memory at the same bytes per
+ * lattice update; it needs lambda = mu and one step per launch (time_block 0
+ * or 1), and gives fields bit-identical to LBM_STREAM_TWO_BUFFERS. */
+typedef enum { LBM_STREAM_TWO_BUFFERS = 0, LBM_STREAM_IN_PLACE = 1 } lbm_streaming;
+
 /* Boundary-condition kinds (Sec. 2, Eqs. bcdir and bcneu). */
 typedef enum {
     LBM_BC_DIRICHLET = 0, /* value[0..1] = d(u*)/dt  (velocity of the wall)  */
@@ -151,6 +161,7 @@ typedef struct {
                                cross HBM once per launch; needs FP32 storage and
                                nx >= 128 (LBM_ERR_ARG otherwise).  Every stored
                                value is bit-identical to time_block = 1. */
+    int32_t streaming;   /* lbm_streaming (0: two buffers) */
 } lbm_desc;
 
 /* Steps per launch of the temporally blocked kernel (lbm_desc.time_block). */
@@ -168,7 +179,7 @@ typedef struct {
     int64_t kernel_launches; /* kernels this handle has launched so far */
     int32_t time_block;      /* steps per launch in use: 1, LBM_TIME_BLOCK, or 4
                                 (temporal blocking with lambda != mu) */
-    int32_t reserved;        /* 0 */
+    int32_t streaming;       /* lbm_streaming in use */
 } lbm_info;
 
 /* Accumulated kernel times of timing mode (see lbm_set_timing). */
@@ -308,6 +319,8 @@ typedef struct {
 
 /* Create a batch of `count` instances (host descriptors as for lbm_create,
  * every one with lambda = mu and the same storage), all at rest at t = 0.
+ * The batch steps every instance one step per launch with two population
+ * buffers: time_block and streaming of the descriptors are not used.
  * Device memory: one arena sized for all instances.  Synchronous. */
 lbm_status lbm_batch_create(const lbm_desc *descs, int32_t count, void *stream, lbm_batch *out);
 /* Advance every instance by nsteps (asynchronous). */

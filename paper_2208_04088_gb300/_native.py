@@ -18,6 +18,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_NOMEM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIME
 LBM_F32, LBM_F16_DEV, LBM_BF16_DEV = 0, 1, 2
 LBM_WALL_EXTRAPOLATE, LBM_WALL_NODE = 0, 1
 LBM_TIME_BLOCK = 8  # steps per launch of the temporally blocked kernel (include/lbm.h)
+LBM_STREAM_TWO_BUFFERS, LBM_STREAM_IN_PLACE = 0, 1  # lbm_streaming
 STORAGE = {"f32": LBM_F32, "f16": LBM_F16_DEV, "bf16": LBM_BF16_DEV}
 _STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_NOMEM", 3: "LBM_ERR_CUDA",
            4: "LBM_ERR_UNSTABLE", 5: "LBM_ERR_TIMEOUT"}
@@ -56,7 +57,8 @@ class lbm_desc(C.Structure):
                 ("tau", C.c_double), ("force", C.c_double * 2),
                 ("node_type", C.POINTER(C.c_uint8)), ("links", C.c_void_p),
                 ("nlinks", C.c_int64), ("bcs", C.POINTER(lbm_bc)), ("nbcs", C.c_int32),
-                ("storage", C.c_int32), ("wall_values", C.c_int32), ("time_block", C.c_int32)]
+                ("storage", C.c_int32), ("wall_values", C.c_int32), ("time_block", C.c_int32),
+                ("streaming", C.c_int32)]
 
 
 class lbm_info(C.Structure):
@@ -64,7 +66,7 @@ class lbm_info(C.Structure):
                 ("storage", C.c_int32), ("time", C.c_int64), ("boundary_nodes", C.c_int64),
                 ("interior_nodes", C.c_int64), ("workspace_bytes", C.c_uint64),
                 ("storage_scale", C.c_float), ("bytes_per_update", C.c_float),
-                ("kernel_launches", C.c_int64), ("time_block", C.c_int32), ("reserved", C.c_int32)]
+                ("kernel_launches", C.c_int64), ("time_block", C.c_int32), ("streaming", C.c_int32)]
 
 
 class lbm_launch_shape(C.Structure):
@@ -200,7 +202,7 @@ class Desc:
     """Owns the host arrays an lbm_desc points to."""
 
     def __init__(self, node_type, links, bcs, lam, mu, rho0=1.0, dx=1.0, dt=1.0, tau=0.55,
-                 force=(0.0, 0.0), storage="f32", wall_node=False, time_block=0):
+                 force=(0.0, 0.0), storage="f32", wall_node=False, time_block=0, in_place=False):
         self.node_type = np.ascontiguousarray(node_type, dtype=np.uint8)
         self.links = np.ascontiguousarray(links, dtype=LINK_DTYPE)
         self.bcs = make_bcs(bcs)
@@ -218,17 +220,18 @@ class Desc:
         d.wall_values = LBM_WALL_NODE if wall_node else LBM_WALL_EXTRAPOLATE
         # 0: library default, 1: one step per launch, LBM_TIME_BLOCK: temporal blocking
         d.time_block = int(time_block)
+        d.streaming = LBM_STREAM_IN_PLACE if in_place else LBM_STREAM_TWO_BUFFERS
         self.c = d
 
 
 def desc_from_workload(w, storage="f32", links_edit=None, wall_node=None,
-                       time_block=0) -> Desc:
+                       time_block=0, in_place=False) -> Desc:
     nt, links = lbm_geom_build(**w.geometry_args())
     if links_edit is not None:
         links = links_edit(links)
     wn = w.wall_node if wall_node is None else wall_node
     return Desc(nt, links, w.bcs, w.lam, w.mu, w.rho0, tau=w.tau, storage=storage, wall_node=wn,
-                time_block=time_block)
+                time_block=time_block, in_place=in_place)
 
 
 def lbm_workspace_size(desc: Desc) -> int:

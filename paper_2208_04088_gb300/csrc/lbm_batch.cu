@@ -490,11 +490,13 @@ lbm_status engine_init(lbm_engine *E, int storage, void *stream) {
     return LBM_OK;
 }
 
-// The batched kernels step every instance one step per launch, so instances
-// are created without the tables of the temporally blocked kernel.
+// The batched kernels step every instance one step per launch between two
+// buffers, so instances are created without the tables of the temporally
+// blocked kernel and with two population buffers.
 lbm_desc one_step(const lbm_desc &d) {
     lbm_desc o = d;
     o.time_block = 1;
+    o.streaming = LBM_STREAM_TWO_BUFFERS;
     return o;
 }
 

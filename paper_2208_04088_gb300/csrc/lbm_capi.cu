@@ -43,7 +43,8 @@ int64_t complex_boundary_nodes(const Tables &t) {
 }
 
 int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
-    const bool ok = d.storage == LBM_F32 && t.nx >= kWaveC && t.bnodes.size() < (size_t(1) << 28);
+    const bool ok = d.storage == LBM_F32 && t.nx >= kWaveC && t.bnodes.size() < (size_t(1) << 28) &&
+                    d.streaming != LBM_STREAM_IN_PLACE;
     const int k = u.lam == u.mu ? kWaveK : kWaveGradK;
     if (d.time_block == 1) return 1;
     if (d.time_block == LBM_TIME_BLOCK) return ok ? k : 0;
@@ -62,8 +63,9 @@ int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
     return ok && faster ? k : 1;
 }
 
-Layout layout(const Tables &t, int storage, bool grad, int block) {
+Layout layout(const Tables &t, int storage, bool grad, int block, bool in_place) {
     const size_t plane = (size_t)t.pitch * t.ny;
+    const size_t fplane = in_place ? (size_t)t.pitch * (t.ny + 2) : plane;
     const size_t esz = storage == LBM_F32 ? 4 : 2;
     const size_t N = (size_t)t.nx * t.ny;
     Layout l;
@@ -73,8 +75,8 @@ Layout layout(const Tables &t, int storage, bool grad, int block) {
         o += align256(bytes);
         return at;
     };
-    l.f0 = take(9 * plane * esz);
-    l.f1 = take(9 * plane * esz);
+    l.f0 = take(9 * fplane * esz);
+    l.f1 = in_place ? 0 : take(9 * fplane * esz);
     l.ucomp = take(plane * sizeof(float4));
     l.cls = take(plane);
     l.bnodes = take(std::max<size_t>(1, t.bnodes.size()) * sizeof(BNode));
@@ -83,7 +85,9 @@ Layout layout(const Tables &t, int storage, bool grad, int block) {
     l.rho = grad ? take(plane * sizeof(float)) : 0;
     l.status = take(sizeof(uint32_t));
     l.time = take(sizeof(int64_t));
-    l.stage = take(7 * N * sizeof(float));
+    // field staging; in place it also holds the boundary nodes' populations
+    // between their update and their store (9 per boundary node)
+    l.stage = take(std::max(7 * N, in_place ? 9 * t.bnodes.size() : 0) * sizeof(float));
     l.probe = take(7 * (size_t)kMaxProbe * sizeof(float));
     l.probe_idx = take((size_t)kMaxProbe * sizeof(int32_t));
     l.nw = block > 1 ? take(plane * sizeof(uint64_t)) : 0;
@@ -101,6 +105,7 @@ Lattice make_lattice(const Tables &t, const Units &u, int storage) {
     L.pitch = t.pitch;
     L.nb = (int32_t)t.bnodes.size();
     L.plane = (int64_t)t.pitch * t.ny;
+    L.fplane = L.plane;
     L.omega = (float)(1.0 / u.tau);
     L.src = (float)(1.0 - 1.0 / (2.0 * u.tau));
     L.fx = (float)u.fx;
@@ -194,10 +199,10 @@ extern "C" lbm_status lbm_workspace_size(const lbm_desc *desc, uint64_t *bytes) 
     if (st != LBM_OK) return st;
     const int block = steps_per_launch(*desc, t, u);
     if (block == 0) {
-        set_error("lbm_workspace_size: time_block = LBM_TIME_BLOCK needs FP32 storage and nx >= 128");
+        set_error("lbm_workspace_size: time_block = LBM_TIME_BLOCK needs FP32 storage, nx >= 128 and two buffers");
         return LBM_ERR_ARG;
     }
-    *bytes = layout(t, desc->storage, u.lam != u.mu, block).total;
+    *bytes = layout(t, desc->storage, u.lam != u.mu, block, desc->streaming == LBM_STREAM_IN_PLACE).total;
     return LBM_OK;
 }
 
@@ -221,11 +226,16 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
     h->L.wall_node = desc->wall_values == LBM_WALL_NODE ? 1 : 0;
     h->block = steps_per_launch(*desc, h->tab, h->units);
     if (h->block == 0) {
-        set_error("lbm_create: time_block = LBM_TIME_BLOCK needs FP32 storage and nx >= 128");
+        set_error("lbm_create: time_block = LBM_TIME_BLOCK needs FP32 storage, nx >= 128 and two buffers");
         delete h;
         return LBM_ERR_ARG;
     }
-    const Layout lay = layout(h->tab, h->storage, h->L.grad != 0, h->block);
+    const bool in_place = desc->streaming == LBM_STREAM_IN_PLACE;
+    if (in_place) {
+        h->L.in_place = 1;
+        h->L.fplane = (int64_t)h->tab.pitch * (h->tab.ny + 2);
+    }
+    const Layout lay = layout(h->tab, h->storage, h->L.grad != 0, h->block, in_place);
     h->bytes = lay.total;
     cudaError_t e = cudaSuccess;
     if (workspace) {
@@ -259,8 +269,10 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
     }
     char *b = static_cast<char *>(h->base);
     DevState &S = h->S;
-    S.f[0] = b + lay.f0;
-    S.f[1] = b + lay.f1;
+    const size_t esz = h->storage == LBM_F32 ? 4 : 2;
+    // in place: node (0, 0) sits one row and one column into the padded planes
+    S.f[0] = b + lay.f0 + (in_place ? (size_t)(h->tab.pitch + 1) * esz : 0);
+    S.f[1] = in_place ? nullptr : b + lay.f1;
     S.ucomp = reinterpret_cast<float4 *>(b + lay.ucomp);
     S.cls = reinterpret_cast<uint8_t *>(b + lay.cls);
     S.bnodes = reinterpret_cast<BNode *>(b + lay.bnodes);
@@ -564,7 +576,7 @@ extern "C" lbm_status lbm_get_info(lbm_handle h, lbm_info *info) {
     info->bytes_per_update = 2.0f * 9.0f * esz + 32.0f;  // f read + write, u and compensation R+W
     info->kernel_launches = h->launches;
     info->time_block = h->block;
-    info->reserved = 0;
+    info->streaming = h->L.in_place ? LBM_STREAM_IN_PLACE : LBM_STREAM_TWO_BUFFERS;
     return LBM_OK;
 }
 

@@ -283,6 +283,42 @@ __device__ __forceinline__ void pull_interior(const T *__restrict__ src, int64_t
 }
 
 
+// Where a step finds f_m^col(z, t-1) and puts f_m^col(x, t) (the stepping
+// form).  kPull: two buffers; plane m at the node, read from one and written
+// to the other.  kAAEven / kAAOdd: one buffer, updated in place in the AA
+// pattern.  An even step reads every incoming population of x from x itself
+// (f_m^col(z) sits at node z + c_m, plane m) and writes f_m^col(x) back into
+// x, plane opp(m); an odd step reads f_m^col(z) from node z, plane opp(m), and
+// writes f_m^col(x) to node x + c_m, plane m.  Each node then reads and writes
+// the same nine locations, which no other node touches.  Population planes
+// are L.fplane elements apart; with kAA the buffer has a ring of one node
+// around the lattice for the populations leaving across the box edges.
+enum : int { kPull = 0, kAAEven = 1, kAAOdd = 2 };
+
+template <int LAY>
+__device__ __forceinline__ int64_t col_at(int64_t kz, int m, const Lattice &L) {
+    if (LAY == kAAEven) return m * L.fplane + kz + (int64_t)c_cy(m) * L.pitch + c_cx(m);
+    if (LAY == kAAOdd) return opp(m) * L.fplane + kz;
+    return m * L.fplane + kz;
+}
+
+template <int LAY>
+__device__ __forceinline__ int64_t out_at(int64_t kx, int m, const Lattice &L) {
+    if (LAY == kAAEven) return opp(m) * L.fplane + kx;
+    if (LAY == kAAOdd) return m * L.fplane + kx + (int64_t)c_cy(m) * L.pitch + c_cx(m);
+    return m * L.fplane + kx;
+}
+
+// Interior pull in any stepping form: f_i(x, t) = f_i^col(x - c_i, t - 1).
+template <int LAY, class T>
+__device__ __forceinline__ void pull_interior_at(const T *src, int64_t k, const Lattice &L,
+                                                 float f[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        f[i] = Store<T>::ld(src + col_at<LAY>(k - (int64_t)c_cy(i) * L.pitch - c_cx(i), i, L),
+                            L.inv_scale);
+}
+
 // ---------------------------------------------------------------------------
 // Cooperative boundary update: eight lanes per boundary node.  Lane j owns the
 // population k = j + 1 and the link i = opp(k) through which it arrives.  Every
@@ -464,29 +500,28 @@ __device__ __forceinline__ float cut_link_value(int k, bool miss, bool dirich, b
 // abbcon at s = l/2) from f^col(., t-1), rho(., t-1), sigma(., t-1) and the
 // boundary data at t-1.  rho and P are collision invariants, so their values
 // at t-1 are the moments of the stored post-collision populations.
-template <class T>
-__device__ __forceinline__ void pull_boundary(const T *__restrict__ src, const BNode &b,
+template <class T, int LAY = kPull>
+__device__ __forceinline__ void pull_boundary(const T *src, const BNode &b,
                                               const BLink *__restrict__ links,
                                               const BCDev *__restrict__ bcs, float tb,
                                               const Lattice &L, float f[9]) {
     const int64_t k = (int64_t)b.y * L.pitch + b.x;
-    const int64_t P = L.plane;
     // Phase 1: every load that depends only on the node record, issued before
     // any arithmetic so their latencies overlap.  Cut directions read the
     // node itself (a valid address whose value is not used).
     float gx[9], pl[9], gy1[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) gx[i] = Store<T>::ld(src + i * P + k, L.inv_scale);
+    for (int i = 0; i < 9; ++i) gx[i] = Store<T>::ld(src + col_at<LAY>(k, i, L), L.inv_scale);
 #pragma unroll
     for (int kk = 1; kk < 9; ++kk) {
         const int i = opp(kk);
         const bool cut = (b.cut >> i) & 1u;
         const int64_t sk = cut ? k : k - (int64_t)c_cy(kk) * L.pitch - c_cx(kk);
-        pl[kk] = Store<T>::ld(src + kk * P + sk, L.inv_scale);
+        pl[kk] = Store<T>::ld(src + col_at<LAY>(sk, kk, L), L.inv_scale);
         // f_i^col at the upstream node x - c_i of the cut link i (kappa term)
         const bool up = cut && !((b.miss >> i) & 1u);
         const int64_t ku = up ? k - (int64_t)c_cy(i) * L.pitch - c_cx(i) : k;
-        gy1[i] = Store<T>::ld(src + i * P + ku, L.inv_scale);
+        gy1[i] = Store<T>::ld(src + col_at<LAY>(ku, i, L), L.inv_scale);
     }
     const Mom mx = moments(gx);
     f[0] = gx[0];
@@ -507,7 +542,7 @@ __device__ __forceinline__ void pull_boundary(const T *__restrict__ src, const B
             const int64_t ku = k - (int64_t)c_cy(i) * L.pitch - c_cx(i);
             float gy[9];
 #pragma unroll
-            for (int m = 0; m < 9; ++m) gy[m] = Store<T>::ld(src + m * P + ku, L.inv_scale);
+            for (int m = 0; m < 9; ++m) gy[m] = Store<T>::ld(src + col_at<LAY>(ku, m, L), L.inv_scale);
             const Mom my = moments(gy);
             my_dr = my.dr;
             my_xx = my.pxx;
@@ -565,17 +600,16 @@ __device__ __forceinline__ float boundary8_pull(const Ld &ld, uint32_t cutm, uin
 }
 
 // The same from the distributions in global memory.
-template <class T>
-__device__ __forceinline__ float pull_boundary8(const T *__restrict__ src, const BNode &b, int k,
+template <class T, int LAY = kPull>
+__device__ __forceinline__ float pull_boundary8(const T *src, const BNode &b, int k,
                                                 const BLink *__restrict__ links,
                                                 const BCDev *__restrict__ bcs, float tb,
                                                 const Lattice &L, float &f0) {
     const int64_t kn = (int64_t)b.y * L.pitch + b.x;
-    const int64_t P = L.plane;
     const int pitch = L.pitch;
     const float inv = L.inv_scale;
     auto ld = [&](int m, int dx, int dy) {
-        return Store<T>::ld(src + m * P + kn + (int64_t)dy * pitch + dx, inv);
+        return Store<T>::ld(src + col_at<LAY>(kn + (int64_t)dy * pitch + dx, m, L), inv);
     };
     auto link = [&](int i) { return links[i - 1]; };
     return boundary8_pull(ld, b.cut, b.dirich, b.corner, b.miss, k, link, bcs, tb, L, f0);
@@ -689,7 +723,7 @@ __device__ __forceinline__ float node_drho(const T *__restrict__ src,
                                            const Lattice &L) {
     if (__ldg(cls + k) != kInterior) return rho[k];
     float f[9];
-    pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
+    pull_interior(src, k, L.pitch, L.fplane, L.inv_scale, f);
     return moments(f).dr;
 }
 
@@ -733,22 +767,23 @@ __device__ __forceinline__ void source_boundary8(const T *__restrict__ src,
 // One interior node: pull (Eq. stream), moments with the source, collision
 // (Eq. coll), store, displacement.  Every load -- the nine pulled
 // populations and the displacement record -- is issued before any arithmetic.
-template <class T>
-__device__ __forceinline__ void interior_node(const T *__restrict__ src, T *__restrict__ dst,
-                                              float4 *__restrict__ uc,
+// With kAA src and dst are the same buffer: the node reads all nine of its
+// locations before it writes any.
+template <class T, int LAY = kPull>
+__device__ __forceinline__ void interior_node(const T *src, T *dst, float4 *__restrict__ uc,
                                               const uint8_t *__restrict__ cls,
                                               const float *__restrict__ rho, const Lattice &L,
                                               int64_t k, uint32_t *__restrict__ status) {
     if (__ldg(cls + k) != kInterior) return;
     float f[9];
-    pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
+    pull_interior_at<LAY>(src, k, L, f);
     float4 w = uc[k];
     float sx = L.fx, sy = L.fy;
     if (L.grad) source_interior(rho, k, L.pitch, rho[k], L, sx, sy);
     float dr, jx, jy;
     collide(f, sx, sy, L, dr, jx, jy);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.plane + k, f[i], L.scale);
+    for (int i = 0; i < 9; ++i) Store<T>::st(dst + out_at<LAY>(k, i, L), f[i], L.scale);
     integrate_u_value(w, jx, jy, L.rho0 + dr);
     uc[k] = w;
     flag_nonfinite(status, dr, jx, jy);
@@ -759,30 +794,39 @@ constexpr int kB8 = 128;  // threads per block of the cooperative boundary kerne
 // One boundary node g (a valid index of the compacted list) handled by the
 // 8-lane group that lane j belongs to.  A group with live == false computes and
 // stores nothing visible, so every lane can take part in the shuffles.
-template <class T>
-__device__ __forceinline__ void boundary8_node(const T *__restrict__ src, T *__restrict__ dst,
-                                               float4 *__restrict__ uc,
+// With a non-null `stage` the node's nine post-collision populations go to
+// stage[9 g + m] (FP32) instead of the buffer: the in-place form stores them
+// only after every boundary node has read its inputs.
+template <class T, int LAY = kPull>
+__device__ __forceinline__ void boundary8_node(const T *src, T *dst, float4 *__restrict__ uc,
                                                const BNode *__restrict__ bnodes,
                                                const BLink *__restrict__ blinks,
                                                const BCDev *__restrict__ bcs,
                                                const uint8_t *__restrict__ cls,
                                                const float *__restrict__ rho, const Lattice &L,
                                                int g, bool live, int j, float tb,
-                                               uint32_t *__restrict__ status) {
+                                               uint32_t *__restrict__ status,
+                                               float *__restrict__ stage = nullptr) {
     const bool lane0 = j == 0;
     const BNode b = bnodes[g];
     const int kdir = j + 1;
     float f0;
-    const float fk = pull_boundary8(src, b, kdir, blinks + (int64_t)g * 8, bcs, tb, L, f0);
+    const float fk =
+        pull_boundary8<T, LAY>(src, b, kdir, blinks + (int64_t)g * 8, bcs, tb, L, f0);
     const int64_t kn = (int64_t)b.y * L.pitch + b.x;
     float sx = L.fx, sy = L.fy;
     if (L.grad) source_boundary8(src, cls, rho, b, kn, L, j, sx, sy);
     float fr, jx, jy, m00;
     const float mine = boundary8_collide(fk, f0, kdir, sx, sy, L, fr, jx, jy, m00);
     if (!live) return;
-    Store<T>::st(dst + kdir * L.plane + kn, mine, L.scale);
+    if (stage) {
+        stage[(int64_t)g * 9 + kdir] = mine;
+        if (lane0) stage[(int64_t)g * 9] = fr;
+    } else {
+        Store<T>::st(dst + out_at<LAY>(kn, kdir, L), mine, L.scale);
+        if (lane0) Store<T>::st(dst + out_at<LAY>(kn, 0, L), fr, L.scale);
+    }
     if (lane0) {
-        Store<T>::st(dst + kn, fr, L.scale);
         integrate_u(uc + kn, jx, jy, L.rho0 + m00);
         flag_nonfinite(status, m00, jx, jy);
     }

@@ -298,6 +298,16 @@ lbm_status classify(const lbm_desc &d, const Units &u, Tables *t) {
         set_error("lbm_create: unknown wall_values, or time_block not 0, 1 or LBM_TIME_BLOCK");
         return LBM_ERR_ARG;
     }
+    if (d.streaming != LBM_STREAM_TWO_BUFFERS && d.streaming != LBM_STREAM_IN_PLACE) {
+        set_error("lbm_create: unknown streaming");
+        return LBM_ERR_ARG;
+    }
+    if (d.streaming == LBM_STREAM_IN_PLACE && u.lam != u.mu) {
+        // the source's density gradient would read neighbours' populations
+        // that the in-place step overwrites
+        set_error("lbm_create: in-place streaming needs lambda = mu");
+        return LBM_ERR_ARG;
+    }
     const int64_t N = (int64_t)nx * ny;
     // boundary conditions
     t->bcs.resize(d.nbcs);
@@ -342,7 +352,8 @@ lbm_status classify(const lbm_desc &d, const Units &u, Tables *t) {
 
     t->nx = nx;
     t->ny = ny;
-    t->pitch = (nx + 63) / 64 * 64;
+    // in-place streaming keeps a ring of one node around the population planes
+    t->pitch = (nx + (d.streaming == LBM_STREAM_IN_PLACE ? 2 : 0) + 63) / 64 * 64;
     t->cls.assign((size_t)t->pitch * ny, kVoid);
     t->bnodes.clear();
     t->blinks.clear();

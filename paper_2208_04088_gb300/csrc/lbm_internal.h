@@ -66,6 +66,10 @@ struct Lattice {
     float out_u, out_v, out_s;  // lattice -> physical units for the fields
     int32_t grad;               // lambda != mu: the source needs grad rho
     int32_t wall_node;          // Neumann wall values at the boundary node (no extrapolation)
+    int64_t fplane;             // elements per population plane: plane, or with
+                                // in-place streaming pitch * (ny + 2) (a ring of one node)
+    int32_t in_place;           // one population buffer, AA pattern (lbm_desc.streaming)
+    int32_t pad;
 };
 
 // Host-side result of validating and classifying an lbm_desc.
@@ -99,7 +103,9 @@ lbm_status classify(const lbm_desc &d, const Units &u, Tables *t);
 // f^col(t).  d_time holds the number of completed steps; a launch with offset
 // `toff` computes f at time t = *d_time + toff.
 struct DevState {
-    void *f[2] = {nullptr, nullptr};  // two distribution buffers (9 planes each)
+    void *f[2] = {nullptr, nullptr};  // two distribution buffers (9 planes each); with
+                                      // in-place streaming f[0] only, at node (0, 0) of
+                                      // its padded planes
     float4 *ucomp = nullptr;          // (u_x, u_y, kahan_x, kahan_y) per node
     uint8_t *cls = nullptr;
     BNode *bnodes = nullptr;

@@ -8,7 +8,9 @@
 // Distributions are stored as deviations from the zero-stress rest state,
 // delta f = f - f^eq(rho0, 0, 0), in structure-of-arrays planes
 // [9][ny][pitch].  The buffer holds f^col(t-1); a step pulls f_i(x, t) =
-// f_i^col(x - c_i, t-1) (Eq. stream), collides (Eq. coll) and writes f^col(x, t).
+// f_i^col(x - c_i, t-1) (Eq. stream), collides (Eq. coll) and writes f^col(x, t)
+// to the other buffer, or, with in-place streaming, to the same buffer in the
+// AA pattern (see col_at / out_at).
 // All arithmetic is FP32.  The rest state is a fixed point of every rule, so
 // each rule acts on the deviations with the same coefficients it has for f.
 #include <cstdint>
@@ -31,8 +33,8 @@ constexpr int kBB = 64;  // threads per block of the boundary-list kernels
 // Every load of a node -- the nine pulled populations and the displacement
 // record -- is issued before any arithmetic, so all of them are in flight
 // together.
-template <class T, int NR>
-__global__ void __launch_bounds__(kBX *kBY, 8) k_interior(const T *__restrict__ src, T *__restrict__ dst,
+template <class T, int NR, int LAY = kPull>
+__global__ void __launch_bounds__(kBX *kBY, 8) k_interior(const T *src, T *dst,
                                                        float4 *__restrict__ uc,
                                                        const uint8_t *__restrict__ cls,
                                                        const float *__restrict__ rho, Lattice L,
@@ -43,7 +45,8 @@ __global__ void __launch_bounds__(kBX *kBY, 8) k_interior(const T *__restrict__ 
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int y = y0 + r * kBY;
-        if (y < L.ny) interior_node(src, dst, uc, cls, rho, L, (int64_t)y * L.pitch + x, status);
+        if (y < L.ny)
+            interior_node<T, LAY>(src, dst, uc, cls, rho, L, (int64_t)y * L.pitch + x, status);
     }
 }
 
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict_
         const uint8_t c = __ldg(cls + k);
         if (c == kInterior) {
             live = true;
-            pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
+            pull_interior(src, k, L.pitch, L.fplane, L.inv_scale, f);
             w = uc[k];
             own = moments(f).dr;
         } else if (c == kBoundary) {
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict_
             const uint8_t c = __ldg(cls + kk);
             if (c == kInterior) {
                 float g[9];
-                pull_interior(src, kk, L.pitch, L.plane, L.inv_scale, g);
+                pull_interior(src, kk, L.pitch, L.fplane, L.inv_scale, g);
                 v = moments(g).dr;
             } else if (c == kBoundary) {
                 v = rho[kk];
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict_
     float dr, jx, jy;
     collide(f, sx, sy, L, dr, jx, jy);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.plane + k, f[i], L.scale);
+    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.fplane + k, f[i], L.scale);
     integrate_u_value(w, jx, jy, L.rho0 + dr);
     uc[k] = w;
     flag_nonfinite(status, dr, jx, jy);
@@ -153,28 +156,52 @@ __global__ void __launch_bounds__(kBB) k_boundary(const T *__restrict__ src, T *
     float dr, jx, jy;
     collide(f, sx, sy, L, dr, jx, jy);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.plane + k, f[i], L.scale);
+    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.fplane + k, f[i], L.scale);
     integrate_u(uc + k, jx, jy, L.rho0 + dr);
     flag_nonfinite(status, dr, jx, jy);
 }
 
 
-template <class T>
-__global__ void __launch_bounds__(kB8) k_boundary8(const T *__restrict__ src, T *__restrict__ dst,
-                                                   float4 *__restrict__ uc,
+template <class T, int LAY = kPull>
+__global__ void __launch_bounds__(kB8) k_boundary8(const T *src, T *dst, float4 *__restrict__ uc,
                                                    const BNode *__restrict__ bnodes,
                                                    const BLink *__restrict__ blinks,
                                                    const BCDev *__restrict__ bcs,
                                                    const uint8_t *__restrict__ cls,
                                                    const float *__restrict__ rho, Lattice L,
                                                    const int64_t *__restrict__ time, int toff,
-                                                   uint32_t *__restrict__ status) {
+                                                   uint32_t *__restrict__ status,
+                                                   float *__restrict__ stage) {
     const int g = (blockIdx.x * kB8 + threadIdx.x) >> 3;  // boundary node of this lane group
     const float tb = (float)(*time + toff - 1);           // boundary data at the time of f^col
     // groups past the end of the list work on node 0 and store nothing
     const bool live = g < L.nb;
-    boundary8_node(src, dst, uc, bnodes, blinks, bcs, cls, rho, L, live ? g : 0, live,
-                   threadIdx.x & 7, tb, status);
+    boundary8_node<T, LAY>(src, dst, uc, bnodes, blinks, bcs, cls, rho, L, live ? g : 0, live,
+                           threadIdx.x & 7, tb, status, stage);
+}
+
+// In-place streaming: the post-collision populations of the boundary nodes,
+// staged by k_boundary8, into the buffer (one thread per node and direction).
+template <class T, int LAY>
+__global__ void __launch_bounds__(kBB) k_boundary_scatter(const float *__restrict__ stage,
+                                                          T *dst,
+                                                          const BNode *__restrict__ bnodes,
+                                                          Lattice L) {
+    const int64_t e = (int64_t)blockIdx.x * kBB + threadIdx.x;
+    if (e >= (int64_t)L.nb * 9) return;
+    const int g = (int)(e / 9), m = (int)(e % 9);
+    const BNode b = bnodes[g];
+    const int64_t kn = (int64_t)b.y * L.pitch + b.x;
+    int64_t o = 0;
+    switch (m) {  // out_at for a run-time direction
+#define LBM_OUT(mm) \
+    case mm:        \
+        o = out_at<LAY>(kn, mm, L); \
+        break;
+        LBM_OUT(0) LBM_OUT(1) LBM_OUT(2) LBM_OUT(3) LBM_OUT(4) LBM_OUT(5) LBM_OUT(6) LBM_OUT(7) LBM_OUT(8)
+#undef LBM_OUT
+    }
+    Store<T>::st(dst + o, stage[e], L.scale);
 }
 
 // Density at time t of every material node (lambda != mu): pull, with the
@@ -190,7 +217,7 @@ __global__ void __launch_bounds__(kBX *kBY) k_density_interior(const T *__restri
     const int64_t k = (int64_t)y * L.pitch + x;
     if (cls[k] != kInterior) return;
     float f[9];
-    pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
+    pull_interior(src, k, L.pitch, L.fplane, L.inv_scale, f);
     rho[k] = moments(f).dr;
 }
 
@@ -228,7 +255,7 @@ __device__ __forceinline__ void write_fields(float *__restrict__ out, int64_t N,
     out[6 * N + o] = (-m.pxy) * L.out_s;
 }
 
-template <class T>
+template <class T, int LAY = kPull>
 __global__ void __launch_bounds__(kBX *kBY) k_fields_interior(const T *__restrict__ src,
                                                               const float4 *__restrict__ uc,
                                                               const uint8_t *__restrict__ cls,
@@ -247,13 +274,13 @@ __global__ void __launch_bounds__(kBX *kBY) k_fields_interior(const T *__restric
         return;
     }
     float f[9];
-    pull_interior(src, k, L.pitch, L.plane, L.inv_scale, f);
+    pull_interior_at<LAY>(src, k, L, f);
     float sx = L.fx, sy = L.fy;
     if (L.grad) source_interior(rho, k, L.pitch, rho[k], L, sx, sy);
     write_fields(out, N, o, f, sx, sy, uc[k], L);
 }
 
-template <class T>
+template <class T, int LAY = kPull>
 __global__ void __launch_bounds__(kBB) k_fields_boundary(const T *__restrict__ src,
                                                          const float4 *__restrict__ uc,
                                                          const BNode *__restrict__ bnodes,
@@ -267,7 +294,7 @@ __global__ void __launch_bounds__(kBB) k_fields_boundary(const T *__restrict__ s
     const BNode b = bnodes[m];
     const float tb = (float)(*time - 1);
     float f[9];
-    pull_boundary(src, b, blinks + (int64_t)m * 8, bcs, tb, L, f);
+    pull_boundary<T, LAY>(src, b, blinks + (int64_t)m * 8, bcs, tb, L, f);
     const int64_t k = (int64_t)b.y * L.pitch + b.x;
     float sx = L.fx, sy = L.fy;
     if (L.grad) source_boundary(rho, b, k, rho[k], L, sx, sy);
@@ -305,9 +332,9 @@ static int high_priority() {
     return p;
 }
 
-template <class T>
+template <class T, int LAY = kPull>
 static cudaError_t launch_boundary(const T *src, T *dst, const DevState &S, const Lattice &L,
-                                   int toff, cudaStream_t s) {
+                                   int toff, cudaStream_t s, float *stage = nullptr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((L.nb + kB8 / 8 - 1) / (kB8 / 8));
     cfg.blockDim = dim3(kB8);
@@ -318,10 +345,10 @@ static cudaError_t launch_boundary(const T *src, T *dst, const DevState &S, cons
     attr[0].val.priority = high_priority();
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_boundary8<T>, src, dst, S.ucomp,
+    return cudaLaunchKernelEx(&cfg, k_boundary8<T, LAY>, src, dst, S.ucomp,
                               (const BNode *)S.bnodes, (const BLink *)S.blinks,
                               (const BCDev *)S.bcs, (const uint8_t *)S.cls, (const float *)S.rho, L,
-                              (const int64_t *)S.time, toff, S.status);
+                              (const int64_t *)S.time, toff, S.status, stage);
 }
 
 template <class T>
@@ -339,10 +366,48 @@ static void launch_interior(const T *src, T *dst, const DevState &S, const Latti
     k_interior<T, NR><<<grd, blk, 0, s>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status);
 }
 
+// In-place step of parity LAY: every boundary node reads its inputs and
+// stages its result before any population is overwritten (a boundary rule
+// reads the node's own and upstream post-collision populations, which their
+// pulling neighbours overwrite in place); then the interior kernel, and beside
+// it the scatter of the staged boundary populations (the two touch disjoint
+// locations).
+template <class T, int LAY>
+static cudaError_t step_in_place(const Lattice &L, const DevState &S, int toff,
+                                 cudaStream_t s_main, cudaStream_t s_side, cudaEvent_t fork,
+                                 cudaEvent_t join, const StepEvents *ev) {
+    T *f = static_cast<T *>(S.f[0]);
+    const bool split = s_side && fork && join && L.nb > 0;
+    if (L.nb > 0) {
+        if (ev) cudaEventRecord(ev->before_boundary, s_main);
+        launch_boundary<T, LAY>(f, f, S, L, toff, s_main, S.stage);
+        if (ev) cudaEventRecord(ev->after_boundary, s_main);
+    }
+    const int nsc = (int)(((int64_t)L.nb * 9 + kBB - 1) / kBB);
+    if (split) {
+        cudaEventRecord(fork, s_main);
+        cudaStreamWaitEvent(s_side, fork, 0);
+        k_boundary_scatter<T, LAY><<<nsc, kBB, 0, s_side>>>(S.stage, f, S.bnodes, L);
+        cudaEventRecord(join, s_side);
+    }
+    if (ev) cudaEventRecord(ev->before_interior, s_main);
+    const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
+    k_interior<T, 1, LAY><<<grd, blk, 0, s_main>>>(f, f, S.ucomp, S.cls, S.rho, L, S.status);
+    if (ev) cudaEventRecord(ev->after_interior, s_main);
+    if (split)
+        cudaStreamWaitEvent(s_main, join, 0);
+    else if (L.nb > 0)
+        k_boundary_scatter<T, LAY><<<nsc, kBB, 0, s_main>>>(S.stage, f, S.bnodes, L);
+    return cudaGetLastError();
+}
+
 template <class T>
 static cudaError_t step_t(const Lattice &L, const DevState &S, int cur, int toff,
                           cudaStream_t s_main, cudaStream_t s_side, cudaEvent_t fork,
                           cudaEvent_t join, const StepEvents *ev) {
+    if (L.in_place)  // the parity of the step is that of `cur`
+        return cur ? step_in_place<T, kAAOdd>(L, S, toff, s_main, s_side, fork, join, ev)
+                   : step_in_place<T, kAAEven>(L, S, toff, s_main, s_side, fork, join, ev);
     const T *src = static_cast<const T *>(S.f[cur]);
     T *dst = static_cast<T *>(S.f[cur ^ 1]);
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
@@ -388,7 +453,9 @@ cudaError_t launch_step(int storage, const Lattice &L, const DevState &S, int cu
     }
 }
 
-int kernels_per_step(const Lattice &L) { return (L.grad && L.nb > 0 ? 1 : 0) + 1 + (L.nb > 0 ? 1 : 0); }
+int kernels_per_step(const Lattice &L) {
+    return (L.grad && L.nb > 0 ? 1 : 0) + 1 + (L.nb > 0 ? (L.in_place ? 2 : 1) : 0);
+}
 int kernels_per_fields(const Lattice &L) { return (L.grad ? (L.nb > 0 ? 2 : 1) : 0) + 1 + (L.nb > 0 ? 1 : 0); }
 
 cudaError_t launch_advance(const DevState &S, int64_t n, cudaStream_t s) {
@@ -396,8 +463,25 @@ cudaError_t launch_advance(const DevState &S, int64_t n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <class T, int LAY>
+static void fields_in_place(const Lattice &L, const DevState &S, cudaStream_t s) {
+    const T *src = static_cast<const T *>(S.f[0]);
+    const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
+    k_fields_interior<T, LAY><<<grd, blk, 0, s>>>(src, S.ucomp, S.cls, S.rho, L, S.stage);
+    if (L.nb > 0)
+        k_fields_boundary<T, LAY><<<(L.nb + kBB - 1) / kBB, kBB, 0, s>>>(
+            src, S.ucomp, S.bnodes, S.blinks, S.bcs, S.rho, L, S.time, S.stage);
+}
+
 template <class T>
 static cudaError_t fields_t(const Lattice &L, const DevState &S, int cur, cudaStream_t s) {
+    if (L.in_place) {  // lambda = mu only: no density pass
+        if (cur)
+            fields_in_place<T, kAAOdd>(L, S, s);
+        else
+            fields_in_place<T, kAAEven>(L, S, s);
+        return cudaGetLastError();
+    }
     const T *src = static_cast<const T *>(S.f[cur]);
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
     const int nbb = (L.nb + kBB - 1) / kBB;
@@ -445,9 +529,11 @@ cudaError_t launch_gather_probe(const Lattice &L, const DevState &S, int count, 
 
 cudaError_t launch_reset(int storage, const Lattice &L, const DevState &S, cudaStream_t s) {
     const size_t esz = storage == LBM_F32 ? 4 : 2;
-    const size_t fbytes = (size_t)9 * L.plane * esz;
-    cudaError_t e = cudaMemsetAsync(S.f[0], 0, fbytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S.f[1], 0, fbytes, s);
+    const size_t fbytes = (size_t)9 * L.fplane * esz;
+    // in place: the planes start one row and one column before node (0, 0)
+    char *f0 = static_cast<char *>(S.f[0]) - (L.in_place ? (size_t)(L.pitch + 1) * esz : 0);
+    cudaError_t e = cudaMemsetAsync(f0, 0, fbytes, s);
+    if (e == cudaSuccess && S.f[1]) e = cudaMemsetAsync(S.f[1], 0, fbytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.ucomp, 0, (size_t)L.plane * sizeof(float4), s);
     if (e == cudaSuccess && S.rho) e = cudaMemsetAsync(S.rho, 0, (size_t)L.plane * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.status, 0, sizeof(uint32_t), s);

@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                         own[kdir * kC + cb - c] = mine;
                                         if (lane0) own[cb - c] = fr;
                                     } else {
-                                        dst[kdir * L.plane + gb] = mine;
+                                        dst[kdir * L.fplane + gb] = mine;
                                         if (lane0) dst[gb] = fr;
                                     }
                                     if (lane0 && core_row && cb >= kK && cb < kC - kK) {
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (lv < kK)
                             store_pair(own, kC, f, do_a, do_b);
                         else
-                            store_pair(dst + grow, L.plane, f, do_a, do_b);
+                            store_pair(dst + grow, L.fplane, f, do_a, do_b);
                         if (core_row) {
                             float dra, drb, jxa, jxb, jya, jyb;
                             f2_split(dr, dra, drb);
@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(kGradThreads, 1)
                                        if (kdir == q) mine = f[q];
                                    if (!live) return;
                                    if (lv < kGradK) own[kdir * kC + cb] = mine;
-                                   else dst[kdir * L.plane + krow + cb] = mine;
+                                   else dst[kdir * L.fplane + krow + cb] = mine;
                                    if (kdir == 1) {
                                        if (lv < kGradK) own[cb] = f[0];
                                        else dst[krow + cb] = f[0];
@@ -868,7 +868,7 @@ __global__ void __launch_bounds__(kGradThreads, 1)
                         if (lv < kGradK)
                             store_pair(own + c, kC, f, do_a, do_b);
                         else
-                            store_pair(dst + krow + c, L.plane, f, do_a, do_b);
+                            store_pair(dst + krow + c, L.fplane, f, do_a, do_b);
                         if (core_row) {
                             float dra, drb, jxa, jxb, jya, jyb;
                             f2_split(dr, dra, drb);
@@ -1247,7 +1247,7 @@ cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, W
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const cuuint64_t fdims[3] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, 9};
-    const cuuint64_t fstr[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
+    const cuuint64_t fstr[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.fplane * 4};
     const cuuint32_t fbox[3] = {(cuuint32_t)kC, 1, 9};
     for (int b = 0; b < 2; ++b)
         if (!encode(&m->f[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S.f[b], fdims, fstr, fbox))

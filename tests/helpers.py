@@ -16,13 +16,14 @@ def run_oracle(oracle_mod, wl, steps, links_edit=None, bcs=None):
     return {"u": F["u"], "v": F["v"], "sigma": F["sigma"], "mask": nt.astype(bool)}
 
 
-def run_gpu(wl, steps, storage="f32", links_edit=None, bcs=None, chunks=None, time_block=0):
+def run_gpu(wl, steps, storage="f32", links_edit=None, bcs=None, chunks=None, time_block=0,
+            in_place=False):
     from paper_2208_04088_gb300 import _native as N
     nt, links = N.lbm_geom_build(**wl.geometry_args())
     if links_edit is not None:
         links = links_edit(links)
     d = N.Desc(nt, links, wl.bcs if bcs is None else bcs, wl.lam, wl.mu, wl.rho0, tau=wl.tau,
-               storage=storage, wall_node=wl.wall_node, time_block=time_block)
+               storage=storage, wall_node=wl.wall_node, time_block=time_block, in_place=in_place)
     s = N.Solver(d)
     if chunks is None:
         s.step(steps)

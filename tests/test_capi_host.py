@@ -155,3 +155,63 @@ def test_time_block_selection_and_validation():
     with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
         N.lbm_workspace_size(_desc(narrow, time_block=N.LBM_TIME_BLOCK))
     assert N.lbm_workspace_size(_desc(narrow)) == N.lbm_workspace_size(_desc(narrow, time_block=1))
+
+
+def test_in_place_streaming_selection_and_validation():
+    """lbm_desc.streaming = LBM_STREAM_IN_PLACE: one population buffer (9
+    planes padded by a ring of one node) instead of two, one step per launch,
+    lambda = mu only."""
+    wl = W.hole_plate(256, 128, 16.0, 0)
+    two = N.lbm_workspace_size(_desc(wl, time_block=1))
+    one = N.lbm_workspace_size(N.desc_from_workload(wl, in_place=True))
+    # one buffer fewer; the ring widens the pitch of every per-node array here
+    # (256 -> 320 columns), so less than a whole buffer is saved at this size
+    buf_two = 9 * 4 * 256 * 128
+    assert two - one >= buf_two // 2
+    # temporal blocking keeps two buffers
+    with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
+        N.lbm_workspace_size(N.desc_from_workload(wl, time_block=N.LBM_TIME_BLOCK, in_place=True))
+    # the default form with in-place streaming is one step per launch (no node words)
+    crack = W.edge_crack(2048, 512, 0)
+    assert N.lbm_workspace_size(N.desc_from_workload(crack, in_place=True)) < \
+        N.lbm_workspace_size(N.desc_from_workload(crack, time_block=1))
+    # lambda != mu: the source's density gradient would read overwritten populations
+    nonpoisson = W.hole_plate(256, 128, 16.0, 0, lam_over_mu=0.8)
+    with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
+        N.lbm_workspace_size(N.desc_from_workload(nonpoisson, in_place=True))
+    bad = N.desc_from_workload(wl)
+    bad.c.streaming = 7
+    with pytest.raises(N.LbmError, match="LBM_ERR_ARG"):
+        N.lbm_workspace_size(bad)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets of the
+    C structures in include/lbm.h (compiled here with the host C compiler)."""
+    import shutil
+    import subprocess
+    import ctypes as C
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"lbm_desc": N.lbm_desc, "lbm_info": N.lbm_info, "lbm_bc": N.lbm_bc,
+               "lbm_geom": N.lbm_geom, "lbm_launch_shape": N.lbm_launch_shape,
+               "lbm_batch_stats": N.lbm_batch_stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbm.h"', "int main(void) {"]
+    c_names = {"lam": "lambda"}  # Python keyword avoided in the binding
+    for sname, cls in structs.items():
+        lines.append(f'printf("{sname} %zu\\n", sizeof({sname}));')
+        for fname, _ in cls._fields_:
+            cname = c_names.get(fname, fname)
+            lines.append(f'printf("{sname}.{fname} %zu\\n", offsetof({sname}, {cname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.split("\n") if l)
+    for sname, cls in structs.items():
+        assert int(out[sname]) == C.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert int(out[f"{sname}.{fname}"]) == getattr(cls, fname).offset, (sname, fname)
