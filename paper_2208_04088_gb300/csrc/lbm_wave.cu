@@ -674,21 +674,23 @@ __global__ void __launch_bounds__(kGradThreads, 1)
             f[6] = ld2(rm + 6 * kC + 1);
             f[7] = ld2(rp + 7 * kC + 1);
             f[8] = ld2(rp + 8 * kC - 1);
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = f2(0.0f, 0.0f);
+            for (int i = 0; i < 9; ++i) f[i] = f2(0.0f, 0.0f);
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            float g[9];
-            const int dc = h << 5;
-            if (h ? sim_b : sim_a) simple_pull(Rows{rm - c, r0 - c, rp - c, c + dc}, h ? nwb : nwa, bcs, tb, L, g);
-            else pull_rows(rm, r0, rp, dc, g);
+            for (int h = 0; h < 2; ++h) {
+                float g[9];
+                const int dc = h << 5;
+                if (h ? sim_b : sim_a)
+                    simple_pull(Rows{rm - c, r0 - c, rp - c, c + dc}, h ? nwb : nwa, bcs, tb, L, g);
+                else
+                    pull_rows(rm, r0, rp, dc, g);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                float va, vb;
-                f2_split(f[i], va, vb);
-                f[i] = h ? f2(va, g[i]) : f2(g[i], vb);
+                for (int i = 0; i < 9; ++i) {
+                    float va, vb;
+                    f2_split(f[i], va, vb);
+                    f[i] = h ? f2(va, g[i]) : f2(g[i], vb);
+                }
             }
         }
     };
