@@ -278,7 +278,8 @@ def run_batch(args):
     wls = W.batched_instances(args.batch_count, seed=4, steps=args.batch_steps)
     stream = torch.cuda.Stream(device=dev)
     wall_node = args.wall_values == "node"
-    descs = [N.desc_from_workload(w, storage=args.storage, wall_node=wall_node) for w in wls]
+    descs = [N.desc_from_workload(w, storage=args.storage, wall_node=wall_node,
+                                  in_place=args.streaming == "in-place") for w in wls]
     b = N.Batch(descs, stream=stream)
     shape = b.tune(steps_per_trial=20)
     nodes = b.info()["nodes"]
@@ -382,7 +383,8 @@ def run_serve(args):
             now = time.perf_counter() - t0
             while pending and pending[0][0] <= now:
                 at, w = pending.pop(0)
-                d = N.desc_from_workload(w, storage=args.storage, wall_node=wall_node)
+                d = N.desc_from_workload(w, storage=args.storage, wall_node=wall_node,
+                                         in_place=args.streaming == "in-place")
                 live[srv.submit(d, w.steps)] = (at, w.nodes * w.steps)
             if not live:
                 time.sleep(min(0.01, max(0.0, pending[0][0] - now)))

@@ -319,8 +319,9 @@ typedef struct {
 
 /* Create a batch of `count` instances (host descriptors as for lbm_create,
  * every one with lambda = mu and the same storage), all at rest at t = 0.
- * The batch steps every instance one step per launch with two population
- * buffers: time_block and streaming of the descriptors are not used.
+ * The batch steps every instance one step per launch (time_block of the
+ * descriptors is not used); each instance keeps the streaming form its
+ * descriptor asks for, and in-place instances take less of the arena.
  * Device memory: one arena sized for all instances.  Synchronous. */
 lbm_status lbm_batch_create(const lbm_desc *descs, int32_t count, void *stream, lbm_batch *out);
 /* Advance every instance by nsteps (asynchronous). */

@@ -28,7 +28,8 @@ namespace lbm {
 // Device descriptor of one instance.
 struct InstDev {
     Lattice L;
-    void *f[2];
+    void *f[2];      // two buffers, or f[0] alone with in-place streaming (L.in_place)
+    float *stage;    // in place: the boundary nodes' staged populations
     float4 *uc;
     const uint8_t *cls;
     const BNode *bn;
@@ -95,8 +96,18 @@ __global__ void __launch_bounds__(TX *TY, 2048 / (TX * TY)) k_batch_interior(con
             const int x = tx * TX + threadIdx.x, y = ty * TY + threadIdx.y;
             if (x < I.L.nx && y < I.L.ny) {
                 const int cur = (int)(time & 1);
-                interior_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]),
-                                 I.uc, I.cls, nullptr, I.L, (int64_t)y * I.L.pitch + x, I.status);
+                const int64_t k = (int64_t)y * I.L.pitch + x;
+                if (I.L.in_place) {  // one buffer: the AA step of the instance's parity
+                    T *f = static_cast<T *>(I.f[0]);
+                    if (cur)
+                        interior_node<T, kAAOdd>(f, f, I.uc, I.cls, nullptr, I.L, k, I.status);
+                    else
+                        interior_node<T, kAAEven>(f, f, I.uc, I.cls, nullptr, I.L, k, I.status);
+                } else {
+                    interior_node<T>(static_cast<const T *>(I.f[cur]),
+                                     static_cast<T *>(I.f[cur ^ 1]), I.uc, I.cls, nullptr, I.L, k,
+                                     I.status);
+                }
             }
         }
         if (schedule == 2) break;
@@ -121,9 +132,52 @@ __global__ void __launch_bounds__(kB8) k_batch_boundary(const InstDev *__restric
         const int64_t time = *I.time;
         const bool live = in_list && time < I.target;
         const int cur = (int)(time & 1);
-        boundary8_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]), I.uc,
-                          I.bn, I.bl, I.bcs, I.cls, nullptr, I.L, m.y, live, j,
-                          (float)(time - 1), I.status);
+        if (I.L.in_place) {
+            // stage: the instance's populations are stored by k_batch_scatter
+            // once every boundary node has read its inputs
+            T *f = static_cast<T *>(I.f[0]);
+            if (cur)
+                boundary8_node<T, kAAOdd>(f, f, I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, I.L, m.y,
+                                          live, j, (float)(time - 1), I.status, I.stage);
+            else
+                boundary8_node<T, kAAEven>(f, f, I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, I.L, m.y,
+                                           live, j, (float)(time - 1), I.status, I.stage);
+        } else {
+            boundary8_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]),
+                              I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, I.L, m.y, live, j,
+                              (float)(time - 1), I.status);
+        }
+    }
+}
+
+// In-place instances: the staged boundary populations into the buffer (one
+// thread per boundary node and direction), beside the interior kernel.
+template <class T>
+__global__ void __launch_bounds__(256) k_batch_scatter(const InstDev *__restrict__ insts,
+                                                       const int2 *__restrict__ bmap,
+                                                       const BatchCounts *__restrict__ counts) {
+    const int64_t n = (int64_t)counts->nbnodes * 9;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)gridDim.x * 256) {
+        const int2 m = bmap[e / 9];
+        const int d = (int)(e % 9);
+        const InstDev &I = insts[m.x];
+        if (!I.L.in_place) continue;
+        const int64_t time = *I.time;
+        if (time >= I.target) continue;
+        const BNode b = I.bn[m.y];
+        const int64_t kn = (int64_t)b.y * I.L.pitch + b.x;
+        int64_t o = 0;
+        const bool odd = time & 1;
+        switch (d) {  // out_at for a run-time direction and parity
+#define LBM_OUT(mm) \
+    case mm:        \
+        o = odd ? out_at<kAAOdd>(kn, mm, I.L) : out_at<kAAEven>(kn, mm, I.L); \
+        break;
+            LBM_OUT(0) LBM_OUT(1) LBM_OUT(2) LBM_OUT(3) LBM_OUT(4) LBM_OUT(5) LBM_OUT(6) LBM_OUT(7)
+            LBM_OUT(8)
+#undef LBM_OUT
+        }
+        Store<T>::st(static_cast<T *>(I.f[0]) + o, I.stage[(int64_t)m.y * 9 + d], I.L.scale);
     }
 }
 
@@ -261,6 +315,8 @@ struct lbm_engine {
     lbm_launch_shape shape{32, 8, 8, 0};
     int sms = 0;
     cudaGraphExec_t graph = nullptr;
+    bool graph_in_place = false;  // the captured graph orders the boundary kernel first
+    int n_in_place = 0;           // instances with in-place streaming
     int64_t launches = 0;
     int64_t step_count = 0;  // steps run by the engine
     ~lbm_engine();
@@ -314,6 +370,7 @@ lbm_status rebuild_tables(lbm_engine *E) {
         d.L = h->L;
         d.f[0] = h->S.f[0];
         d.f[1] = h->S.f[1];
+        d.stage = h->S.stage;
         d.uc = h->S.ucomp;
         d.cls = h->S.cls;
         d.bn = h->S.bnodes;
@@ -329,6 +386,13 @@ lbm_status rebuild_tables(lbm_engine *E) {
     }
     lbm_status st = ensure_capacity(E, (int)hi.size(), (int64_t)tiles.size(), (int64_t)bmap.size());
     if (st != LBM_OK) return st;
+    E->n_in_place = 0;
+    for (const InstDev &d : hi) E->n_in_place += d.L.in_place ? 1 : 0;
+    if (E->graph && E->graph_in_place != (E->n_in_place > 0)) {
+        // the order of the step's kernels changes
+        cudaGraphExecDestroy(E->graph);
+        E->graph = nullptr;
+    }
     if (E->shape.dynamic == 2 && (int64_t)tiles.size() != E->ntiles && E->graph) {
         // one block per tile: the captured grid must match the table
         cudaGraphExecDestroy(E->graph);
@@ -380,13 +444,20 @@ cudaError_t launch_interior_shape(lbm_engine *E, cudaStream_t s) {
 
 template <class T>
 cudaError_t launch_batch_step_t(lbm_engine *E, cudaStream_t s_main, cudaStream_t s_side) {
-    // boundary nodes beside the interior tiles, at the highest priority
-    cudaEventRecord(E->fork, s_main);
-    cudaStreamWaitEvent(s_side, E->fork, 0);
+    // boundary nodes beside the interior tiles, at the highest priority; with
+    // in-place instances the boundary kernel goes first (it stages their
+    // boundary populations before their neighbours are overwritten) and the
+    // scatter of the staged populations runs beside the interior tiles
+    const bool in_place = E->n_in_place > 0;
+    cudaStream_t s_b = in_place ? s_main : s_side;
+    if (!in_place) {
+        cudaEventRecord(E->fork, s_main);
+        cudaStreamWaitEvent(s_side, E->fork, 0);
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * E->sms);
     cfg.blockDim = dim3(kB8);
-    cfg.stream = s_side;
+    cfg.stream = s_b;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributePriority;
     attr[0].val.priority = high_priority_value();
@@ -396,6 +467,12 @@ cudaError_t launch_batch_step_t(lbm_engine *E, cudaStream_t s_main, cudaStream_t
                                        (const int2 *)E->d_bmap,
                                        (const BatchCounts *)E->d_counts);
     if (e != cudaSuccess) return e;
+    if (in_place) {
+        cudaEventRecord(E->fork, s_main);
+        cudaStreamWaitEvent(s_side, E->fork, 0);
+        k_batch_scatter<T><<<2 * E->sms, 256, 0, s_side>>>(
+            (const InstDev *)E->d_inst, (const int2 *)E->d_bmap, (const BatchCounts *)E->d_counts);
+    }
     cudaEventRecord(E->join, s_side);
     const int TX = E->shape.tile_x, TY = E->shape.tile_y;
     if (TX == 32 && TY == 8)
@@ -438,6 +515,7 @@ lbm_status build_batch_graph(lbm_engine *E) {
     e = cudaGraphInstantiate(&E->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail_cuda(e, "batch: instantiate");
+    E->graph_in_place = E->n_in_place > 0;
     return LBM_OK;
 }
 
@@ -464,7 +542,7 @@ lbm_status engine_steps(lbm_engine *E, int64_t nsteps) {
         e = launch_batch_step(E, E->stream, E->cap_side);
         if (e != cudaSuccess) return fail_cuda(e, "batch: launch");
     }
-    E->launches += 3 * nsteps;
+    E->launches += (E->n_in_place > 0 ? 4 : 3) * nsteps;
     E->step_count += nsteps;
     for (auto &I : E->inst) {
         I.done = E->server ? std::min(I.steps, I.done + nsteps) : I.done + nsteps;
@@ -490,13 +568,12 @@ lbm_status engine_init(lbm_engine *E, int storage, void *stream) {
     return LBM_OK;
 }
 
-// The batched kernels step every instance one step per launch between two
-// buffers, so instances are created without the tables of the temporally
-// blocked kernel and with two population buffers.
+// The batched kernels step every instance one step per launch, so instances
+// are created without the tables of the temporally blocked kernel; each keeps
+// the streaming form its descriptor asks for.
 lbm_desc one_step(const lbm_desc &d) {
     lbm_desc o = d;
     o.time_block = 1;
-    o.streaming = LBM_STREAM_TWO_BUFFERS;
     return o;
 }
 

@@ -108,3 +108,57 @@ def test_server_rejects_requests_it_cannot_run():
     with pytest.raises(N.LbmError):
         srv.result(rid)
     srv.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_batch_in_place_instances_match_alone(storage):
+    """Instances with in-place streaming, alone or mixed with two-buffer ones,
+    give the fields of the two-buffer solver run alone."""
+    from paper_2208_04088_gb300 import _native as N
+    wls = _mix()
+    ref = [_alone(w, 75, storage) for w in wls]
+    for mixed in (False, True):
+        descs = [N.desc_from_workload(w, storage=storage, in_place=not mixed or k % 2 == 0)
+                 for k, w in enumerate(wls)]
+        b = N.Batch(descs)
+        b.step(75)
+        b.sync()
+        for k, w in enumerate(wls):
+            assert _same(b.fields_host(k), ref[k]), (mixed, w.name)
+        for shape in [(32, 4, 16, 0), (64, 4, 8, 1)]:
+            b.reset()
+            b.set_shape(*shape)
+            b.step(75)
+            for k in range(len(wls)):
+                assert _same(b.fields_host(k), ref[k]), (mixed, shape, wls[k].name)
+        b.close()
+
+
+def test_server_in_place_requests_join_at_any_parity():
+    """In-place requests joining a running server at odd and even times of the
+    others (each instance keeps its own clock and parity) end with the fields
+    they have alone; they also need less of the budget."""
+    from paper_2208_04088_gb300 import _native as N
+    reqs = [(W.hole_plate(256, 128, 16.0, 0), 90, True), (W.edge_crack(128, 32, 0), 37, False),
+            (W.square_plate(64, 0), 151, True), (W.hole_plate(77, 45, 9.5, 0), 21, True),
+            (W.edge_crack(96, 24, 0, ny=64), 64, False), (W.square_plate(48, 0), 5, True)]
+    w0 = reqs[0][0]
+    assert N.lbm_workspace_size(N.desc_from_workload(w0, in_place=True)) < \
+        N.lbm_workspace_size(N.desc_from_workload(w0))
+    srv = N.Server(N.lbm_workspace_size(N.desc_from_workload(w0)) * 3)
+    ids, results, pending, ticks = [], {}, list(reqs), 0
+    while len(results) < len(reqs):
+        if pending and ticks % 2 == 0:
+            w, n, ip = pending.pop(0)
+            ids.append((srv.submit(N.desc_from_workload(w, in_place=ip), n), w, n))
+        srv.tick(max_steps=7)  # odd ticks: requests join at odd and even times of the others
+        for rid, w, n in ids:
+            if rid not in results:
+                r = srv.result(rid)
+                if r is not None:
+                    results[rid] = (r, w, n)
+        ticks += 1
+        assert ticks < 500
+    for rid, (r, w, n) in results.items():
+        assert _same(r, _alone(w, n)), (w.name, n)
+    srv.close()
