@@ -68,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
     for src in cpp:
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
         objs.append(obj)
-        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall",
+        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-ffp-contract=off", "-Wall",
                      "-I", INC, "-I", CSRC, "-I", os.path.join(home, "include"), "-c", src,
                      "-o", obj])
 
@@ -85,7 +85,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
             if verbose and log:
                 print(log, file=sys.stderr)
     tmp = LIB + f".tmp{os.getpid()}"
-    run([nvcc, ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"])
+    run([nvcc, ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC", "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -358,134 +359,176 @@ lbm_status classify(const lbm_desc &d, const Units &u, Tables *t) {
     t->bnodes.clear();
     t->blinks.clear();
     t->interior = 0;
-    size_t p = 0;
-    // full[x] of row y: the node and its eight neighbours are all material.
-    // Formed as the AND of three horizontal 3-ANDs (rows y - 1, y, y + 1;
-    // outside the box counts as void), so most nodes are classified interior
-    // without the per-link checks below.
-    std::vector<uint8_t> h0((size_t)nx, 0), h1((size_t)nx, 0), h2((size_t)nx, 0),
-        full((size_t)nx, 0);
-    auto hrow = [&](int32_t yy, std::vector<uint8_t> &h) {
-        if (yy < 0 || yy >= ny) {
-            std::fill(h.begin(), h.end(), (uint8_t)0);
-            return;
-        }
-        const uint8_t *__restrict__ r = d.node_type + (int64_t)yy * nx;
-        uint8_t *__restrict__ o = h.data();
-        o[0] = 0;
-        o[nx - 1] = 0;
-        for (int32_t x = 1; x < nx - 1; ++x)
-            o[x] = (uint8_t)((r[x - 1] != 0) & (r[x] != 0) & (r[x + 1] != 0));
+    // Rows are classified in contiguous chunks on host threads; each chunk
+    // keeps its own boundary lists, merged in row order, so the tables are
+    // those of a single pass.  Errors are reported for the first offending
+    // node in row-major order (the error text is set by the calling thread).
+    struct Part {
+        std::vector<BNode> bn;
+        std::vector<BLink> bl;
+        int64_t interior = 0;
+        std::string err;
     };
-    hrow(-1, h0);
-    hrow(0, h1);
-    for (int32_t y = 0; y < ny; ++y) {
-        hrow(y + 1, h2);
-        {
-            const uint8_t *__restrict__ a = h0.data(), *__restrict__ b = h1.data(),
-                                       *__restrict__ c = h2.data();
-            uint8_t *__restrict__ o = full.data();
-            for (int32_t x = 0; x < nx; ++x) o[x] = (uint8_t)(a[x] & b[x] & c[x]);
-        }
-        std::swap(h0, h1);
-        std::swap(h1, h2);
-        const int64_t row0 = (int64_t)y * nx;
-        uint8_t *crow = t->cls.data() + (size_t)y * t->pitch;
-        static_assert(kInterior == 1, "a full node's class is its flag");
-        for (int32_t x = 0; x < nx; ++x) {
-            // the run of nodes up to the next one with cut links: its full
-            // nodes are interior (one branch-free pass); any other material
-            // node of the run goes through the checks below (which reject it:
-            // it lacks a cut link towards a void or outside neighbour)
-            const int32_t xl = (p < L.size() && L[p]->node < row0 + nx)
-                                   ? (int32_t)(L[p]->node - row0) : nx;
-            if (x < xl) {
-                const uint8_t *__restrict__ fr = full.data();
-                uint8_t *__restrict__ cr = crow;
-                uint32_t cnt = 0;
-                for (int32_t q = x; q < xl; ++q) {
-                    cr[q] = fr[q];
-                    cnt += fr[q];
-                }
-                t->interior += cnt;
-                int32_t bad = xl;
-                for (int32_t q = x; q < xl; ++q)
-                    if (!full[q] && d.node_type[row0 + q]) {
-                        bad = q;
-                        break;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nparts = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)hw, 16, ny / 64}));
+    std::vector<Part> parts((size_t)nparts);
+    auto classify_rows = [&](int part) {
+        Part &out = parts[(size_t)part];
+        const int32_t ya = (int32_t)((int64_t)ny * part / nparts);
+        const int32_t yb = (int32_t)((int64_t)ny * (part + 1) / nparts);
+        // first cut link of the chunk
+        size_t p = (size_t)(std::lower_bound(L.begin(), L.end(), (int64_t)ya * nx,
+                                             [](const lbm_link *l, int64_t node) {
+                                                 return l->node < node;
+                                             }) -
+                            L.begin());
+        // full[x] of row y: the node and its eight neighbours are all material.
+        // Formed as the AND of three horizontal 3-ANDs (rows y - 1, y, y + 1;
+        // outside the box counts as void), so most nodes are classified interior
+        // without the per-link checks below.
+        std::vector<uint8_t> h0((size_t)nx, 0), h1((size_t)nx, 0), h2((size_t)nx, 0),
+            full((size_t)nx, 0);
+        auto hrow = [&](int32_t yy, std::vector<uint8_t> &h) {
+            if (yy < 0 || yy >= ny) {
+                std::fill(h.begin(), h.end(), (uint8_t)0);
+                return;
+            }
+            const uint8_t *__restrict__ r = d.node_type + (int64_t)yy * nx;
+            uint8_t *__restrict__ o = h.data();
+            o[0] = 0;
+            o[nx - 1] = 0;
+            for (int32_t x = 1; x < nx - 1; ++x)
+                o[x] = (uint8_t)((r[x - 1] != 0) & (r[x] != 0) & (r[x + 1] != 0));
+        };
+        hrow(ya - 1, h0);
+        hrow(ya, h1);
+        for (int32_t y = ya; y < yb; ++y) {
+            hrow(y + 1, h2);
+            {
+                const uint8_t *__restrict__ a = h0.data(), *__restrict__ b = h1.data(),
+                                           *__restrict__ c = h2.data();
+                uint8_t *__restrict__ o = full.data();
+                for (int32_t x = 0; x < nx; ++x) o[x] = (uint8_t)(a[x] & b[x] & c[x]);
+            }
+            std::swap(h0, h1);
+            std::swap(h1, h2);
+            const int64_t row0 = (int64_t)y * nx;
+            uint8_t *crow = t->cls.data() + (size_t)y * t->pitch;
+            static_assert(kInterior == 1, "a full node's class is its flag");
+            for (int32_t x = 0; x < nx; ++x) {
+                // the run of nodes up to the next one with cut links: its full
+                // nodes are interior (one branch-free pass); any other material
+                // node of the run goes through the checks below (which reject it:
+                // it lacks a cut link towards a void or outside neighbour)
+                const int32_t xl = (p < L.size() && L[p]->node < row0 + nx)
+                                       ? (int32_t)(L[p]->node - row0) : nx;
+                if (x < xl) {
+                    const uint8_t *__restrict__ fr = full.data();
+                    uint8_t *__restrict__ cr = crow;
+                    uint32_t cnt = 0;
+                    for (int32_t q = x; q < xl; ++q) {
+                        cr[q] = fr[q];
+                        cnt += fr[q];
                     }
-                if (bad == xl) {
-                    x = xl - 1;
+                    out.interior += cnt;
+                    int32_t bad = xl;
+                    for (int32_t q = x; q < xl; ++q)
+                        if (!full[q] && d.node_type[row0 + q]) {
+                            bad = q;
+                            break;
+                        }
+                    if (bad == xl) {
+                        x = xl - 1;
+                        continue;
+                    }
+                    x = bad;
+                    crow[x] = kVoid;
+                }
+                const int64_t node = row0 + x;
+                const lbm_link *mine[kQ] = {nullptr};
+                uint16_t cut = 0;
+                while (p < L.size() && L[p]->node == node) {
+                    mine[L[p]->dir] = L[p];
+                    cut |= (uint16_t)(1u << L[p]->dir);
+                    ++p;
+                }
+                if (!d.node_type[node]) continue;
+                // every link to a void or outside node must be cut
+                for (int i = 1; i < kQ; ++i) {
+                    const int32_t tx = x + kCx[i], ty = y + kCy[i];
+                    const bool outside = tx < 0 || tx >= nx || ty < 0 || ty >= ny;
+                    if ((outside || !d.node_type[(int64_t)ty * nx + tx]) && !(cut & (1u << i))) {
+                        out.err = "lbm_create: node (" + std::to_string(x) + "," + std::to_string(y) +
+                                  ") links to a void or outside node in direction " +
+                                  std::to_string(i) + " without a cut link";
+                        return;
+                    }
+                }
+                if (!cut) {
+                    crow[x] = kInterior;
+                    ++out.interior;
                     continue;
                 }
-                x = bad;
-                crow[x] = kVoid;
-            }
-            const int64_t node = row0 + x;
-            const lbm_link *mine[kQ] = {nullptr};
-            uint16_t cut = 0;
-            while (p < L.size() && L[p]->node == node) {
-                mine[L[p]->dir] = L[p];
-                cut |= (uint16_t)(1u << L[p]->dir);
-                ++p;
-            }
-            if (!d.node_type[node]) continue;
-            // every link to a void or outside node must be cut
-            for (int i = 1; i < kQ; ++i) {
-                const int32_t tx = x + kCx[i], ty = y + kCy[i];
-                const bool outside = tx < 0 || tx >= nx || ty < 0 || ty >= ny;
-                if ((outside || !d.node_type[(int64_t)ty * nx + tx]) && !(cut & (1u << i))) {
-                    set_error("lbm_create: node (" + std::to_string(x) + "," + std::to_string(y) +
-                              ") links to a void or outside node in direction " +
-                              std::to_string(i) + " without a cut link");
-                    return LBM_ERR_ARG;
+                crow[x] = kBoundary;
+                BNode bn;
+                std::memset(&bn, 0, sizeof bn);
+                bn.x = x;
+                bn.y = y;
+                bn.cut = cut;
+                BLink slots[8];
+                std::memset(slots, 0, sizeof slots);
+                for (int i = 1; i < kQ; ++i) {
+                    if (!(cut & (1u << i))) continue;
+                    const lbm_link &l = *mine[i];
+                    BLink &s = slots[i - 1];
+                    s.q = (float)l.q;
+                    s.n0 = (float)l.n[0];
+                    s.n1 = (float)l.n[1];
+                    // upstream node x - c_i usable?
+                    const int32_t ux = x - kCx[i], uy = y - kCy[i];
+                    const bool up_ok = ux >= 0 && ux < nx && uy >= 0 && uy < ny &&
+                                       d.node_type[(int64_t)uy * nx + ux] && !(cut & (1u << kOpp[i]));
+                    if (!up_ok) bn.miss |= (uint16_t)(1u << i);
+                    const bool da = d.bcs[l.bc].kind == LBM_BC_DIRICHLET;
+                    const bool db = l.bc2 >= 0 && d.bcs[l.bc2].kind == LBM_BC_DIRICHLET;
+                    if (da || db) {
+                        bn.dirich |= (uint16_t)(1u << i);
+                        const int32_t first = da ? l.bc : l.bc2;
+                        const int32_t second = (da && db) ? l.bc2 : first;
+                        s.bc = (uint16_t)first;
+                        s.bc2 = (uint16_t)second;
+                    } else if (l.bc2 >= 0) {
+                        bn.corner |= (uint16_t)(1u << i);
+                        s.bc = (uint16_t)l.bc;
+                        s.bc2 = (uint16_t)l.bc2;
+                    } else {
+                        s.bc = (uint16_t)l.bc;
+                        s.bc2 = (uint16_t)l.bc;
+                    }
                 }
+                out.bn.push_back(bn);
+                for (int i = 0; i < 8; ++i) out.bl.push_back(slots[i]);
             }
-            if (!cut) {
-                t->cls[(size_t)y * t->pitch + x] = kInterior;
-                ++t->interior;
-                continue;
-            }
-            t->cls[(size_t)y * t->pitch + x] = kBoundary;
-            BNode bn;
-            std::memset(&bn, 0, sizeof bn);
-            bn.x = x;
-            bn.y = y;
-            bn.cut = cut;
-            BLink slots[8];
-            std::memset(slots, 0, sizeof slots);
-            for (int i = 1; i < kQ; ++i) {
-                if (!(cut & (1u << i))) continue;
-                const lbm_link &l = *mine[i];
-                BLink &s = slots[i - 1];
-                s.q = (float)l.q;
-                s.n0 = (float)l.n[0];
-                s.n1 = (float)l.n[1];
-                // upstream node x - c_i usable?
-                const int32_t ux = x - kCx[i], uy = y - kCy[i];
-                const bool up_ok = ux >= 0 && ux < nx && uy >= 0 && uy < ny &&
-                                   d.node_type[(int64_t)uy * nx + ux] && !(cut & (1u << kOpp[i]));
-                if (!up_ok) bn.miss |= (uint16_t)(1u << i);
-                const bool da = d.bcs[l.bc].kind == LBM_BC_DIRICHLET;
-                const bool db = l.bc2 >= 0 && d.bcs[l.bc2].kind == LBM_BC_DIRICHLET;
-                if (da || db) {
-                    bn.dirich |= (uint16_t)(1u << i);
-                    const int32_t first = da ? l.bc : l.bc2;
-                    const int32_t second = (da && db) ? l.bc2 : first;
-                    s.bc = (uint16_t)first;
-                    s.bc2 = (uint16_t)second;
-                } else if (l.bc2 >= 0) {
-                    bn.corner |= (uint16_t)(1u << i);
-                    s.bc = (uint16_t)l.bc;
-                    s.bc2 = (uint16_t)l.bc2;
-                } else {
-                    s.bc = (uint16_t)l.bc;
-                    s.bc2 = (uint16_t)l.bc;
-                }
-            }
-            t->bnodes.push_back(bn);
-            for (int i = 0; i < 8; ++i) t->blinks.push_back(slots[i]);
         }
+    };
+    std::vector<std::thread> workers;
+    for (int part = 1; part < nparts; ++part) workers.emplace_back(classify_rows, part);
+    classify_rows(0);
+    for (auto &w : workers) w.join();
+    size_t nb = 0;
+    for (const Part &q : parts) {
+        if (!q.err.empty()) {  // the first chunk with an error holds the first offending node
+            set_error(q.err);
+            return LBM_ERR_ARG;
+        }
+        nb += q.bn.size();
+    }
+    t->bnodes.reserve(nb);
+    t->blinks.reserve(nb * 8);
+    for (const Part &q : parts) {
+        t->bnodes.insert(t->bnodes.end(), q.bn.begin(), q.bn.end());
+        t->blinks.insert(t->blinks.end(), q.bl.begin(), q.bl.end());
+        t->interior += q.interior;
     }
     return LBM_OK;
 }
