@@ -188,14 +188,25 @@ def lbm_geom_build(nx, ny, edge_bc=(0, 0, 0, 0), hole=None, crack=None):
     if crack is not None:
         g.crack_len, g.crack_bc = int(crack[0]), int(crack[1])
         g.crack_x0 = int(crack[2]) if len(crack) > 2 else 0
-    nt = np.zeros(int(nx) * int(ny), dtype=np.uint8)
+    nt = np.empty(int(nx) * int(ny), dtype=np.uint8)
     n = C.c_int64(0)
     ntp = nt.ctypes.data_as(C.POINTER(C.c_uint8))
-    _check(lib.lbm_geom_build(C.byref(g), ntp, None, 0, C.byref(n)))
-    links = np.zeros(n.value, dtype=LINK_DTYPE)
-    _check(lib.lbm_geom_build(C.byref(g), ntp, links.ctypes.data_as(C.c_void_p), n.value,
-                              C.byref(n)))
-    return nt.reshape(int(ny), int(nx)), links
+    # one build with room for every link of the box edges, the crack faces and
+    # the hole rim; a second only if that was too small (the first call
+    # reports the count)
+    cap = 16 * (int(nx) + int(ny)) + 64
+    if crack is not None:
+        cap += 16 * int(crack[0])
+    if hole is not None:
+        cap += int(64 * (abs(float(hole[2])) + 2))
+    links = np.empty(cap, dtype=LINK_DTYPE)
+    st = lib.lbm_geom_build(C.byref(g), ntp, links.ctypes.data_as(C.c_void_p), cap, C.byref(n))
+    if st != LBM_OK and n.value > cap:
+        links = np.empty(n.value, dtype=LINK_DTYPE)
+        st = lib.lbm_geom_build(C.byref(g), ntp, links.ctypes.data_as(C.c_void_p), n.value,
+                                C.byref(n))
+    _check(st)
+    return nt.reshape(int(ny), int(nx)), links[:n.value]
 
 
 class Desc:

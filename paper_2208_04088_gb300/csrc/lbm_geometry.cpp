@@ -74,17 +74,31 @@ static lbm_status build_geometry(const lbm_geom &g, uint8_t *node_type, std::vec
         return LBM_ERR_ARG;
     }
 
-    // node mask: void strictly inside the circle
+    // node mask: void strictly inside the circle (rows in chunks on host threads)
     const double R = g.hole_r;
-    for (int32_t y = 0; y < ny; ++y)
-        for (int32_t x = 0; x < nx; ++x) {
-            uint8_t m = 1;
-            if (hole) {
-                const double dx = x - g.hole_cx, dy = y - g.hole_cy;
-                if (dx * dx + dy * dy < R * R) m = 0;
+    {
+        auto rows = [&](int32_t ya, int32_t yb) {
+            for (int32_t y = ya; y < yb; ++y) {
+                uint8_t *row = node_type + (int64_t)y * nx;
+                std::memset(row, 1, (size_t)nx);
+                if (!hole) continue;
+                const double dy = y - g.hole_cy;
+                if (dy * dy >= R * R) continue;
+                for (int32_t x = 0; x < nx; ++x) {
+                    const double dx = x - g.hole_cx;
+                    if (dx * dx + dy * dy < R * R) row[x] = 0;
+                }
             }
-            node_type[(int64_t)y * nx + x] = m;
-        }
+        };
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nparts = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)hw, 16, ny / 64}));
+        std::vector<std::thread> workers;
+        for (int part = 1; part < nparts; ++part)
+            workers.emplace_back(rows, (int32_t)((int64_t)ny * part / nparts),
+                                 (int32_t)((int64_t)ny * (part + 1) / nparts));
+        rows(0, (int32_t)((int64_t)ny / nparts));
+        for (auto &w : workers) w.join();
+    }
 
     // crack plane between rows yb and yb + 1; tip at x = crack_len - 1/2
     const int32_t yb = ny / 2 - 1;
