@@ -215,8 +215,9 @@ lbm_status lbm_workspace_size(const lbm_desc *desc, uint64_t *bytes);
  * The caller keeps ownership of every host array; none is referenced after
  * return.  With temporal blocking, three blocked launches on the zero state
  * measure the SM cycles of every block and the strips are re-cut to balance
- * them (a launch plan with the smallest measured maximum is kept); the state
- * is then reset.  Synchronises the stream before returning. */
+ * them (a launch plan with the smallest measured maximum is kept; a lattice
+ * created again in the same process reuses it); the state is then reset.
+ * Synchronises the stream before returning. */
 lbm_status lbm_create(const lbm_desc *desc, void *stream, void *workspace,
                       uint64_t workspace_bytes, lbm_handle *out);
 

@@ -164,6 +164,8 @@ bool wave_supported(const Lattice &L);
 // the source needs the density gradient (lambda != mu).
 constexpr int kWaveGradK = 4;
 size_t wave_smem_bytes();
+// SMs of the current device (148 if it cannot be queried).
+int device_sms();
 // Upper bound of the blocks of one launch (entries of S.wave_tab and S.wave_cyc).
 size_t wave_table_entries(int nx, int ny);
 // Whether boundary node g takes the blocked kernel's eight-lane update (curved
@@ -182,7 +184,8 @@ cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, W
 // scaled by its block's measured/modelled ratio and the strips are cut again
 // (twice); the plan with the smallest measured maximum is kept in
 // S.wave_tab.  Leaves f[1], the displacements and the status word modified:
-// the caller resets the state.
+// the caller resets the state.  A lattice created again in the same process
+// (same size, boundary tables, kernel and device) reuses its measured plan.
 cudaError_t wave_calibrate(const Tables &t, const Lattice &L, const DevState &S, WaveMaps *m,
                            cudaStream_t s);
 // kWaveK steps from buffer `cur` into buffer cur ^ 1; the first of them is
