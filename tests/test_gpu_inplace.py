@@ -43,6 +43,9 @@ CASES = [
     _moving_wall_plate(),
     _with(W.edge_crack(256, 64, 0), wall_node=True, name="edge_crack_256_L64_node"),
     _with(W.centre_crack(32, 0), name="centre_crack_128_L32"),
+    # nearly every node a boundary node: the staging area is sized by the boundary list
+    _with(W.square_plate(3, 0), name="square_3"),
+    _with(W.square_plate(5, 0), name="square_5"),
 ]
 
 
