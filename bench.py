@@ -215,12 +215,19 @@ def run_reference(args):
 
 
 def _sources_sha(kernel):
+    """sha256 (first 16 hex) of the kernel's sources with comments and
+    whitespace removed: a record stays valid across comment edits, not code
+    edits."""
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_2208_04088_gb300", "csrc")
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -145,9 +145,10 @@ cudaError_t launch_gather_probe(const Lattice &L, const DevState &S, int count,
                                 cudaStream_t s);
 cudaError_t launch_reset(int storage, const Lattice &L, const DevState &S, cudaStream_t s);
 
-// Temporally blocked stepping (lbm_wave.cu): kWaveK steps per launch, FP32
-// storage, lambda = mu.  A block owns kWaveC columns, of which the middle
-// kWaveW are its core.
+// Temporally blocked stepping (kernels in lbm_wave.cu, launch plans in
+// lbm_plan.cpp): kWaveK steps per launch (kWaveGradK when lambda != mu), FP32
+// storage.  A block owns kWaveC columns, of which the middle kWaveW are its
+// core.
 constexpr int kWaveK = 8;
 constexpr int kWaveC = 128;
 constexpr int kWaveW = kWaveC - 2 * kWaveK;

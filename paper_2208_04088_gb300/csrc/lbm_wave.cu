@@ -19,11 +19,13 @@
 //
 // Per node and level the arithmetic is that of the one-step kernels: the
 // incoming populations (pulled, or given by the rules of Sec. 4) go through
-// collide().  Box edges and crack faces ("simple" boundary nodes) are updated
-// one lane per node; other boundary nodes by eight lanes, as in the
-// cooperative boundary kernel.  The rules are explicitly rounded and the
+// the same collision (collide_v), two nodes per lane as paired f32x2
+// operations.  Box edges and crack faces ("simple" boundary nodes) are pulled
+// one lane per node; other boundary nodes are updated by eight lanes, as in
+// the cooperative boundary kernel.  The rules are explicitly rounded and the
 // moments formed in one order, so every stored value is bit-identical to the
-// one-step path.
+// one-step path.  The blocks of a launch are planned on the host
+// (lbm_plan.cpp).
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
