@@ -69,29 +69,12 @@ __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict_
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kGY;
     const int x = x0 + tx, y = y0 + ty;
-    bool live = false;
-    float f[9];
-    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-    int64_t k = 0;
-    float own = 0.0f;
-    if (x < L.nx && y < L.ny) {
-        k = (int64_t)y * L.pitch + x;
-        const uint8_t c = __ldg(cls + k);
-        if (c == kInterior) {
-            live = true;
-            pull_interior(src, k, L.pitch, L.fplane, L.inv_scale, f);
-            w = uc[k];
-            own = moments(f).dr;
-        } else if (c == kBoundary) {
-            own = rho[k];
-        }
-    }
-    rs[ty + 1][tx + 1] = own;
     // the ring: top and bottom rows (kBX + 2 each), left and right columns (kGY each)
     const int tid = ty * kBX + tx;
     constexpr int kRing = 2 * (kBX + 2) + 2 * kGY;
+    int hx = 0, hy = 0;
+    int64_t kk = -1;  // lattice index of this thread's ring node, if any
     if (tid < kRing) {
-        int hx, hy;
         if (tid < kBX + 2) {
             hx = tid;
             hy = 0;
@@ -106,20 +89,36 @@ __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict_
             hy = tid - 2 * (kBX + 2) - kGY + 1;
         }
         const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-        float v = 0.0f;
-        if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
-            const int64_t kk = (int64_t)gy * L.pitch + gx;
-            const uint8_t c = __ldg(cls + kk);
-            if (c == kInterior) {
-                float g[9];
-                pull_interior(src, kk, L.pitch, L.fplane, L.inv_scale, g);
-                v = moments(g).dr;
-            } else if (c == kBoundary) {
-                v = rho[kk];
-            }
-        }
-        rs[hy][hx] = v;
+        if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) kk = (int64_t)gy * L.pitch + gx;
     }
+    // the node's and the ring node's loads are all issued before either
+    // density is summed, so a ring thread waits for one memory round trip
+    bool live = false, ring_int = false;
+    float f[9], g[9];
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t k = 0;
+    float own = 0.0f, v = 0.0f;
+    uint8_t c = kVoid, cr = kVoid;
+    if (x < L.nx && y < L.ny) {
+        k = (int64_t)y * L.pitch + x;
+        c = __ldg(cls + k);
+    }
+    if (kk >= 0) cr = __ldg(cls + kk);
+    if (c == kInterior) {
+        live = true;
+        pull_interior(src, k, L.pitch, L.fplane, L.inv_scale, f);
+        w = uc[k];
+    }
+    if (cr == kInterior) {
+        ring_int = true;
+        pull_interior(src, kk, L.pitch, L.fplane, L.inv_scale, g);
+    }
+    if (live) own = moments(f).dr;
+    else if (c == kBoundary) own = rho[k];
+    if (ring_int) v = moments(g).dr;
+    else if (cr == kBoundary) v = rho[kk];
+    rs[ty + 1][tx + 1] = own;
+    if (tid < kRing) rs[hy][hx] = v;
     __syncthreads();
     if (!live) return;
     // interior nodes have all four axis neighbours: central differences
