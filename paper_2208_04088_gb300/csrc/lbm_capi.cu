@@ -50,7 +50,7 @@ int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
     if (d.time_block == LBM_TIME_BLOCK) return ok ? k : 0;
     // The library default: blocked where that measured faster on GB300 --
     // lambda = mu (with lambda != mu the blocked kernel carries 4 levels and
-    // its collision warps set each row's time: 48 vs 45 GLUPS on the 2048^2
+    // its collision warps set each row's time: 48 vs 47 GLUPS on the 2048^2
     // crack, too small a margin to make it the default), lattices of at
     // least 2^21 nodes (below, the fill of each block's row pipeline dominates:
     // 1024^2 plate 29 vs 80 GLUPS), and at most one boundary node off box edges
