@@ -53,7 +53,7 @@ int steps_per_launch(const lbm_desc &d, const Tables &t, const Units &u) {
     // its collision warps set each row's time: 48 vs 47 GLUPS on the 2048^2
     // crack, too small a margin to make it the default), lattices of at
     // least 2^21 nodes (below, the fill of each block's row pipeline dominates:
-    // 1024^2 plate 29 vs 80 GLUPS), and at most one boundary node off box edges
+    // 1024^2 plate 57 vs 80 GLUPS), and at most one boundary node off box edges
     // and crack faces per 800 nodes: the blocked kernel updates those eight
     // lanes to a node at every level (2048^2 plates with a hole: radius 512,
     // one per 1022 nodes, 74 vs 59 GLUPS; radius 900, one per 582, 34 vs 48).
