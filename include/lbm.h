@@ -135,7 +135,7 @@ typedef struct {
  * of Sec. 5.1 to a relative 1e-3; the scheme then runs in lattice units with
  * mu_lattice = rho0/3 and lambda_lattice = (lambda/mu) rho0/3. */
 typedef struct {
-    int32_t nx, ny;          /* lattice size, 1..65535 each */
+    int32_t nx, ny;          /* lattice size, 2..65535 each (lbm_geom: 1..65535) */
     double lambda, mu, rho0; /* Lame parameters and reference density */
     double dx, dt;           /* lattice spacing, time step */
     double tau;              /* relaxation time tau_bar/dt of Eq. (coll), > 0.5 */

@@ -185,3 +185,73 @@ def serving_trace(count: int = 500, seed: int = 5, rate: float = 50.0,
             w = edge_crack(side, max(2, side // 4), steps, load)
         out.append((t, w))
     return out
+
+
+# Direction numbering of the link tables (the C ABI's lbm_link.dir): 1 +x,
+# 2 +y, 3 -x, 4 -y, 5 (+,+), 6 (-,+), 7 (-,-), 8 (+,-).
+_DIRS = ((0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1))
+_OPPOSITE = (0, 3, 4, 1, 2, 7, 8, 5, 6)
+
+
+def fragmented_solid(nx: int, ny: int, seed: int, void_frac: float = 0.2,
+                     crack_frac: float = 0.05, nbcs: int = 4):
+    """Seeded node mask and cut-link table of a fragmented solid, a stress case
+    for the boundary rules (no geometry of the paper has one).
+
+    Each node is void with probability `void_frac`.  Every link from a material
+    node to a void node or out of the box is cut; each link between two
+    material nodes is cut with probability `crack_frac`, on both sides (a crack
+    through the link).  A cut's wall distance q is 1/2 with probability 1/4 and
+    otherwise uniform in (0, 1]; across a crack the far side gets 1 - q (drawn
+    in (0, 1) there) and the opposite normal.  Normals are uniform unit vectors;
+    boundary-condition indices are uniform in range(nbcs); no corner links.
+
+    Returns node_type (uint8, ny x nx) and a dict of equal-length columns
+    node, dir, bc, bc2, q, n0, n1 in (node, dir) order.
+    """
+    rng = np.random.default_rng(seed)
+    mat = (rng.random((ny, nx)) >= void_frac).astype(np.uint8)
+    crack = rng.random((ny, nx, 9)) < crack_frac
+    u = rng.random((ny, nx, 9))
+    q = np.where(rng.random((ny, nx, 9)) < 0.25, 0.5, 1.0 - u)  # 1 - u is in (0, 1]
+    q_crack = np.clip(u, 1e-3, 1.0 - 1e-3)
+    ang = rng.uniform(0.0, 2.0 * math.pi, (ny, nx, 9))
+    bcs = rng.integers(0, nbcs, (ny, nx, 9))
+    cut = {}
+    for y in range(ny):
+        for x in range(nx):
+            if not mat[y, x]:
+                continue
+            for i in range(1, 9):
+                tx, ty = x + _DIRS[i][0], y + _DIRS[i][1]
+                inside = 0 <= tx < nx and 0 <= ty < ny
+                if not inside or not mat[ty, tx]:
+                    cut[(y * nx + x, i)] = (int(bcs[y, x, i]), float(q[y, x, i]),
+                                            math.cos(ang[y, x, i]), math.sin(ang[y, x, i]))
+                elif (ty * nx + tx) > (y * nx + x) and crack[y, x, i]:
+                    # one draw per material-material link, taken at its lower node
+                    qa = float(q_crack[y, x, i])
+                    c, s = math.cos(ang[y, x, i]), math.sin(ang[y, x, i])
+                    b = int(bcs[y, x, i])
+                    cut[(y * nx + x, i)] = (b, qa, c, s)
+                    cut[(ty * nx + tx, _OPPOSITE[i])] = (b, 1.0 - qa, -c, -s)
+    keys = sorted(cut)
+    cols = {
+        "node": np.array([k[0] for k in keys], dtype=np.int32),
+        "dir": np.array([k[1] for k in keys], dtype=np.int32),
+        "bc": np.array([cut[k][0] for k in keys], dtype=np.int32),
+        "bc2": np.full(len(keys), -1, dtype=np.int32),
+        "q": np.array([cut[k][1] for k in keys], dtype=np.float64),
+        "n0": np.array([cut[k][2] for k in keys], dtype=np.float64),
+        "n1": np.array([cut[k][3] for k in keys], dtype=np.float64),
+    }
+    return mat, cols
+
+
+def fragmented_bcs(load: float = 5e-4) -> List[dict]:
+    """The four boundary conditions `fragmented_solid` indexes: a moving wall
+    (ramped), a traction, a pressure (ramped) and a general stress."""
+    return [bc(DIRICHLET, (0.4 * load, -0.3 * load), RAMP, 20.0),
+            bc(TRACTION, (0.6 * load, 0.2 * load)),
+            bc(PRESSURE, (0.5 * load,), RAMP, 10.0),
+            bc(STRESS, (0.7 * load, -0.4 * load, 0.3 * load))]

@@ -48,3 +48,39 @@ def rel_l2(a, b, mask):
 
 def compare(gpu, ora, keys=("u", "v", "sigma")):
     return {k: rel_l2(gpu[k], ora[k], ora["mask"]) for k in keys}
+
+
+def _table(dtype, cols):
+    t = np.zeros(len(cols["node"]), dtype=dtype)
+    for k in ("node", "dir", "bc", "bc2", "q", "n0", "n1"):
+        t[k] = cols[k]
+    return t
+
+
+def run_gpu_tables(nt, cols, bcs, lam, steps, time_block=0, in_place=False, storage="f32"):
+    """run_gpu for a node mask and cut-link columns given directly (not built
+    from an analytic geometry)."""
+    from paper_2208_04088_gb300 import _native as N
+    from paper_2208_04088_gb300 import workloads as W
+    d = N.Desc(nt, _table(N.LINK_DTYPE, cols), bcs, lam, W.MU, W.RHO0, tau=W.TAU,
+               storage=storage, time_block=time_block, in_place=in_place)
+    s = N.Solver(d)
+    s.step(steps)
+    s.sync()
+    F = s.fields_host()
+    F["info"] = s.info()
+    F["mask"] = nt.astype(bool)
+    s.close()
+    return F
+
+
+def run_oracle_tables(oracle_mod, nt, cols, bcs, lam, steps):
+    """run_oracle for the same tables; every link takes the curved rules, which
+    reduce to the lattice-conforming ones at q = 1/2."""
+    from paper_2208_04088_gb300 import workloads as W
+    links = _table(oracle_mod.LINK_DTYPE, cols)
+    links["curved"] = 1
+    o = oracle_mod.Oracle(nt, links, bcs, lam=lam, mu=W.MU, rho0=W.RHO0, tau=W.TAU)
+    o.step(steps)
+    F = o.fields()
+    return {"u": F["u"], "v": F["v"], "sigma": F["sigma"], "mask": nt.astype(bool)}

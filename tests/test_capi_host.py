@@ -215,3 +215,70 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(out[sname]) == C.sizeof(cls), sname
         for fname, _ in cls._fields_:
             assert int(out[f"{sname}.{fname}"]) == getattr(cls, fname).offset, (sname, fname)
+
+
+def _zero_links():
+    return np.zeros(0, dtype=N.LINK_DTYPE)
+
+
+def test_lattice_size_limits_and_empty_material():
+    bcs = [W.bc(W.DIRICHLET, (0.0, 0.0))]
+    for nx, ny in ((1, 8), (8, 1), (65536, 2), (2, 65536)):
+        with pytest.raises(N.LbmError) as e:
+            N.lbm_workspace_size(N.Desc(np.zeros((ny, nx), np.uint8), _zero_links(), bcs, W.MU, W.MU))
+        assert e.value.status == N.LBM_ERR_ARG
+        assert "2..65535" in N.lbm_last_error()
+    # the smallest lattice, and one with no material node at all, are accepted
+    assert N.lbm_workspace_size(N.Desc(np.zeros((2, 2), np.uint8), _zero_links(), bcs, W.MU, W.MU)) > 0
+    assert N.lbm_workspace_size(N.Desc(np.zeros((64, 256), np.uint8), _zero_links(), bcs, W.MU, W.MU,
+                                       time_block=N.LBM_TIME_BLOCK)) > 0
+    # a material node without its cut links is rejected
+    with pytest.raises(N.LbmError):
+        N.lbm_workspace_size(N.Desc(np.ones((4, 4), np.uint8), _zero_links(), bcs, W.MU, W.MU))
+
+
+DIRS = ((0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1))
+
+
+@pytest.mark.parametrize("args", [(150, 45, 7, 0.2, 0.05), (40, 30, 3, 0.6, 0.05), (33, 17, 1, 0.0, 0.3)])
+def test_fragmented_solid_tables(oracle_mod, args):
+    """The seeded fragmented solid: every link from a material node to a void
+    node or out of the box is cut, every cut between two material nodes is
+    paired with the reverse link (q and 1 - q, opposite normals), and both the
+    library and the oracle accept the tables."""
+    nx, ny, seed, vf, cf = args
+    nt, cols = W.fragmented_solid(nx, ny, seed, void_frac=vf, crack_frac=cf, nbcs=2)
+    cut = {(int(n), int(d)): k for k, (n, d) in enumerate(zip(cols["node"], cols["dir"]))}
+    assert len(cut) == len(cols["node"])
+    assert np.all((cols["q"] > 0) & (cols["q"] <= 1)) and np.all(cols["bc2"] == -1)
+    assert np.allclose(cols["n0"] ** 2 + cols["n1"] ** 2, 1.0)
+    cracks = 0
+    for y in range(ny):
+        for x in range(nx):
+            for i in range(1, 9):
+                key = (y * nx + x, i)
+                tx, ty = x + DIRS[i][0], y + DIRS[i][1]
+                if not nt[y, x]:
+                    assert key not in cut
+                    continue
+                if not (0 <= tx < nx and 0 <= ty < ny) or not nt[ty, tx]:
+                    assert key in cut
+                elif key in cut:
+                    back = cut[(ty * nx + tx, (i + 1) % 4 + 1 if i <= 4 else (i - 3) % 4 + 5)]
+                    k = cut[key]
+                    assert cols["q"][k] + cols["q"][back] == pytest.approx(1.0, abs=1e-12)
+                    assert cols["n0"][k] == -cols["n0"][back] and cols["n1"][k] == -cols["n1"][back]
+                    cracks += 1
+    assert cracks > 0  # every case draws some cracks
+    bcs = [W.bc(W.DIRICHLET, (1e-4, 0.0)), W.bc(W.DIRICHLET, (0.0, 1e-4))]
+    links = np.zeros(len(cols["node"]), dtype=N.LINK_DTYPE)
+    for k in ("node", "dir", "bc", "bc2", "q", "n0", "n1"):
+        links[k] = cols[k]
+    assert N.lbm_workspace_size(N.Desc(nt, links, bcs, W.MU, W.MU)) > 0
+    olinks = np.zeros(len(cols["node"]), dtype=oracle_mod.LINK_DTYPE)
+    for k in ("node", "dir", "bc", "bc2", "q", "n0", "n1"):
+        olinks[k] = cols[k]
+    olinks["curved"] = 1
+    o = oracle_mod.Oracle(nt, olinks, bcs, lam=W.MU, mu=W.MU)
+    o.step(2)
+    assert np.all(np.isfinite(o.fields()["u"]))

@@ -1,0 +1,98 @@
+"""GPU: a fragmented solid and a lattice without material (C ABI vs the oracle).
+
+The seeded fragmented solid (``workloads.fragmented_solid``) makes most
+material nodes boundary nodes:
+
+* isolated nodes with all eight links cut;
+* cracks through links between two material nodes;
+* wall distances q anywhere in (0, 1];
+* upstream nodes missing across cuts (the lattice-conforming fallback);
+* up to a full warp of curved-wall nodes in one row of the blocked kernel.
+
+Its walls are Dirichlet only.  Around single nodes with free surfaces the
+Neumann rules have no elastic restoring force, and such runs grow without bound
+in the oracle as in the library.  Run lengths stay where the oracle's fields are
+bounded and a relative perturbation of 1e-9 grows to no more than about 1e-6.
+
+Tolerance: relative L2 <= 1e-5 per field, except v of the sparse case (1e-4).
+There the walls hold the isolated nodes near the wall velocities while stress
+builds up: |v| is 0.0085 of |sigma| (0.05 in the wide case).  Rounding of the
+populations, which carry both, therefore shows in v amplified against v's
+size.  Uniform noise of 2^-24 of each stored deviation, injected into the
+oracle every step, gives a v error 90 times its u error in that case; the
+library shows 80 times (2.6e-5 against 3.3e-7).
+"""
+import numpy as np
+import pytest
+
+from paper_2208_04088_gb300 import _native as N
+from paper_2208_04088_gb300 import workloads as W
+
+from helpers import compare, run_gpu_tables, run_oracle_tables
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+TB = N.LBM_TIME_BLOCK
+
+BCS = [W.bc(W.DIRICHLET, (2e-4, -1.5e-4), W.RAMP, 20.0), W.bc(W.DIRICHLET, (-1e-4, 3e-4))]
+
+# (nx, ny, seed, void fraction, crack fraction, steps)
+WIDE = (150, 45, 7, 0.2, 0.05, 45)     # nx >= 128: the blocked kernels apply
+SPARSE = (40, 30, 3, 0.6, 0.05, 120)   # mostly isolated nodes
+V_TOL = {WIDE: TOL, SPARSE: 1e-4}
+
+
+def _tables(case):
+    nx, ny, seed, vf, cf, steps = case
+    nt, cols = W.fragmented_solid(nx, ny, seed, void_frac=vf, crack_frac=cf, nbcs=len(BCS))
+    return nt, cols, steps
+
+
+def _assert_same(a, b):
+    for k in ("u", "v", "sigma"):
+        assert np.array_equal(a[k], b[k]), (k, float(np.abs(a[k] - b[k]).max()))
+
+
+@pytest.mark.parametrize("lam_over_mu", [1.0, 0.8])
+@pytest.mark.parametrize("case", [WIDE, SPARSE], ids=["wide", "sparse"])
+def test_fragmented_solid_against_oracle(oracle_mod, case, lam_over_mu):
+    nt, cols, steps = _tables(case)
+    lam = lam_over_mu * W.MU
+    gpu = run_gpu_tables(nt, cols, BCS, lam, steps, time_block=1)
+    assert gpu["info"]["boundary_nodes"] > 0.6 * int(nt.sum())
+    ora = run_oracle_tables(oracle_mod, nt, cols, BCS, lam, steps)
+    err = compare(gpu, ora)
+    assert err["u"] <= TOL and err["sigma"] <= TOL and err["v"] <= V_TOL[case], err
+    for k in ("u", "v", "sigma"):
+        assert np.all(gpu[k][..., ~ora["mask"]] == 0.0)
+
+
+@pytest.mark.parametrize("lam_over_mu", [1.0, 0.8])
+def test_fragmented_solid_blocked_bit_identical(lam_over_mu):
+    nt, cols, steps = _tables(WIDE)
+    lam = lam_over_mu * W.MU
+    a = run_gpu_tables(nt, cols, BCS, lam, steps, time_block=1)
+    b = run_gpu_tables(nt, cols, BCS, lam, steps, time_block=TB)
+    assert a["info"]["time_block"] == 1 and b["info"]["time_block"] > 1
+    _assert_same(a, b)
+
+
+@pytest.mark.parametrize("case", [WIDE, SPARSE], ids=["wide", "sparse"])
+def test_fragmented_solid_in_place_bit_identical(case):
+    nt, cols, steps = _tables(case)
+    a = run_gpu_tables(nt, cols, BCS, W.MU, steps, time_block=1)
+    b = run_gpu_tables(nt, cols, BCS, W.MU, steps, in_place=True)
+    assert b["info"]["streaming"] == N.LBM_STREAM_IN_PLACE
+    _assert_same(a, b)
+
+
+@pytest.mark.parametrize("nx,ny,time_block,in_place",
+                         [(16, 16, 0, False), (16, 16, 0, True), (256, 64, TB, False)])
+def test_lattice_without_material(nx, ny, time_block, in_place):
+    nt = np.zeros((ny, nx), dtype=np.uint8)
+    cols = {k: np.zeros(0, dtype=np.int32 if k in ("node", "dir", "bc", "bc2") else np.float64)
+            for k in ("node", "dir", "bc", "bc2", "q", "n0", "n1")}
+    F = run_gpu_tables(nt, cols, BCS, W.MU, 20, time_block=time_block, in_place=in_place)
+    assert F["info"]["boundary_nodes"] == 0 and F["info"]["interior_nodes"] == 0
+    for k in ("u", "v", "sigma"):
+        assert np.all(F[k] == 0.0)
