@@ -55,8 +55,11 @@ constexpr int kChunk = 16;  // steps per replayed graph
 // shared memory once per tile, so the per-node code reads its lattice
 // parameters from shared memory (as the single-solver kernel reads them from
 // the parameter bank).  Schedules: 0 persistent grid stride, 1 persistent with
-// tiles handed out by an atomic counter, 2 one tile per block.
-template <class T, int TX, int TY>
+// tiles handed out by an atomic counter, 2 one tile per block.  kMixed: the
+// batch holds in-place instances, so each tile branches on its instance's
+// streaming; without them the pull-only form is launched (the three inlined
+// node updates of the mixed form cost registers: 88 bytes of spills against 24).
+template <class T, int TX, int TY, bool kMixed>
 __global__ void __launch_bounds__(TX *TY, 2048 / (TX * TY)) k_batch_interior(const InstDev *__restrict__ insts,
                                                            const int2 *__restrict__ tiles,
                                                            BatchCounts *__restrict__ counts,
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(TX *TY, 2048 / (TX * TY)) k_batch_interior(con
             if (x < I.L.nx && y < I.L.ny) {
                 const int cur = (int)(time & 1);
                 const int64_t k = (int64_t)y * I.L.pitch + x;
-                if (I.L.in_place) {  // one buffer: the AA step of the instance's parity
+                if (kMixed && I.L.in_place) {  // one buffer: the AA step of the instance's parity
                     T *f = static_cast<T *>(I.f[0]);
                     if (cur)
                         interior_node<T, kAAOdd>(f, f, I.uc, I.cls, nullptr, I.L, k, I.status);
@@ -438,7 +441,10 @@ cudaError_t launch_interior_shape(lbm_engine *E, cudaStream_t s) {
     const unsigned blocks = sched == 2 ? (unsigned)std::max<int64_t>(1, E->ntiles)
                                        : (unsigned)(E->shape.blocks_per_sm * E->sms);
     const dim3 blk(TX, TY), grd(blocks);
-    k_batch_interior<T, TX, TY><<<grd, blk, 0, s>>>(E->d_inst, E->d_tiles, E->d_counts, sched);
+    if (E->n_in_place > 0)
+        k_batch_interior<T, TX, TY, true><<<grd, blk, 0, s>>>(E->d_inst, E->d_tiles, E->d_counts, sched);
+    else
+        k_batch_interior<T, TX, TY, false><<<grd, blk, 0, s>>>(E->d_inst, E->d_tiles, E->d_counts, sched);
     return cudaGetLastError();
 }
 
@@ -455,7 +461,11 @@ cudaError_t launch_batch_step_t(lbm_engine *E, cudaStream_t s_main, cudaStream_t
         cudaStreamWaitEvent(s_side, E->fork, 0);
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * E->sms);
+    // four blocks per SM: the boundary kernel is bound by the latency of its
+    // dependent loads (list entry, instance record, populations); two blocks per
+    // SM left 12 % of the warp slots active, and four measured 1-2 % faster
+    // steps on 256 plates with holes (it overlaps the interior tiles)
+    cfg.gridDim = dim3(4 * E->sms);
     cfg.blockDim = dim3(kB8);
     cfg.stream = s_b;
     cudaLaunchAttribute attr[1];
