@@ -282,3 +282,52 @@ def test_fragmented_solid_tables(oracle_mod, args):
     o = oracle_mod.Oracle(nt, olinks, bcs, lam=W.MU, mu=W.MU)
     o.step(2)
     assert np.all(np.isfinite(o.fields()["u"]))
+
+
+def _random_geometry(rng):
+    nx, ny = int(rng.integers(2, 90)), int(rng.integers(2, 90))
+    edge_bc = tuple(int(b) for b in rng.integers(0, 3, 4))
+    kind = int(rng.integers(0, 3))
+    hole = crack = None
+    if kind == 1:
+        # centres anywhere (on half-integers too, or off the box), radii from
+        # below one spacing to beyond the box
+        cx = float(rng.choice([rng.uniform(-5, nx + 5), rng.integers(0, nx) + 0.5]))
+        cy = float(rng.choice([rng.uniform(-5, ny + 5), rng.integers(0, ny) + 0.5]))
+        hole = (cx, cy, float(rng.uniform(0.3, 0.6 * max(nx, ny))), 3)
+    elif kind == 2:
+        ny += ny % 2
+        length = int(rng.integers(1, nx + 3))
+        x0 = int(rng.integers(0, nx)) if rng.random() < 0.5 else 0
+        crack = (length, 3, x0)
+    return dict(nx=nx, ny=ny, edge_bc=edge_bc, hole=hole, crack=crack)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_geometry_tables_bit_exact_with_oracle(oracle_mod, seed):
+    """lbm_geom_build and the oracle's geometry, written apart, on seeded random
+    boxes, holes and cracks: identical masks and bit-identical link tables, or
+    both reject the arguments."""
+    rng = np.random.default_rng(1000 + seed)
+    for _ in range(25):
+        g = _random_geometry(rng)
+        try:
+            nt_o, lk_o = oracle_mod.geometry(**g)
+        except ValueError:
+            with pytest.raises(N.LbmError):
+                N.lbm_geom_build(**g)
+            continue
+        nt_l, lk_l = N.lbm_geom_build(**g)
+        assert np.array_equal(nt_o, nt_l), g
+        assert len(lk_o) == len(lk_l), g
+        for f in ("node", "dir", "bc", "bc2"):
+            assert np.array_equal(lk_o[f], lk_l[f]), (f, g)
+        for f in ("q", "n0", "n1"):
+            assert np.array_equal(lk_o[f].view(np.uint64), lk_l[f].view(np.uint64)), (f, g)
+
+
+def test_hole_covering_the_box_leaves_no_material(oracle_mod):
+    g = dict(nx=12, ny=9, edge_bc=(0, 0, 0, 0), hole=(5.5, 4.0, 50.0, 1), crack=None)
+    nt_o, lk_o = oracle_mod.geometry(**g)
+    nt_l, lk_l = N.lbm_geom_build(**g)
+    assert nt_o.sum() == 0 and nt_l.sum() == 0 and len(lk_o) == 0 and len(lk_l) == 0
