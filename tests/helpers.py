@@ -84,3 +84,24 @@ def run_oracle_tables(oracle_mod, nt, cols, bcs, lam, steps):
     o.step(steps)
     F = o.fields()
     return {"u": F["u"], "v": F["v"], "sigma": F["sigma"], "mask": nt.astype(bool)}
+
+
+def random_geometry(rng, nmin=2, nmax=90):
+    """Seeded random box, hole or crack (geometry arguments of lbm_geom_build);
+    boundary-condition indices 0..3."""
+    nx, ny = int(rng.integers(nmin, nmax)), int(rng.integers(nmin, nmax))
+    edge_bc = tuple(int(b) for b in rng.integers(0, 3, 4))
+    kind = int(rng.integers(0, 3))
+    hole = crack = None
+    if kind == 1:
+        # centres anywhere (on half-integers too, or off the box), radii from
+        # below one spacing to beyond the box
+        cx = float(rng.choice([rng.uniform(-5, nx + 5), rng.integers(0, nx) + 0.5]))
+        cy = float(rng.choice([rng.uniform(-5, ny + 5), rng.integers(0, ny) + 0.5]))
+        hole = (cx, cy, float(rng.uniform(0.3, 0.6 * max(nx, ny))), 3)
+    elif kind == 2:
+        ny += ny % 2
+        length = int(rng.integers(1, nx + 3))
+        x0 = int(rng.integers(0, nx)) if rng.random() < 0.5 else 0
+        crack = (length, 3, x0)
+    return dict(nx=nx, ny=ny, edge_bc=edge_bc, hole=hole, crack=crack)

@@ -11,6 +11,8 @@ import re
 import numpy as np
 import pytest
 
+from helpers import random_geometry
+
 from paper_2208_04088_gb300 import _native as N
 from paper_2208_04088_gb300 import workloads as W
 
@@ -284,25 +286,6 @@ def test_fragmented_solid_tables(oracle_mod, args):
     assert np.all(np.isfinite(o.fields()["u"]))
 
 
-def _random_geometry(rng):
-    nx, ny = int(rng.integers(2, 90)), int(rng.integers(2, 90))
-    edge_bc = tuple(int(b) for b in rng.integers(0, 3, 4))
-    kind = int(rng.integers(0, 3))
-    hole = crack = None
-    if kind == 1:
-        # centres anywhere (on half-integers too, or off the box), radii from
-        # below one spacing to beyond the box
-        cx = float(rng.choice([rng.uniform(-5, nx + 5), rng.integers(0, nx) + 0.5]))
-        cy = float(rng.choice([rng.uniform(-5, ny + 5), rng.integers(0, ny) + 0.5]))
-        hole = (cx, cy, float(rng.uniform(0.3, 0.6 * max(nx, ny))), 3)
-    elif kind == 2:
-        ny += ny % 2
-        length = int(rng.integers(1, nx + 3))
-        x0 = int(rng.integers(0, nx)) if rng.random() < 0.5 else 0
-        crack = (length, 3, x0)
-    return dict(nx=nx, ny=ny, edge_bc=edge_bc, hole=hole, crack=crack)
-
-
 @pytest.mark.parametrize("seed", range(6))
 def test_random_geometry_tables_bit_exact_with_oracle(oracle_mod, seed):
     """lbm_geom_build and the oracle's geometry, written apart, on seeded random
@@ -310,7 +293,7 @@ def test_random_geometry_tables_bit_exact_with_oracle(oracle_mod, seed):
     both reject the arguments."""
     rng = np.random.default_rng(1000 + seed)
     for _ in range(25):
-        g = _random_geometry(rng)
+        g = random_geometry(rng)
         try:
             nt_o, lk_o = oracle_mod.geometry(**g)
         except ValueError:

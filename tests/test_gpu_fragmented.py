@@ -18,9 +18,9 @@ Tolerance: relative L2 <= 1e-5 per field, except v of the sparse case (1e-4).
 There the walls hold the isolated nodes near the wall velocities while stress
 builds up: |v| is 0.0085 of |sigma| (0.05 in the wide case).  Rounding of the
 populations, which carry both, therefore shows in v amplified against v's
-size.  Uniform noise of 2^-24 of each stored deviation, injected into the
-oracle every step, gives a v error 90 times its u error in that case; the
-library shows 80 times (2.6e-5 against 3.3e-7).
+size.  Uniform noise of 2^-24 of each stored deviation from the rest state,
+injected into the oracle every step, gives relative errors of 1.2e-5 in v and
+2.4e-7 in u in that case; the library shows 2.6e-5 and 3.3e-7.
 """
 import numpy as np
 import pytest
