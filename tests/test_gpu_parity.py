@@ -193,3 +193,70 @@ def test_centre_crack_non_poisson(oracle_mod):
     """The centre crack of Sec. 5.2 (both tips inside the plate), nu = 0.2174."""
     wl = W.centre_crack(50, 150, lam_over_mu=W.CRACK_PAPER_LAM_OVER_MU)
     _assert_parity(run_gpu(wl, wl.steps), run_oracle(oracle_mod, wl, wl.steps))
+
+
+RANDOM_BCS = [W.bc(W.DIRICHLET, (2e-4, -1e-4), W.RAMP, 15.0), W.bc(W.TRACTION, (6e-4, 2e-4)),
+              W.bc(W.PRESSURE, (4e-4,), W.RAMP, 10.0), W.bc(W.STRESS, (5e-4, -3e-4, 2e-4))]
+
+
+def _random_pair(oracle_mod, g, lam, steps, time_block=0):
+    from paper_2208_04088_gb300 import _native as N
+    from helpers import run_gpu_tables
+    nt, links = N.lbm_geom_build(**g)
+    gpu = run_gpu_tables(nt, links, RANDOM_BCS, lam, steps, time_block=time_block)
+    nt_o, lk_o = oracle_mod.geometry(**g)
+    o = oracle_mod.Oracle(nt_o, lk_o, RANDOM_BCS, lam=lam, mu=W.MU)
+    o.step(steps)
+    F = o.fields()
+    ora = {"u": F["u"], "v": F["v"], "sigma": F["sigma"], "mask": nt_o.astype(bool)}
+    # conditioning: the fields' response to a relative change of 1e-7 in tau
+    o = oracle_mod.Oracle(nt_o, lk_o, RANDOM_BCS, lam=lam, mu=W.MU, tau=W.TAU * (1 + 1e-7))
+    o.step(steps)
+    P = o.fields()
+    sens = compare({k: P[k] for k in ("u", "v", "sigma")}, ora)
+    return gpu, ora, {k: max(TOL, 20.0 * e) for k, e in sens.items()}
+
+
+@pytest.mark.parametrize("seed,lam_over_mu", [(0, 1.0), (1, 0.8)])
+def test_random_geometries(oracle_mod, seed, lam_over_mu):
+    """Seeded random boxes, holes (centres on or off the box, any radius) and
+    edge or centre cracks, 2..89 nodes a side, every edge drawing one of four
+    kinds of boundary condition, 80 steps.  Rounding noise of 2^-24 of each
+    stored deviation, injected into the oracle every step, moves these fields
+    by at most 4e-7.
+
+    Some draws leave small islands of material behind a hole with free walls.
+    These grow, and growth turns a systematic relative error of the FP32 path's
+    coefficients (about 1e-7: their FP32 values, the approximate reciprocal of
+    rho) into a field error some steps times larger.  Each geometry's bar is
+    therefore max(1e-5, 20 x the oracle's response to a 1e-7 change of tau).
+    A well-conditioned draw moves by 1e-8 to 1e-7 under that change, so the
+    bar stays 1e-5.  A 22 x 52 plate whose hole leaves 3-node corner islands
+    moves by 2e-6; the library's error there is 1.1e-5 in v."""
+    from helpers import random_geometry
+    rng = np.random.default_rng(2000 + seed)
+    for _ in range(6):
+        g = random_geometry(rng)
+        gpu, ora, bar = _random_pair(oracle_mod, g, lam_over_mu * W.MU, 80)
+        err = compare(gpu, ora)
+        assert all(err[k] <= bar[k] for k in err), (g, err, bar)
+        for k in ("u", "v", "sigma"):
+            assert np.all(gpu[k][..., ~ora["mask"]] == 0.0)
+
+
+def test_random_wide_geometries_blocked(oracle_mod):
+    """Random geometries of 128..199 nodes a side: the temporally blocked
+    kernel is bit-identical to one step per launch, and both meet the oracle."""
+    from helpers import random_geometry, run_gpu_tables
+    from paper_2208_04088_gb300 import _native as N
+    rng = np.random.default_rng(2002)
+    for _ in range(3):
+        g = random_geometry(rng, 128, 200)
+        gpu, ora, bar = _random_pair(oracle_mod, g, W.MU, 45, time_block=1)
+        err = compare(gpu, ora)
+        assert all(err[k] <= bar[k] for k in err), (g, err, bar)
+        nt, links = N.lbm_geom_build(**g)
+        blk = run_gpu_tables(nt, links, RANDOM_BCS, W.MU, 45, time_block=N.LBM_TIME_BLOCK)
+        assert blk["info"]["time_block"] == N.LBM_TIME_BLOCK
+        for k in ("u", "v", "sigma"):
+            assert np.array_equal(gpu[k], blk[k]), (g, k)
