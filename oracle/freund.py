@@ -18,8 +18,10 @@ of c_d, so the integrals are evaluated with a = 1, b = c_d/c_s, c_r = c_d/c_R
 and upper limit T = c_d t/l_c, and the correction is scaled by sqrt(l_c).
 F_+(0) is the paper's value, 0.8774, stated for its material (nu = 0.2174);
 its definition is not given, so other materials have no value of it here.
-Parity of ki1 against the paper is unpinned (its figure is not available); the
-tests check continuity with ki0 and compare it with the oracle's lattice run.
+ki1: parity unpinned.  Its absolute level is pinned to nothing the paper fixes
+(the figure is not available, and F_+(0) = 0.8774 does not follow from the
+plain Wiener-Hopf factor, which gives 0.8085); the tests check continuity with
+ki0 and compare it with the oracle's lattice run.
 """
 from __future__ import annotations
 
