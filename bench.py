@@ -246,6 +246,206 @@ def _traffic(wl, storage, kernel):
         return None
 
 
+
+def _alu_peak_tflops(dev, sm_mhz):
+    """FP32 rate of the device: SMs x 128 FP32 lanes x 2 (FMA) x SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, sms
+
+
+def _roofline_blocked(nodes, tblock, mean_launch_ms, bytes_per_update, lam_over_mu, hbm_peak,
+                      hbm_kind, clk, dev):
+    """Roofline of one temporally blocked launch: the HBM ceiling (one pass of
+    populations and displacement per launch) and the FP32 ceiling (tblock
+    updates per node); `bound` is the one with the longer minimum time."""
+    fpu = FLOPS_PER_UPDATE if lam_over_mu == 1.0 else FLOPS_PER_UPDATE_GRAD
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    alu_peak, sms = _alu_peak_tflops(dev, sm_mhz)
+    updates = nodes * tblock
+    t = mean_launch_ms * 1e-3
+    bytes_launch = nodes * bytes_per_update
+    flops_launch = updates * fpu
+    hbm = {"achieved": bytes_launch / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+           "frac": bytes_launch / t / 1e9 / hbm_peak, "peak_kind": hbm_kind,
+           "min_launch_us": bytes_launch / (hbm_peak * 1e9) * 1e6,
+           "bytes_per_launch": bytes_launch,
+           "bytes_per_update": bytes_launch / updates}
+    alu = {"achieved": flops_launch / t / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+           "frac": flops_launch / t / 1e12 / alu_peak,
+           "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)",
+           "min_launch_us": flops_launch / (alu_peak * 1e12) * 1e6,
+           "flops_per_update": fpu}
+    bound = "hbm" if hbm["min_launch_us"] >= alu["min_launch_us"] else "alu"
+    lead = hbm if bound == "hbm" else alu
+    return {"bound": bound, "achieved": lead["achieved"], "peak": lead["peak"],
+            "unit": lead["unit"], "frac": lead["frac"], "peak_kind": lead["peak_kind"],
+            "steps_per_launch": tblock, "updates_per_launch": updates,
+            "mean_launch_ms": mean_launch_ms,
+            "ceilings": {"hbm": hbm, "alu": alu},
+            "bound_rule": ("the lower roofline ceiling: arithmetic intensity "
+                           f"{flops_launch / bytes_launch:.2f} FLOP/B against the FP32/HBM ridge "
+                           f"{alu_peak * 1e3 / hbm_peak:.2f} FLOP/B")}
+
+
+
+def _solve_fn(solver, wl, N):
+    """One bench step of a solver: reset, every time step, fields on the device."""
+    import torch
+    dev = solver.workspace.device
+    u = torch.empty((2, wl.ny, wl.nx), device=dev)
+    v = torch.empty((2, wl.ny, wl.nx), device=dev)
+    sg = torch.empty((3, wl.ny, wl.nx), device=dev)
+
+    def solve():
+        solver.reset()
+        solver.step(wl.steps)
+        N.lbm_get_fields(solver.h, u.data_ptr(), v.data_ptr(), sg.data_ptr(), on_device=True)
+    return solve
+
+
+def _variant_record(wl, args, dev, stream, storage, wall_node, time_block, solves=5, warm=2):
+    """Throughput of one variant of the workload (same lattice, another storage,
+    wall reading or stepping form): `solves` graph-replayed solves timed with
+    CUDA events on the solver's stream, then one solve in timing mode for the
+    roofline of its dominant kernel."""
+    import torch
+
+    from paper_2208_04088_gb300 import _native as N
+    desc = N.desc_from_workload(wl, storage=storage, wall_node=wall_node, time_block=time_block)
+    nodes = int(desc.node_type.sum())
+    solver = N.Solver(desc, stream=stream, device=dev)
+    info = solver.info()
+    solve = _solve_fn(solver, wl, N)
+    for _ in range(warm):
+        solve()
+    solver.sync()
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(solves):
+        solve()
+    stop.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = start.elapsed_time(stop)
+    try:
+        solver.sync()
+        unstable = False
+    except N.LbmError as e:
+        unstable = e.status == N.LBM_ERR_UNSTABLE
+        if not unstable:
+            raise
+    tb = int(info["time_block"])
+    solver.set_timing(True)
+    solver.timing()
+    solver.reset()
+    solver.step(wl.steps - (wl.steps % tb if tb > 1 else 0))
+    tim = solver.timing()
+    solver.set_timing(False)
+    peak, peak_kind = _peaks()
+    if tb > 1:
+        mean_ms = tim["interior_ms"] / max(1, tim["steps"] // tb)
+        clk = {"sm_mhz": None}  # the nominal maximum clock for this secondary record
+        roof = _roofline_blocked(nodes, tb, mean_ms, info["bytes_per_update"], wl.lam_over_mu,
+                                 peak, peak_kind, clk, dev)
+        roof["kernel"] = "k_wave" if wl.lam_over_mu == 1.0 else "k_wave_grad"
+    else:
+        mean_ms = tim["interior_ms"] / max(1, tim["steps"])
+        gbs = info["interior_nodes"] * info["bytes_per_update"] / (mean_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                "frac": gbs / peak, "peak_kind": peak_kind,
+                "kernel": "k_interior_grad" if wl.lam_over_mu != 1.0 else "k_interior",
+                "bytes_per_update": info["bytes_per_update"],
+                "updates_per_launch": info["interior_nodes"], "mean_launch_ms": mean_ms,
+                "traffic": _traffic(wl, storage, "k_interior")}
+    solver.close()
+    return {"value": nodes * wl.steps * solves / (ms * 1e-3) / 1e9, "unit": "GLUPS",
+            "ms_per_solve": ms / solves, "solves": solves, "storage": storage,
+            "wall_values": "node" if wall_node else "extrapolate", "time_block": tb,
+            "unstable": unstable, "roofline": roof}
+
+
+def _k_apparent(sigma_yy, length, y):
+    """Apparent stress intensity ahead of the tip (tip at x = length - 1/2):
+    the largest sigma_yy sqrt(2 pi r) over r = 1.5 .. 10.5, sigma_yy averaged
+    over the two rows straddling the crack plane."""
+    import numpy as np
+    sy = 0.5 * (np.asarray(sigma_yy[y], np.float64) + np.asarray(sigma_yy[y - 1], np.float64))
+    xs = np.arange(length + 1, length + 11)
+    return float((sy[xs] * np.sqrt(2 * np.pi * (xs - (length - 0.5)))).max())
+
+
+def _rel_l2(a, b, mask):
+    import numpy as np
+    a = np.asarray(a, np.float64)[..., mask]
+    b = np.asarray(b, np.float64)[..., mask]
+    den = math.sqrt(float((b * b).sum()))
+    return math.sqrt(float(((a - b) ** 2).sum())) / den if den > 0 else float(abs(a).max())
+
+
+def _cpu_baseline_and_accuracy(wl, wall_node, dev, stream, sample_steps, t_k=500):
+    """The cpu_baseline leg: the FP64 oracle, as it stands, on all host cores,
+    over the whole solve of the workload.  Its first `sample_steps` steps are
+    the timed sample.  Its fields at t_k and at the last step are also the
+    reference of the accuracy record: the library's FP32 (default stepping
+    form), FP16 and BF16 solves of the same workload against them (relative L2
+    over material nodes), and the apparent stress intensity at t_k against
+    Freund's K_I^0 (Sec. 5.2, valid for t < l_c/c_d)."""
+    import numpy as np
+
+    import oracle
+    from paper_2208_04088_gb300 import _native as N
+
+    gpu = {}
+    for storage in ("f32", "f16", "bf16"):
+        s = N.Solver(N.desc_from_workload(wl, storage=storage, wall_node=wall_node),
+                     stream=stream, device=dev)
+        s.step(t_k)
+        a = s.fields_host()
+        s.step(wl.steps - t_k)
+        b = s.fields_host()
+        try:
+            s.sync()
+        except N.LbmError:
+            pass
+        gpu[storage] = (a, b)
+        s.close()
+    nt, links = oracle.geometry(**wl.geometry_args())
+    o = oracle.Oracle(nt, links, wl.bcs, lam=wl.lam, mu=wl.mu, rho0=wl.rho0, tau=wl.tau,
+                      wall_node=wall_node)
+    nodes = int(nt.sum())
+    t0 = time.perf_counter()
+    o.step(sample_steps)
+    el = time.perf_counter() - t0
+    cpu = {"value": nodes * sample_steps / el / 1e9, "unit": "GLUPS", "cores": oracle.threads(),
+           "kind": "oracle",
+           "sample": f"first {sample_steps} of {wl.steps} steps of the {wl.nx}x{wl.ny} "
+                     f"{wl.name} lattice ({nodes} material nodes), {el:.1f} s; the oracle "
+                     "then runs the rest of the solve for the accuracy record"}
+    o.step(t_k - o.t)
+    fk = o.fields()
+    o.step(wl.steps - o.t)
+    fl = o.fields()
+    o.close()
+    mask = nt.astype(bool)
+    length = wl.crack[0]
+    y = wl.ny // 2
+    k0 = float(oracle.freund_ki0(t_k, wl.bcs[1]["value"][0], wl.nu, wl.cd))
+    acc = {"reference": "FP64 oracle, same workload and wall reading",
+           "t_last": wl.steps, "t_k": t_k,
+           "K_I0_freund": k0, "K_apparent_oracle": _k_apparent(fk["sigma"][1], length, y)}
+    for storage, (a, b) in gpu.items():
+        ka = _k_apparent(a["sigma"][1], length, y)
+        acc[storage] = {
+            "rel_l2_t_last": {k: _rel_l2(b[k], fl[k], mask) for k in ("u", "v", "sigma")},
+            "rel_l2_t_k": {k: _rel_l2(a[k], fk[k], mask) for k in ("u", "v", "sigma")},
+            "K_apparent": ka,
+            "K_rel_to_oracle": ka / acc["K_apparent_oracle"] - 1.0,
+            "K_over_freund": ka / k0}
+    return cpu, acc
+
+
 def run_profile(args):
     """A short run for ncu captures: --profile N steps of the workload through
     lbm_step (replayed graphs and direct launches, as a solve) and its fields,
@@ -339,7 +539,11 @@ def run_batch(args):
         line = {
             "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": ms / args.steps,
+            "bench_step": (f"one batched solve: reset, {args.batch_steps} time steps of every "
+                           "instance"),
+            "ms_per_time_step": ms / args.steps / args.batch_steps,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": f"batched_{len(wls)}_hole_plates_seed4",
                        "instances": len(wls), "material_nodes": nodes,
@@ -358,6 +562,60 @@ def run_batch(args):
     return 0
 
 
+def _serve_trace(trace, storage, wall_node, budget_gb, tick_steps, in_place=False, gpu=0):
+    """Serve a seeded request trace (arrival time, workload) with the
+    continuous-batching server: requests are submitted when their arrival time
+    has passed on the wall clock, ticks run while any request is live.  Latency
+    runs from arrival to fields on the host; aggregate GLUPS is the work of all
+    requests over the makespan."""
+    import torch
+
+    from paper_2208_04088_gb300 import _native as N
+    from paper_2208_04088_gb300 import workloads as W
+
+    stream = torch.cuda.Stream()
+    srv = N.Server(int(budget_gb * (1 << 30)), storage=storage, stream=stream)
+    # warm the kernels and the graph on a small request
+    wid = srv.submit(N.desc_from_workload(W.square_plate(64, 0), storage=storage,
+                                          wall_node=wall_node), 64)
+    while srv.result(wid) is None:
+        srv.tick(tick_steps)
+    lat = []
+    lu = 0
+    unstable = 0
+    pending = list(trace)
+    live = {}
+    t0 = time.perf_counter()
+    with ClockSampler(gpu) as clocks:
+        while pending or live:
+            now = time.perf_counter() - t0
+            while pending and pending[0][0] <= now:
+                at, w = pending.pop(0)
+                d = N.desc_from_workload(w, storage=storage, wall_node=wall_node,
+                                         in_place=in_place)
+                live[srv.submit(d, w.steps)] = (at, w.nodes * w.steps)
+            if not live:
+                time.sleep(min(0.01, max(0.0, pending[0][0] - now)))
+                continue
+            srv.tick(tick_steps)
+            for rid in list(live):
+                r = srv.result(rid)
+                if r is not None:
+                    unstable += int(r["unstable"])
+                    at, work = live.pop(rid)
+                    lat.append(time.perf_counter() - t0 - at)
+                    lu += work
+    makespan = time.perf_counter() - t0
+    srv.close()
+    lat = sorted(lat)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    return {"value": lu / makespan / 1e9, "unit": "GLUPS", "requests": len(lat),
+            "latency_s": {"p50": p50, "p99": p99, "max": lat[-1]},
+            "unstable_requests": unstable, "makespan_s": makespan,
+            "storage": storage, "clocks": clocks.summary()}
+
+
 def run_serve(args):
     """Config 5: a seeded trace of solve requests with Poisson arrivals, served
     by the continuous-batching server under an HBM budget; p50/p99 latency from
@@ -371,58 +629,24 @@ def run_serve(args):
     N.load(build_if_missing=False)
     trace = W.serving_trace(args.requests, seed=5, rate=args.rate,
                             max_side=args.max_side, max_steps=args.max_steps)
-    wall_node = args.wall_values == "node"
-    stream = torch.cuda.Stream()
-    srv = N.Server(int(args.budget_gb * (1 << 30)), storage=args.storage, stream=stream)
-    # warm the kernels and the graph on a small request
-    wid = srv.submit(N.desc_from_workload(W.square_plate(64, 0), storage=args.storage,
-                                          wall_node=wall_node), 64)
-    while srv.result(wid) is None:
-        srv.tick(args.tick_steps)
-    lat = []
-    lu = 0
-    unstable = 0
-    pending = list(trace)
-    live = {}
-    t0 = time.perf_counter()
-    with ClockSampler(0) as clocks:
-        while pending or live:
-            now = time.perf_counter() - t0
-            while pending and pending[0][0] <= now:
-                at, w = pending.pop(0)
-                d = N.desc_from_workload(w, storage=args.storage, wall_node=wall_node,
-                                         in_place=args.streaming == "in-place")
-                live[srv.submit(d, w.steps)] = (at, w.nodes * w.steps)
-            if not live:
-                time.sleep(min(0.01, max(0.0, pending[0][0] - now)))
-                continue
-            srv.tick(args.tick_steps)
-            for rid in list(live):
-                r = srv.result(rid)
-                if r is not None:
-                    unstable += int(r["unstable"])
-                    at, work = live.pop(rid)
-                    lat.append(time.perf_counter() - t0 - at)
-                    lu += work
-    makespan = time.perf_counter() - t0
-    srv.close()
-    lat = sorted(lat)
-    p50 = lat[len(lat) // 2]
-    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    r = _serve_trace(trace, args.storage, args.wall_values == "node", args.budget_gb,
+                     args.tick_steps, in_place=args.streaming == "in-place")
     line = {
-        "metric": METRIC, "value": lu / makespan / 1e9, "unit": "GLUPS", "n_gpus": 1,
-        "steps": len(lat), "warmup": 1, "ms_per_step": makespan / len(lat) * 1e3,
+        "metric": METRIC, "value": r["value"], "unit": "GLUPS", "n_gpus": 1,
+        "steps": r["requests"], "warmup": 1,
+        "ms_per_step": r["makespan_s"] / r["requests"] * 1e3,
+        "bench_step": "one served request (makespan / requests)",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": f"serving_trace_seed5_rate{args.rate:g}_n{len(lat)}",
-                   "rate_per_s": args.rate, "requests": len(lat),
+        "config": {"workload": f"serving_trace_seed5_rate{args.rate:g}_n{r['requests']}",
+                   "rate_per_s": args.rate, "requests": r["requests"],
                    "sides": f"64..{args.max_side} (powers of two)",
                    "steps": f"1000..{args.max_steps} log-uniform",
                    "budget_gb": args.budget_gb, "tick_steps": args.tick_steps,
                    "storage": args.storage + " deviations", "wall_values": args.wall_values},
-        "latency_s": {"p50": p50, "p99": p99, "max": lat[-1]},
-        "unstable_requests": unstable,
-        "makespan_s": makespan, "clocks": clocks.summary(),
+        "latency_s": r["latency_s"],
+        "unstable_requests": r["unstable_requests"],
+        "makespan_s": r["makespan_s"], "clocks": r["clocks"],
         "roofline": None, "e2e": None, "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)
@@ -514,33 +738,26 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     clk = clocks.summary()
     if tblock > 1:
-        # temporally blocked kernel: a launch carries tblock steps with one HBM
-        # pass, so HBM is not its bound; it is bound by instruction issue.  The
-        # roofline is FP32 arithmetic: the algorithmic operations of one
-        # lattice update (collision on the raw moments and displacement update,
-        # FMA = 2) against 152 SMs x 128 FP32 lanes x 2 x the measured SM clock.
+        # temporally blocked kernel: one launch carries tblock steps of every
+        # node with one HBM pass.  Two roofline ceilings bound its launch time:
+        # HBM (the algorithmic bytes of one pass, bytes_per_update per node,
+        # against the measured copy peak) and FP32 arithmetic (the algorithmic
+        # operations of tblock updates per node, FMA = 2, against SMs x 128
+        # lanes x 2 x the sampled SM clock).  The bound is the ceiling that
+        # allows the smaller throughput, i.e. the longer minimum launch time.
         n_launch = max(1, tim["steps"] // tblock)
         mean_launch_ms = tim["interior_ms"] / n_launch
-        lu_per_launch = nodes * tblock
-        fpu = FLOPS_PER_UPDATE if wl.lam_over_mu == 1.0 else FLOPS_PER_UPDATE_GRAD
         kname = "k_wave" if wl.lam_over_mu == 1.0 else "k_wave_grad"
-        achieved = lu_per_launch * fpu / (mean_launch_ms * 1e-3) / 1e12
-        sm_mhz = clk.get("sm_mhz") or 2070.0
-        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak,
-                    "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage, kname),
-                    "kernel": kname, "steps_per_launch": tblock,
-                    "flops_per_update": fpu, "updates_per_launch": lu_per_launch,
-                    "mean_launch_ms": mean_launch_ms,
-                    "peak_kind": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured)",
-                    "hbm_algorithmic_gbs": nodes * info0["bytes_per_update"] / (mean_launch_ms * 1e-3) / 1e9,
-                    "hbm_peak_gbs": peak,
-                    "timing": (f"events around every blocked launch over {n_timed} solves "
-                               f"({tim['steps']} steps) in timing mode; that pass ran at "
-                               f"{timing_ms / max(1, tim['steps']) * 1e3:.1f} us/step vs "
-                               f"{elapsed_ms / args.steps / wl.steps * 1e3:.1f} us/step "
-                               "for the graph-replayed value")}
+        roofline = _roofline_blocked(nodes, tblock, mean_launch_ms, info0["bytes_per_update"],
+                                     wl.lam_over_mu, peak, peak_kind, clk, dev)
+        roofline.update({
+            "traffic": args.traffic if args.traffic is not None else _traffic(wl, args.storage, kname),
+            "kernel": kname,
+            "timing": (f"events around every blocked launch over {n_timed} solves "
+                       f"({tim['steps']} steps) in timing mode; that pass ran at "
+                       f"{timing_ms / max(1, tim['steps']) * 1e3:.1f} us/step vs "
+                       f"{elapsed_ms / args.steps / wl.steps * 1e3:.1f} us/step "
+                       "for the graph-replayed value")})
     else:
         # one step per launch: the interior kernel is HBM-bound; algorithmic
         # bytes per launch / mean launch time
@@ -601,18 +818,46 @@ def run_gpu(args):
                "includes": "lbm_create from host tables (classification, device allocation, "
                            "H2D), lbm_step, lbm_get_fields to pinned host, lbm_destroy"}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(wl, seconds=args.cpu_seconds)
-
     solver.close()
+
+    # the rest of the metric, measured in the same run (rank 0, one GPU only):
+    # the other wall reading, FP16 storage, a served trace, and the FP64
+    # oracle's run of the same solve (the cpu_baseline leg) with the accuracy
+    # of the FP32, FP16 and BF16 solves against it
+    extras = {}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "crack":
+        extras["paper_rule"] = _variant_record(wl, args, dev, stream, args.storage,
+                                               wall_node=not wall_node,
+                                               time_block=args.time_block)
+        extras["fp16"] = _variant_record(wl, args, dev, stream, "f16", wall_node=wall_node,
+                                         time_block=1)
+        from paper_2208_04088_gb300 import workloads as W
+        trace = W.serving_trace(args.sub_requests, seed=5, rate=args.sub_rate,
+                                max_side=args.sub_max_side, max_steps=args.sub_max_steps)
+        extras["serving"] = {
+            "trace": (f"seed 5, {args.sub_requests} requests, Poisson {args.sub_rate:g}/s, "
+                      f"sides 64..{args.sub_max_side}, steps 1000..{args.sub_max_steps}; "
+                      "150 GB budget, 256 steps per tick"),
+            "f32": _serve_trace(trace, "f32", wall_node, 150.0, 256, gpu=local),
+            "f16": _serve_trace(trace, "f16", wall_node, 150.0, 256, gpu=local)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if args.no_extras or args.workload != "crack":
+            cpu = _cpu_baseline(wl, seconds=args.cpu_seconds)
+        else:
+            cpu, extras["accuracy"] = _cpu_baseline_and_accuracy(
+                wl, wall_node, dev, stream, sample_steps=args.cpu_sample_steps)
     if rank == 0:
         esz = 4 if args.storage == "f32" else 2
         nbuf = 1 if args.streaming == "in-place" else 2  # population buffers
         line = {
             "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "ms_per_step": elapsed_ms / args.steps,
+            "bench_step": (f"one solve: reset, {wl.steps} time steps of the whole lattice, "
+                           "fields on the device"),
+            "ms_per_time_step": elapsed_ms / args.steps / wl.steps,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
             "data": "synthetic",
             "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "time_steps": wl.steps,
@@ -631,6 +876,7 @@ def run_gpu(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -654,7 +900,17 @@ def main():
                          "after ~700 steps of the crack and dominates the fields by 1500")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="oracle sample length when the accuracy record is not taken")
+    ap.add_argument("--cpu-sample-steps", type=int, default=500,
+                    help="timed oracle steps of the cpu_baseline leg (it then runs the rest "
+                         "of the solve untimed for the accuracy record)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the paper-rule, FP16, serving and accuracy records")
+    ap.add_argument("--sub-requests", type=int, default=40)
+    ap.add_argument("--sub-rate", type=float, default=10.0)
+    ap.add_argument("--sub-max-side", type=int, default=1024)
+    ap.add_argument("--sub-max-steps", type=int, default=20000)
     ap.add_argument("--timing-solves", type=int, default=3,
                     help="solves of the second timed pass that times each kernel launch")
     ap.add_argument("--ref-steps-per-step", type=int, default=4)

@@ -105,3 +105,39 @@ def random_geometry(rng, nmin=2, nmax=90):
         x0 = int(rng.integers(0, nx)) if rng.random() < 0.5 else 0
         crack = (length, 3, x0)
     return dict(nx=nx, ny=ny, edge_bc=edge_bc, hole=hole, crack=crack)
+
+
+# Rounding operations of FP32 arithmetic on the longest path from a stored
+# population to the population stored one step later in the library's
+# collision (raw moments 4, relaxation 4, inverse transform 2).
+FP32_ROUNDINGS_PER_STEP = 10
+
+
+def rounding_floor(oracle_mod, nt, links, bcs, lam, steps, seed=0, amp=2.0 ** -24):
+    """The FP32 rounding floor of a problem, measured on the oracle: after
+    every step each stored deviation f - f_rest is multiplied by 1 + e, e
+    uniform in [-amp, amp] (one FP32 rounding, amp = 2^-24), and the fields at
+    `steps` are compared with the clean run (relative L2 per field).  Errors of
+    independent roundings add in quadrature, so a path of n roundings per step
+    has a floor of about sqrt(n) times this."""
+    from paper_2208_04088_gb300 import workloads as W
+    import numpy as np
+    mask = nt.astype(bool)
+    clean = oracle_mod.Oracle(nt, links, bcs, lam=lam, mu=W.MU, rho0=W.RHO0, tau=W.TAU)
+    clean.step(steps)
+    A = clean.fields()
+    clean.close()
+    A["mask"] = mask
+    o = oracle_mod.Oracle(nt, links, bcs, lam=lam, mu=W.MU, rho0=W.RHO0, tau=W.TAU)
+    rng = np.random.default_rng(seed)
+    rest = np.zeros((nt.shape[0], nt.shape[1], 9))
+    rest[mask] = oracle_mod.feq(W.RHO0, (0.0, 0.0), (0.0, 0.0, 0.0))
+    for _ in range(steps):
+        o.step(1)
+        f, u = o.state()
+        d = f - rest
+        d *= 1.0 + amp * rng.uniform(-1.0, 1.0, d.shape)
+        o.set_state(rest + d, u, o.t)
+    B = o.fields()
+    o.close()
+    return compare(B, A)
