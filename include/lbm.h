@@ -50,8 +50,8 @@ typedef enum {
     LBM_ERR_ARG = 1,      /* invalid argument or inconsistent tables */
     LBM_ERR_NOMEM = 2,    /* device memory or workspace too small */
     LBM_ERR_CUDA = 3,     /* a CUDA runtime call failed (see lbm_last_error) */
-    LBM_ERR_UNSTABLE = 4, /* a non-finite moment was produced (Sec. 6: the
-                             scheme is not unconditionally stable) */
+    LBM_ERR_UNSTABLE = 4, /* a non-finite moment was produced (Sec. 6 lists
+                             the scheme's stability as an open issue) */
     LBM_ERR_TIMEOUT = 5   /* a bounded wait expired */
 } lbm_status;
 
@@ -271,6 +271,20 @@ lbm_status lbm_reset(lbm_handle h);
 lbm_status lbm_sync(lbm_handle h);
 
 lbm_status lbm_get_info(lbm_handle h, lbm_info *info);
+
+/* Limit of every bounded wait inside the kernels (the temporally blocked
+ * kernels wait for the tile copies of their input rows), in nanoseconds;
+ * 0 .. 60e9, default 1e9 (1 s).  The paper has no counterpart; this is a
+ * service of the library.  After a wait runs out the block issues no further
+ * copy and finishes its sweep on whatever its shared-memory rows hold (every
+ * table index it reads from them is clamped into its table, so all accesses
+ * stay in bounds); it then waits for every copy it still has in flight, each
+ * with the default limit, and exits.  lbm_sync and the next lbm_step return
+ * LBM_ERR_TIMEOUT, and the state of the lattice is undefined until lbm_reset.  A limit of 0 makes every wait give up at
+ * once, whether or not its copy has landed, so every blocked launch reports
+ * LBM_ERR_TIMEOUT: it exists to test this path.  Synchronises the handle's stream; takes effect
+ * from the next step.  LBM_ERR_ARG for a NULL handle or a limit out of range. */
+lbm_status lbm_set_wait_limit(lbm_handle h, int64_t limit_ns);
 
 /* Timing mode for profiling.  While enabled, lbm_step launches the kernels of
  * each step directly (no graphs; the boundary kernel on a private stream beside

@@ -109,6 +109,7 @@ SIGNATURES = {
     "lbm_reset": (C.c_int, [C.c_void_p]),
     "lbm_sync": (C.c_int, [C.c_void_p]),
     "lbm_get_info": (C.c_int, [C.c_void_p, C.POINTER(lbm_info)]),
+    "lbm_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "lbm_get_timing": (C.c_int, [C.c_void_p, C.POINTER(lbm_timing)]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
@@ -300,6 +301,10 @@ def lbm_get_info(h) -> dict:
     info = lbm_info()
     _check(load().lbm_get_info(h, C.byref(info)))
     return {k: getattr(info, k) for k, _ in lbm_info._fields_}
+
+
+def lbm_set_wait_limit(h, limit_ns: int) -> None:
+    _check(load().lbm_set_wait_limit(h, C.c_int64(int(limit_ns))))
 
 
 def lbm_set_timing(h, enable: bool) -> None:

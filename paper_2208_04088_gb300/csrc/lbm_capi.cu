@@ -104,6 +104,7 @@ Lattice make_lattice(const Tables &t, const Units &u, int storage) {
     L.ny = t.ny;
     L.pitch = t.pitch;
     L.nb = (int32_t)t.bnodes.size();
+    L.nbcs = (int32_t)t.bcs.size();
     L.plane = (int64_t)t.pitch * t.ny;
     L.fplane = L.plane;
     L.omega = (float)(1.0 / u.tau);
@@ -129,6 +130,7 @@ Lattice make_lattice(const Tables &t, const Units &u, int storage) {
     L.out_v = (float)u.U;
     L.out_s = (float)(u.U * u.U);
     L.grad = (u.lam != u.mu) ? 1 : 0;
+    L.wait_ns = kDefaultWaitNs;
     return L;
 }
 
@@ -577,6 +579,24 @@ extern "C" lbm_status lbm_get_info(lbm_handle h, lbm_info *info) {
     info->kernel_launches = h->launches;
     info->time_block = h->block;
     info->streaming = h->L.in_place ? LBM_STREAM_IN_PLACE : LBM_STREAM_TWO_BUFFERS;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_wait_limit(lbm_handle h, int64_t limit_ns) {
+    set_error("");
+    if (!h) {
+        set_error("lbm_set_wait_limit: NULL handle");
+        return LBM_ERR_ARG;
+    }
+    if (limit_ns < 0 || limit_ns > 60 * kDefaultWaitNs) {
+        set_error("lbm_set_wait_limit: the limit must lie in 0 .. 60e9 ns");
+        return LBM_ERR_ARG;
+    }
+    // captured graphs hold the lattice parameters by value: capture again
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_set_wait_limit: sync");
+    destroy_graphs(h);
+    h->L.wait_ns = limit_ns;
     return LBM_OK;
 }
 

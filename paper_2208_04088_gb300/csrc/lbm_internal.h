@@ -69,8 +69,13 @@ struct Lattice {
     int64_t fplane;             // elements per population plane: plane, or with
                                 // in-place streaming pitch * (ny + 2) (a ring of one node)
     int32_t in_place;           // one population buffer, AA pattern (lbm_desc.streaming)
-    int32_t pad;
+    int32_t nbcs;               // entries of the boundary-condition table
+    int64_t wait_ns;            // limit of a kernel's wait for a tile copy (lbm_set_wait_limit)
 };
+
+// Default of Lattice::wait_ns, and the limit of the waits that drain the
+// copies still in flight after a wait has run out: 1 s.
+constexpr int64_t kDefaultWaitNs = 1000000000;
 
 // Host-side result of validating and classifying an lbm_desc.
 struct Tables {

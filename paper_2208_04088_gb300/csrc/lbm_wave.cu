@@ -108,14 +108,16 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for a phase of an mbarrier, giving up after about a second.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for a phase of an mbarrier, giving up after limit_ns nanoseconds; a
+// limit of 0 gives up at once, whether or not the phase has completed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int64_t limit_ns) {
+    if (limit_ns <= 0) return false;
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (int outer = 0; outer < (1 << 24); ++outer) {
         for (int i = 0; i < 32; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > 1000000000ull) return false;
+        if (global_ns() - t0 > (uint64_t)limit_ns) return false;
     }
     return false;
 }
@@ -138,16 +140,28 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// Indices taken from a node word are clamped into their tables.  A node word
+// is only wrong when a block reads a ring row whose copy has not landed (after
+// a wait has run out, the block finishes its sweep on stale rows and reports
+// LBM_ERR_TIMEOUT); the clamps keep every access of such a sweep in bounds.
+//
 // The common link record of a simple node (node-word bits 35-52).
-__device__ __forceinline__ BLink simple_link(uint32_t hi) {
+__device__ __forceinline__ BLink simple_link(uint32_t hi, const Lattice &L) {
     const uint32_t code = (hi >> 16) & 3u;
+    const uint32_t bc = hi & 0xffffu;
     BLink sl;
     sl.q = 0.5f;
     sl.n0 = code == 0 ? 1.0f : (code == 1 ? -1.0f : 0.0f);
     sl.n1 = code == 2 ? 1.0f : (code == 3 ? -1.0f : 0.0f);
-    sl.bc = (uint16_t)(hi & 0xffffu);
+    sl.bc = (uint16_t)(bc < (uint32_t)L.nbcs ? bc : 0u);
     sl.bc2 = sl.bc;
     return sl;
+}
+
+// The boundary-list index of a node word (bits 35-63).
+__device__ __forceinline__ int64_t boundary_index(uint64_t w, const Lattice &L) {
+    const uint32_t g = (uint32_t)(w >> 35);
+    return g < (uint32_t)L.nb ? g : 0;
 }
 
 // Three consecutive ring rows of the level below and the node's column.
@@ -170,7 +184,7 @@ __device__ __forceinline__ void simple_pull(const Rows &ld, uint64_t nw,
                                             const BCDev *__restrict__ bcs, float tb,
                                             const Lattice &L, float f[9]) {
     const uint32_t cut = nw_mask(nw, 2), dirich = nw_mask(nw, 10), miss = nw_mask(nw, 26);
-    const BLink sl = simple_link((uint32_t)(nw >> 35));
+    const BLink sl = simple_link((uint32_t)(nw >> 35), L);
     float g[9];
 #pragma unroll
     for (int m = 0; m < 9; ++m) g[m] = ld(m, 0, 0);
@@ -290,8 +304,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         tma_load_2d(smem_addr(sm + kOffNw + (size_t)(j % kNU) * kNwRowBytes), &tnw, xin, y, bar);
         tma_load_3d(smem_addr(sm + kOffU + (size_t)(j % kNU) * kURowBytes), &tu, 0, X0, y, bar);
     };
-    auto wait_row = [&](int j) {
-        return mbar_wait(bar0 + 8u * (uint32_t)(j & (kNI - 1)), (uint32_t)((j / kNI) & 1));
+    auto wait_row = [&](int j, int64_t limit) {
+        return mbar_wait(bar0 + 8u * (uint32_t)(j & (kNI - 1)), (uint32_t)((j / kNI) & 1), limit);
     };
 
     bool ok = true;       // thread 0: every wait so far completed
@@ -308,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             j_issued = j;
         }
         for (int j = 0; j <= 2 && j <= j_last && ok; ++j) {
-            ok = wait_row(j);
+            ok = wait_row(j, L.wait_ns);
             last_waited = ok ? j : j - 1;
         }
     }
@@ -325,9 +339,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     // The sweep, compiled twice: with the boundary updates, and without them
     // for regions that hold no boundary node (their interior update is then
     // scheduled on its own).
+    float nonfinite = 0.0f;  // the last level's moments, summed: non-finite if any one is
     auto sweep = [&](auto with_boundary) {
         constexpr bool kB = decltype(with_boundary)::value;
         int ju_next = ((1 - 2 * (lv - 1)) % kNU + kNU) % kNU;
+        // node words of the row of the next step, loaded a step ahead (their
+        // rows landed at least one step earlier)
+        uint64_t pf_a, pf_b;
+        {
+            const int y0 = y_in0 + 1 - 2 * (lv - 1);
+            const bool in = y0 >= lo && y0 <= hi;
+            pf_a = (in && live_a) ? nwr[ju_next * kC + c] : 0ull;
+            pf_b = (in && live_b) ? nwr[ju_next * kC + c + 32] : 0ull;
+        }
         for (int n = 0; n < nsweep; ++n) {
             if (tid == 0 && n + kD + 2 <= j_last && ok) {
                 // order the block's earlier shared-memory accesses before the copy
@@ -342,8 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ju = ju_next;
             ju_next = ju + 1 == kNU ? 0 : ju + 1;
             if (y >= lo && y <= hi) {  // warp-uniform: one level per warp
-                const uint64_t nwa = live_a ? nwr[ju * kC + c] : 0ull;
-                const uint64_t nwb = live_b ? nwr[ju * kC + c + 32] : 0ull;
+                const uint64_t nwa = pf_a, nwb = pf_b;
                 const uint32_t cla = (uint32_t)(nwa & 3u), clb = (uint32_t)(nwb & 3u);
                 const float *rm = prev_base + ((j - 1) & pmask) * kRowF + c;
                 const float *r0 = prev_base + (j & pmask) * kRowF + c;
@@ -387,9 +410,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 const uint64_t wb = hb ? wbb : wa;
                                 const int cb = (half << 6) + m;
                                 const bool simple = (wb >> 34) & 1u;
-                                const uint32_t bh = (uint32_t)(wb >> 35);
-                                const BLink sl = simple_link(bh);
-                                const BLink *lrec = blinks + (int64_t)bh * 8;
+                                const BLink sl = simple_link((uint32_t)(wb >> 35), L);
+                                const BLink *lrec = blinks + boundary_index(wb, L) * 8;
                                 auto link = [&](int i) { return simple ? sl : lrec[i - 1]; };
                                 float f0;
                                 const float fk = boundary8_pull(
@@ -415,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                             *up = w;
                                         } else {
                                             uc[gb] = w;
-                                            flag_nonfinite(status, m00, jx, jy);
+                                            nonfinite = radd(nonfinite, radd(radd(m00, jx), jy));
                                         }
                                     }
                                 }
@@ -488,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     *up = w;
                                 } else {
                                     uc[grow + dc] = w;
-                                    flag_nonfinite(status, d, mx, my);
+                                    nonfinite = radd(nonfinite, radd(radd(d, mx), my));
                                 }
                             };
                             if (do_a && core_a) u_one(0, dra, jxa, jya);
@@ -501,8 +523,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 else
                     row(std::false_type{});
             }
+            {
+                const int yn = y + 1;
+                const bool in = yn >= lo && yn <= hi;
+                pf_a = (in && live_a) ? nwr[ju_next * kC + c] : 0ull;
+                pf_b = (in && live_b) ? nwr[ju_next * kC + c + 32] : 0ull;
+            }
             if (tid == 0 && n + 3 <= j_last && ok) {
-                ok = wait_row(n + 3);
+                ok = wait_row(n + 3, L.wait_ns);
                 if (!ok) last_waited = n + 2;
             }
             __syncthreads();
@@ -512,13 +540,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         sweep(std::true_type{});
     else
         sweep(std::false_type{});
+    if (!isfinite(nonfinite)) flag_nonfinite(status, nonfinite, 0.0f, 0.0f);
     if (cycles && tid == 0) cycles[blockIdx.x] = clock64() - t_start;
     if (tid == 0 && !ok) {
-        // a copy did not land in time: flag it, and give the copies still in
-        // flight a bounded chance to land before the block's shared memory goes
+        // a copy did not land within the limit (the rest of the sweep ran on
+        // stale rows; thread 0 issued no copy after that): flag it, then wait
+        // for every copy issued after the last completed wait, each with the
+        // default limit, so that none is still writing this block's shared
+        // memory when the block exits
         atomicOr(status, 2u);
-        for (int j = last_waited + 1; j <= j_issued; ++j)
-            if (!wait_row(j)) break;
+        for (int j = last_waited + 1; j <= j_issued; ++j) wait_row(j, kDefaultWaitNs);
     }
 }
 
@@ -624,9 +655,9 @@ __global__ void __launch_bounds__(kGradThreads, 1)
         tma_load_3d(smem_addr(sm + kGOffU + (size_t)(j % kGradNU) * kURowBytes), &tu, 0, X0, y,
                     bar);
     };
-    auto wait_row = [&](int j) {
+    auto wait_row = [&](int j, int64_t limit) {
         return mbar_wait(bar0 + 8u * (uint32_t)(j & (kGradNI - 1)),
-                         (uint32_t)((j / kGradNI) & 1));
+                         (uint32_t)((j / kGradNI) & 1), limit);
     };
 
     bool ok = true;        // thread 0: every wait so far completed
@@ -643,7 +674,7 @@ __global__ void __launch_bounds__(kGradThreads, 1)
             j_issued = j;
         }
         for (int j = 0; j <= 2 && j <= j_last && ok; ++j) {
-            ok = wait_row(j);
+            ok = wait_row(j, L.wait_ns);
             last_waited = ok ? j : j - 1;
         }
     }
@@ -718,7 +749,7 @@ __global__ void __launch_bounds__(kGradThreads, 1)
             const uint64_t wbb = __shfl_sync(0xffffffffu, nwb, src);
             const uint64_t wb = (m >> 5) ? wbb : wa;
             const int cb = (half << 6) + m;
-            const BLink *lrec = blinks + (int64_t)(uint32_t)(wb >> 35) * 8;
+            const BLink *lrec = blinks + boundary_index(wb, L) * 8;
             auto link = [&](int i) { return lrec[i - 1]; };
             float g0, f[9];
             const float fk = boundary8_pull(Rows{rm - c, r0 - c, rp - c, cb}, nw_mask(wb, 2),
@@ -892,7 +923,7 @@ __global__ void __launch_bounds__(kGradThreads, 1)
                     row(std::false_type{});
             }
             if (tid == 0 && n + 3 <= j_last && ok) {
-                ok = wait_row(n + 3);
+                ok = wait_row(n + 3, L.wait_ns);
                 if (!ok) last_waited = n + 2;
             }
             __syncthreads();
@@ -904,11 +935,13 @@ __global__ void __launch_bounds__(kGradThreads, 1)
         sweep(std::false_type{});
     if (cycles && tid == 0) cycles[blockIdx.x] = clock64() - t_start;
     if (tid == 0 && !ok) {
-        // a copy did not land in time: flag it, and give the copies still in
-        // flight a bounded chance to land before the block's shared memory goes
+        // a copy did not land within the limit (the rest of the sweep ran on
+        // stale rows; thread 0 issued no copy after that): flag it, then wait
+        // for every copy issued after the last completed wait, each with the
+        // default limit, so that none is still writing this block's shared
+        // memory when the block exits
         atomicOr(status, 2u);
-        for (int j = last_waited + 1; j <= j_issued; ++j)
-            if (!wait_row(j)) break;
+        for (int j = last_waited + 1; j <= j_issued; ++j) wait_row(j, kDefaultWaitNs);
     }
 }
 

@@ -162,3 +162,37 @@ def test_blocked_nonpoisson_full_size_crack_bit_identical():
     b = run_gpu(wl, wl.steps, time_block=TB)
     for k in ("u", "v", "sigma"):
         assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("lam_over_mu", [1.0, 0.8], ids=["k_wave", "k_wave_grad"])
+def test_wait_limit_runs_out_cleanly(lam_over_mu):
+    """With a wait limit of 0 the blocked kernels give up on their first tile
+    copy: every block stops before reading a ring row that has not landed,
+    drains the copies it has in flight and exits, and the host sees
+    LBM_ERR_TIMEOUT from lbm_sync and from the next lbm_step.  The context
+    stays usable: with the default limit back and a reset, the same handle
+    runs bit-identically to one step per launch."""
+    wl = W.edge_crack(256, 64, 0, lam_over_mu=lam_over_mu)
+    s = N.Solver(N.desc_from_workload(wl, time_block=TB))
+    assert s.info()["time_block"] > 1
+    N.lbm_set_wait_limit(s.h, 0)
+    s.step(16)
+    with pytest.raises(N.LbmError) as e:
+        s.sync()
+    assert e.value.status == N.LBM_ERR_TIMEOUT
+    with pytest.raises(N.LbmError) as e:   # the next asynchronous call reports it too
+        s.step(1)
+        s.step(1)
+    assert e.value.status == N.LBM_ERR_TIMEOUT
+    with pytest.raises(N.LbmError) as e:
+        N.lbm_set_wait_limit(s.h, -1)
+    assert e.value.status == N.LBM_ERR_ARG
+    N.lbm_set_wait_limit(s.h, 10 ** 9)
+    s.reset()
+    s.step(45)
+    s.sync()
+    got = s.fields_host()
+    s.close()
+    ref = run_gpu(wl, 45, time_block=1)
+    for k in ("u", "v", "sigma"):
+        assert np.array_equal(got[k], ref[k]), k
