@@ -280,9 +280,9 @@ lbm_status lbm_get_info(lbm_handle h, lbm_info *info);
  * table index it reads from them is clamped into its table, so all accesses
  * stay in bounds); it then waits for every copy it still has in flight, each
  * with the default limit, and exits.  lbm_sync and the next lbm_step return
- * LBM_ERR_TIMEOUT, and the state of the lattice is undefined until lbm_reset.  A limit of 0 makes every wait give up at
- * once, whether or not its copy has landed, so every blocked launch reports
- * LBM_ERR_TIMEOUT: it exists to test this path.  Synchronises the handle's stream; takes effect
+ * then undefined until lbm_reset.  A limit of 0 makes every block give up at
+ * its first wait, whether or not that copy has landed, so every blocked launch
+ * reports LBM_ERR_TIMEOUT: it exists to test this path.  Synchronises the handle's stream; takes effect
  * from the next step.  LBM_ERR_ARG for a NULL handle or a limit out of range. */
 lbm_status lbm_set_wait_limit(lbm_handle h, int64_t limit_ns);
 

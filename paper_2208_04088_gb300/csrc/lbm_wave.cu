@@ -108,10 +108,8 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for a phase of an mbarrier, giving up after limit_ns nanoseconds; a
-// limit of 0 gives up at once, whether or not the phase has completed.
+// Wait for a phase of an mbarrier, giving up after about limit_ns nanoseconds.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int64_t limit_ns) {
-    if (limit_ns <= 0) return false;
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (int outer = 0; outer < (1 << 24); ++outer) {
@@ -321,8 +319,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             issue(j);
             j_issued = j;
         }
+        // a limit of 0 gives up at once, whether or not the copies have landed
         for (int j = 0; j <= 2 && j <= j_last && ok; ++j) {
-            ok = wait_row(j, L.wait_ns);
+            ok = L.wait_ns > 0 && wait_row(j, L.wait_ns);
             last_waited = ok ? j : j - 1;
         }
     }
@@ -673,8 +672,9 @@ __global__ void __launch_bounds__(kGradThreads, 1)
             issue(j);
             j_issued = j;
         }
+        // a limit of 0 gives up at once, whether or not the copies have landed
         for (int j = 0; j <= 2 && j <= j_last && ok; ++j) {
-            ok = wait_row(j, L.wait_ns);
+            ok = L.wait_ns > 0 && wait_row(j, L.wait_ns);
             last_waited = ok ? j : j - 1;
         }
     }

@@ -12,9 +12,12 @@ t = 1500 are shared by the tests of this module.
 * The paper's extrapolated wall values (Eqs. abbcon and abbnoncon with the
   extrapolated rho^bd) grow a density mode at the traction-free box edges that
   reaches max |sigma| of about 13 (13000 x the load) by t = 1500 in the oracle
-  itself.  The library meets the same 1e-5 bar there at t = 500 and t = 1500;
-  the assertion message carries the oracle's response to a relative change of
-  1e-7 in tau, the conditioning of that run.
+  itself.  At t = 500 the library meets the 1e-5 bar.  At t = 1500 that run is
+  so ill-conditioned that a relative change of 1e-7 in tau (the size of one
+  FP32 rounding of an input) moves the oracle's u by 3 %, v by 2e-3 and sigma
+  by 1.2e-5; no FP32 computation can be closer to it than that.  The bar there
+  is therefore the oracle's own response to that change, field by field
+  (measured library error: 8e-3, 8e-4, 9e-6).
 * FP16 and BF16 storage: relative L2 against the oracle at t = 1500 within
   3e-3 (FP16) and 5e-2 (BF16; measured 2.0e-2 / 3.7e-2 / 3.3e-2 on u / v /
   sigma: rounding to nearest in an 8-bit significand keeps a population whose
@@ -97,13 +100,14 @@ def test_fp32_full_length_parity_paper_rule(oracle_mod):
     wl = _workload(False)
     ok, ol = _oracle_run(oracle_mod, wl)
     a, b, _ = _gpu_run(wl)
-    err_k, err_l = compare(a, ok), compare(b, ol)
-    if not all(e <= 1e-5 for e in list(err_k.values()) + list(err_l.values())):
-        _, pert = _oracle_run(oracle_mod, wl, tau=wl.tau * (1.0 + 1e-7))
-        sens = compare(pert, ol)
-        raise AssertionError(
-            f"max|sigma| at t=1500 is {float(np.abs(ol['sigma']).max()):.3g}; oracle response "
-            f"to a 1e-7 change of tau {sens}; library error at t=500 {err_k}, at t=1500 {err_l}")
+    err_k = compare(a, ok)
+    assert all(e <= 1e-5 for e in err_k.values()), err_k
+    _, pert = _oracle_run(oracle_mod, wl, tau=wl.tau * (1.0 + 1e-7))
+    sens = compare(pert, ol)
+    err_l = compare(b, ol)
+    assert all(err_l[k] <= max(1e-5, sens[k]) for k in err_l), (
+        f"max|sigma| at t=1500 is {float(np.abs(ol['sigma']).max()):.3g}; oracle response "
+        f"to a 1e-7 change of tau {sens}; library error {err_l}")
 
 
 @pytest.mark.parametrize("storage,bound,k_bound", [("f16", 3e-3, 1e-3), ("bf16", 5e-2, 1e-2)])
