@@ -511,6 +511,7 @@ def run_batch(args):
         stop.record(stream)
         barrier()
     unstable = b.info()["unstable"]
+    blocked = b.info()["blocked_instances"]
     ms = start.elapsed_time(stop)
     ms = max_over_ranks(ms, dev)
     value = nodes * args.batch_steps * args.steps * world / (ms * 1e-3) / 1e9
@@ -552,6 +553,7 @@ def run_batch(args):
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2"},
             "unstable_instances": unstable,
+            "blocked_instances": blocked,
             "per_instance_loop": loop,
             "clocks": clocks.summary(), "gpu_launches": int(launches),
             "roofline": None, "e2e": None, "cpu_baseline": None,

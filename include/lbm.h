@@ -330,14 +330,22 @@ typedef struct {
     uint64_t device_bytes;   /* arena bytes in use */
     int64_t kernel_launches;
     lbm_launch_shape shape;
+    int32_t blocked_instances; /* instances stepped by the temporally blocked kernel */
+    int32_t pad;
 } lbm_batch_stats;
 
 /* Create a batch of `count` instances (host descriptors as for lbm_create,
  * every one with lambda = mu and the same storage), all at rest at t = 0.
- * The batch steps every instance one step per launch (time_block of the
- * descriptors is not used); each instance keeps the streaming form its
- * descriptor asks for, and in-place instances take less of the arena.
- * Device memory: one arena sized for all instances.  Synchronous. */
+ * FP32 instances with two population buffers and nx >= 128 are stepped by the
+ * temporally blocked kernel: one persistent launch per LBM_TIME_BLOCK steps
+ * over the strip segments of all of them (segments of about 384 rows, the
+ * longest first, taken by the blocks from a counter).  The other instances
+ * are stepped one step per launch by the batched interior and boundary
+ * kernels.  time_block of the descriptors is not used; each instance keeps
+ * the streaming form its descriptor asks for, and in-place instances take
+ * less of the arena.  Either way every instance's fields are bit-identical
+ * to the instance stepped alone.  Device memory: one arena sized for all
+ * instances.  Synchronous. */
 lbm_status lbm_batch_create(const lbm_desc *descs, int32_t count, void *stream, lbm_batch *out);
 /* Advance every instance by nsteps (asynchronous). */
 lbm_status lbm_batch_step(lbm_batch b, int64_t nsteps);

@@ -77,7 +77,8 @@ class lbm_launch_shape(C.Structure):
 class lbm_batch_stats(C.Structure):
     _fields_ = [("instances", C.c_int32), ("unstable", C.c_int32), ("nodes", C.c_int64),
                 ("steps", C.c_int64), ("device_bytes", C.c_uint64),
-                ("kernel_launches", C.c_int64), ("shape", lbm_launch_shape)]
+                ("kernel_launches", C.c_int64), ("shape", lbm_launch_shape),
+                ("blocked_instances", C.c_int32), ("pad", C.c_int32)]
 
 
 class lbm_server_stats(C.Structure):

@@ -10,6 +10,12 @@
 // bit-identical fields alone and in a batch.  The table sizes and every
 // instance's clock live in device memory, so one captured CUDA graph stays
 // valid while instances come and go.
+//
+// In the lockstep batch, FP32 instances with two population buffers and at
+// least kWaveC columns are stepped by the temporally blocked kernel instead:
+// one persistent launch per kWaveK steps over the strip segments (regions) of
+// all of them, longest first, each block taking the next region from a
+// counter.  Its per-node arithmetic is that of the one-step kernels too.
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -38,7 +44,8 @@ struct InstDev {
     uint32_t *status;
     int64_t *time;   // completed steps (the instance's own clock)
     int64_t target;  // the instance stops stepping at this time
-    int32_t tiles_x, pad;
+    int32_t tiles_x;
+    int32_t blocked;  // stepped by the temporally blocked batch kernel
 };
 
 // Sizes of the work tables and the dynamic-schedule counters (device memory).
@@ -188,10 +195,17 @@ __global__ void k_batch_advance(const InstDev *__restrict__ insts,
                                 BatchCounts *__restrict__ counts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) counts->tile_counter = 0;
-    if (i < counts->ninst) {
+    if (i < counts->ninst && !insts[i].blocked) {
         int64_t *t = insts[i].time;
         if (*t < insts[i].target) *t += 1;
     }
+}
+
+// The clocks of the instances stepped by the blocked kernel, n steps on.
+__global__ void k_batch_advance_blocked(const InstDev *__restrict__ insts,
+                                        const BatchCounts *__restrict__ counts, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < counts->ninst && insts[i].blocked) *insts[i].time += n;
 }
 
 lbm_status fail_cuda(cudaError_t e, const char *where) {
@@ -275,6 +289,8 @@ struct DescCopy {
 
 struct Instance {
     int64_t id = -1;
+    bool blocked = false;  // stepped by the blocked batch kernel
+    int plan_blocks = 0;   // its regions (strip segments)
     lbm_solver *h = nullptr;
     uint64_t off = 0, bytes = 0;
     int64_t steps = 0;   // requested steps
@@ -317,8 +333,14 @@ struct lbm_engine {
     bool tables_dirty = true;
     lbm_launch_shape shape{32, 8, 8, 0};
     int sms = 0;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by the blocked instances' buffer
     bool graph_in_place = false;  // the captured graph orders the boundary kernel first
+    // instances stepped by the blocked kernel: their records and regions
+    WaveInst *d_winst = nullptr;
+    int4 *d_regions = nullptr;
+    int32_t *d_region_inst = nullptr, *d_wcounter = nullptr;
+    int cap_winst = 0, cap_regions = 0, nregions = 0, nblocked = 0;
+    int wcur = 0;  // the buffer that holds their populations
     int n_in_place = 0;           // instances with in-place streaming
     int64_t launches = 0;
     int64_t step_count = 0;  // steps run by the engine
@@ -326,6 +348,14 @@ struct lbm_engine {
 };
 
 namespace {
+
+void drop_graphs(lbm_engine *E) {
+    for (auto &g : E->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
 
 lbm_status ensure_capacity(lbm_engine *E, int ninst, int64_t ntiles, int64_t nbnodes) {
     bool realloc = false;
@@ -354,10 +384,83 @@ lbm_status ensure_capacity(lbm_engine *E, int ninst, int64_t ntiles, int64_t nbn
         realloc = true;
     }
     if (e != cudaSuccess) return fail_cuda(e, "batch: table allocation");
-    if (realloc && E->graph) {
-        cudaGraphExecDestroy(E->graph);
-        E->graph = nullptr;
+    if (realloc) drop_graphs(E);
+    return LBM_OK;
+}
+
+// Regions of the blocked instances: per instance, the strip segments of a
+// plan for plan_blocks blocks; all of them ordered by modelled cost (rows
+// swept), longest first, so that the blocks that take them from the counter
+// end close together.
+lbm_status rebuild_wave_tables(lbm_engine *E) {
+    std::vector<WaveInst> wi;
+    std::vector<std::pair<int, int4>> reg;  // (record, region)
+    for (size_t i = 0; i < E->inst.size(); ++i) {
+        const Instance &I = E->inst[i];
+        if (!I.blocked) continue;
+        const lbm_solver *h = I.h;
+        WaveInst w;
+        std::memset(&w, 0, sizeof w);
+        w.tf[0] = h->wave.f[0];
+        w.tf[1] = h->wave.f[1];
+        w.tnw = h->wave.nw;
+        w.tu = h->wave.u;
+        w.f[0] = static_cast<float *>(h->S.f[0]);
+        w.f[1] = static_cast<float *>(h->S.f[1]);
+        w.uc = h->S.ucomp;
+        w.blinks = h->S.blinks;
+        w.bcs = h->S.bcs;
+        w.time = h->S.time;
+        w.status = h->S.status;
+        w.L = h->L;
+        for (const int4 &r : wave_plan(h->tab, I.plan_blocks))
+            reg.emplace_back((int)wi.size(), r);
+        wi.push_back(w);
     }
+    std::stable_sort(reg.begin(), reg.end(),
+                     [](const std::pair<int, int4> &a, const std::pair<int, int4> &b) {
+                         return a.second.z > b.second.z;
+                     });
+    std::vector<int4> regions(reg.size());
+    std::vector<int32_t> rinst(reg.size());
+    for (size_t r = 0; r < reg.size(); ++r) {
+        regions[r] = reg[r].second;
+        rinst[r] = reg[r].first;
+    }
+    cudaError_t e = cudaSuccess;
+    if ((int)wi.size() > E->cap_winst) {
+        if (E->d_winst) cudaFree(E->d_winst);
+        E->cap_winst = std::max((int)wi.size(), 2 * E->cap_winst);
+        e = cudaMalloc(&E->d_winst, sizeof(WaveInst) * E->cap_winst);
+        drop_graphs(E);
+    }
+    if (e == cudaSuccess && (int)regions.size() > E->cap_regions) {
+        if (E->d_regions) cudaFree(E->d_regions);
+        if (E->d_region_inst) cudaFree(E->d_region_inst);
+        E->cap_regions = std::max((int)regions.size(), 2 * E->cap_regions);
+        e = cudaMalloc(&E->d_regions, sizeof(int4) * E->cap_regions);
+        if (e == cudaSuccess) e = cudaMalloc(&E->d_region_inst, sizeof(int32_t) * E->cap_regions);
+        drop_graphs(E);
+    }
+    if (e == cudaSuccess && !E->d_wcounter) e = cudaMalloc(&E->d_wcounter, sizeof(int32_t));
+    // sets the kernel's shared-memory limit (outside any capture); launches nothing
+    if (e == cudaSuccess && !wi.empty())
+        e = launch_wave_batch(nullptr, nullptr, nullptr, 0, nullptr, 0, 0, E->sms, E->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "batch: blocked tables");
+    if ((int)regions.size() != E->nregions || (int)wi.size() != E->nblocked) drop_graphs(E);
+    E->nregions = (int)regions.size();
+    E->nblocked = (int)wi.size();
+    if (!wi.empty())
+        e = cudaMemcpyAsync(E->d_winst, wi.data(), sizeof(WaveInst) * wi.size(),
+                            cudaMemcpyHostToDevice, E->stream);
+    if (e == cudaSuccess && !regions.empty())
+        e = cudaMemcpyAsync(E->d_regions, regions.data(), sizeof(int4) * regions.size(),
+                            cudaMemcpyHostToDevice, E->stream);
+    if (e == cudaSuccess && !rinst.empty())
+        e = cudaMemcpyAsync(E->d_region_inst, rinst.data(), sizeof(int32_t) * rinst.size(),
+                            cudaMemcpyHostToDevice, E->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);  // the host vectors die here
+    if (e != cudaSuccess) return fail_cuda(e, "batch: blocked tables upload");
     return LBM_OK;
 }
 
@@ -383,6 +486,8 @@ lbm_status rebuild_tables(lbm_engine *E) {
         d.time = h->S.time;
         d.target = E->server ? E->inst[i].steps : INT64_MAX;
         d.tiles_x = (h->L.nx + TX - 1) / TX;
+        d.blocked = E->inst[i].blocked ? 1 : 0;
+        if (d.blocked) continue;  // not in the one-step tables
         const int tiles_y = (h->L.ny + TY - 1) / TY;
         for (int t = 0; t < d.tiles_x * tiles_y; ++t) tiles.push_back(make_int2((int)i, t));
         for (int b = 0; b < h->L.nb; ++b) bmap.push_back(make_int2((int)i, b));
@@ -391,16 +496,12 @@ lbm_status rebuild_tables(lbm_engine *E) {
     if (st != LBM_OK) return st;
     E->n_in_place = 0;
     for (const InstDev &d : hi) E->n_in_place += d.L.in_place ? 1 : 0;
-    if (E->graph && E->graph_in_place != (E->n_in_place > 0)) {
-        // the order of the step's kernels changes
-        cudaGraphExecDestroy(E->graph);
-        E->graph = nullptr;
+    if (E->graph_in_place != (E->n_in_place > 0)) drop_graphs(E);  // the kernels' order changes
+    if (E->shape.dynamic == 2 && (int64_t)tiles.size() != E->ntiles) {
+        drop_graphs(E);  // one block per tile: the captured grid must match the table
     }
-    if (E->shape.dynamic == 2 && (int64_t)tiles.size() != E->ntiles && E->graph) {
-        // one block per tile: the captured grid must match the table
-        cudaGraphExecDestroy(E->graph);
-        E->graph = nullptr;
-    }
+    lbm_status wst = rebuild_wave_tables(E);
+    if (wst != LBM_OK) return wst;
     E->ntiles = (int64_t)tiles.size();
     BatchCounts c;
     std::memset(&c, 0, sizeof c);
@@ -511,18 +612,49 @@ cudaError_t launch_batch_step(lbm_engine *E, cudaStream_t s_main, cudaStream_t s
     }
 }
 
+// kChunk steps of the instances stepped by the blocked kernel: kChunk/kWaveK
+// launches from buffer `wcur` (an even number, so they end in it), then their
+// clocks.  They read the clocks at the start of the chunk (toff = the launch's
+// first step within it).
+static_assert(kChunk % (2 * kWaveK) == 0, "blocked launches per chunk");
+
+cudaError_t launch_blocked_chunk(lbm_engine *E, cudaStream_t s) {
+    if (E->nblocked == 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    int cur = E->wcur;
+    for (int toff = 0; toff < kChunk && e == cudaSuccess; toff += kWaveK) {
+        e = cudaMemsetAsync(E->d_wcounter, 0, sizeof(int32_t), s);
+        if (e == cudaSuccess)
+            e = launch_wave_batch(E->d_winst, E->d_regions, E->d_region_inst, E->nregions,
+                                  E->d_wcounter, cur, toff, E->sms, s);
+        cur ^= 1;
+    }
+    if (e != cudaSuccess) return e;
+    k_batch_advance_blocked<<<(std::max(1, E->cap_inst) + 255) / 256, 256, 0, s>>>(
+        E->d_inst, E->d_counts, kChunk);
+    return cudaGetLastError();
+}
+
+// Launches of one chunk beyond the blocked part: the one-step steps of the
+// other instances (none when every instance is blocked).
+int64_t one_step_instances(const lbm_engine *E) {
+    return (int64_t)E->inst.size() - E->nblocked;
+}
+
 lbm_status build_batch_graph(lbm_engine *E) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(E->cap_main, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail_cuda(e, "batch: begin capture");
-    for (int s = 0; s < kChunk && e == cudaSuccess; ++s)
-        e = launch_batch_step(E, E->cap_main, E->cap_side);
+    e = launch_blocked_chunk(E, E->cap_main);
+    if (one_step_instances(E) > 0)
+        for (int s = 0; s < kChunk && e == cudaSuccess; ++s)
+            e = launch_batch_step(E, E->cap_main, E->cap_side);
     cudaError_t e2 = cudaStreamEndCapture(E->cap_main, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return fail_cuda(e != cudaSuccess ? e : e2, "batch: capture");
     }
-    e = cudaGraphInstantiate(&E->graph, g, 0);
+    e = cudaGraphInstantiate(&E->graph[E->wcur], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail_cuda(e, "batch: instantiate");
     E->graph_in_place = E->n_in_place > 0;
@@ -538,26 +670,55 @@ lbm_status engine_steps(lbm_engine *E, int64_t nsteps) {
     if (E->inst.empty() || nsteps <= 0) return LBM_OK;
     cudaError_t e = cudaSuccess;
     int64_t done = 0;
+    const int per_step = one_step_instances(E) > 0 ? (E->n_in_place > 0 ? 4 : 3) : 0;
     if (nsteps >= kChunk) {
-        if (!E->graph) {
+        if (!E->graph[E->wcur]) {
             lbm_status st = build_batch_graph(E);
             if (st != LBM_OK) return st;
         }
         for (; done + kChunk <= nsteps; done += kChunk) {
-            e = cudaGraphLaunch(E->graph, E->stream);
+            e = cudaGraphLaunch(E->graph[E->wcur], E->stream);
             if (e != cudaSuccess) return fail_cuda(e, "batch: graph launch");
+            E->launches += per_step * kChunk + (E->nblocked > 0 ? kChunk / kWaveK + 1 : 0);
         }
     }
-    for (; done < nsteps; ++done) {
-        e = launch_batch_step(E, E->stream, E->cap_side);
-        if (e != cudaSuccess) return fail_cuda(e, "batch: launch");
+    const int64_t rest = nsteps - done;
+    if (rest > 0) {
+        if (one_step_instances(E) > 0)
+            for (int64_t k = 0; k < rest; ++k) {
+                e = launch_batch_step(E, E->stream, E->cap_side);
+                if (e != cudaSuccess) return fail_cuda(e, "batch: launch");
+            }
+        E->launches += per_step * rest;
+        // the blocked instances take the rest of the steps with their own
+        // launches, as lbm_step would: blocked launches, then one-step ones
+        for (auto &I : E->inst) {
+            if (!I.blocked) continue;
+            lbm_solver *h = I.h;
+            for (int64_t k = 0; k < rest && e == cudaSuccess;) {
+                if (rest - k >= kWaveK) {
+                    e = launch_wave(h->L, h->S, h->wave, h->cur, (int)k, E->stream);
+                    k += kWaveK;
+                    E->launches += 1;
+                } else {
+                    e = launch_step(h->storage, h->L, h->S, h->cur, (int)k, E->stream, nullptr,
+                                    nullptr, nullptr, nullptr);
+                    k += 1;
+                    E->launches += kernels_per_step(h->L);
+                }
+                h->cur ^= 1;
+            }
+            if (e == cudaSuccess) e = launch_advance(h->S, rest, E->stream);
+            if (e != cudaSuccess) return fail_cuda(e, "batch: blocked instance launch");
+            E->launches += 1;
+            E->wcur = h->cur;  // the same for every blocked instance
+        }
     }
-    E->launches += (E->n_in_place > 0 ? 4 : 3) * nsteps;
     E->step_count += nsteps;
     for (auto &I : E->inst) {
         I.done = E->server ? std::min(I.steps, I.done + nsteps) : I.done + nsteps;
         I.h->time = I.done;
-        I.h->cur = (int)(I.done & 1);
+        if (!I.blocked) I.h->cur = (int)(I.done & 1);
     }
     return LBM_OK;
 }
@@ -587,9 +748,30 @@ lbm_desc one_step(const lbm_desc &d) {
     return o;
 }
 
+// Rows of the strip segments a blocked batch instance is cut into: long
+// enough that the 3 kWaveK - 3 rows of a segment's pipeline fill and drain
+// stay a small part of it, short enough that a batch holds many more segments
+// than the device has SMs.
+constexpr int kBatchSegmentRows = 384;
+
+// Whether an instance of the lockstep batch takes the temporally blocked
+// kernel: FP32 storage, two population buffers and at least kWaveC columns.
+bool batch_blocked(const lbm_engine *E, const lbm_desc &d) {
+    return !E->server && d.storage == LBM_F32 && d.streaming == LBM_STREAM_TWO_BUFFERS &&
+           d.nx >= kWaveC;
+}
+
+// The descriptor an instance is created from: the blocked form for the
+// instances batch_blocked() picks, one step per launch for the others.
+lbm_desc instance_desc(const lbm_engine *E, const lbm_desc &d_in) {
+    lbm_desc o = one_step(d_in);
+    if (batch_blocked(E, d_in)) o.time_block = LBM_TIME_BLOCK;
+    return o;
+}
+
 // Admit one instance into the arena; LBM_ERR_NOMEM if it does not fit now.
 lbm_status admit(lbm_engine *E, const lbm_desc &d_in, int64_t id, int64_t steps) {
-    const lbm_desc d = one_step(d_in);
+    const lbm_desc d = instance_desc(E, d_in);
     uint64_t bytes = 0;
     lbm_status st = lbm_workspace_size(&d, &bytes);
     if (st != LBM_OK) return st;
@@ -613,13 +795,21 @@ lbm_status admit(lbm_engine *E, const lbm_desc &d_in, int64_t id, int64_t steps)
         return LBM_ERR_NOMEM;
     }
     lbm_handle h = nullptr;
-    st = lbm_create(&d, E->stream, E->arena.base() + off, bytes, &h);
+    int plan_blocks = 0;
+    if (d.time_block == LBM_TIME_BLOCK) {
+        const int strips = (d.nx + kWaveW - 1) / kWaveW;
+        const int segments = std::max(1, (d.ny + kBatchSegmentRows / 2) / kBatchSegmentRows);
+        plan_blocks = strips * segments;
+    }
+    st = create_solver(&d, E->stream, E->arena.base() + off, bytes, plan_blocks, &h);
     if (st != LBM_OK) {
         E->arena.release(off, bytes);
         return st;
     }
     Instance I;
     I.id = id;
+    I.blocked = h->block == kWaveK;
+    I.plan_blocks = plan_blocks;
     I.h = h;
     I.off = off;
     I.bytes = bytes;
@@ -644,7 +834,12 @@ lbm_engine::~lbm_engine() {
     if (stream) cudaStreamSynchronize(stream);
     for (auto &I : inst) lbm_destroy(I.h);
     inst.clear();
-    if (graph) cudaGraphExecDestroy(graph);
+    for (auto &g : graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (d_winst) cudaFree(d_winst);
+    if (d_regions) cudaFree(d_regions);
+    if (d_region_inst) cudaFree(d_region_inst);
+    if (d_wcounter) cudaFree(d_wcounter);
     if (d_inst) cudaFree(d_inst);
     if (d_tiles) cudaFree(d_tiles);
     if (d_bmap) cudaFree(d_bmap);
@@ -674,7 +869,7 @@ extern "C" lbm_status lbm_batch_create(const lbm_desc *descs, int32_t count, voi
     uint64_t total = 0;
     for (int32_t i = 0; i < count; ++i) {
         uint64_t b = 0;
-        const lbm_desc di = one_step(descs[i]);
+        const lbm_desc di = instance_desc(E.get(), descs[i]);
         st = lbm_workspace_size(&di, &b);
         if (st != LBM_OK) return st;
         total += (b + 255) / 256 * 256;
@@ -727,10 +922,7 @@ extern "C" lbm_status lbm_batch_set_shape(lbm_batch b, const lbm_launch_shape *s
     }
     b->shape = *shape;
     b->tables_dirty = true;
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
-    }
+    drop_graphs(b);
     return LBM_OK;
 }
 
@@ -745,6 +937,7 @@ extern "C" lbm_status lbm_batch_reset(lbm_batch b) {
         if (st != LBM_OK) return st;
         I.done = 0;
     }
+    b->wcur = 0;  // lbm_reset puts every instance's populations in buffer 0
     return LBM_OK;
 }
 
@@ -818,6 +1011,7 @@ extern "C" lbm_status lbm_batch_info(lbm_batch b, lbm_batch_stats *stats) {
     stats->device_bytes = b->arena.used();
     stats->kernel_launches = b->launches;
     stats->shape = b->shape;
+    stats->blocked_instances = b->nblocked;
     return LBM_OK;
 }
 

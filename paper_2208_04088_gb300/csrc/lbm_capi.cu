@@ -210,6 +210,13 @@ extern "C" lbm_status lbm_workspace_size(const lbm_desc *desc, uint64_t *bytes) 
 
 extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *workspace,
                                  uint64_t workspace_bytes, lbm_handle *out) {
+    return lbm::create_solver(desc, stream, workspace, workspace_bytes, 0, out);
+}
+
+namespace lbm {
+
+lbm_status create_solver(const lbm_desc *desc, void *stream, void *workspace,
+                         uint64_t workspace_bytes, int plan_blocks, lbm_handle *out) {
     set_error("");
     if (!out) {
         set_error("lbm_create: NULL output handle");
@@ -318,8 +325,9 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
             }
             h->block = 1;  // default: fall back to one step per launch
         } else {
-            e = wave_prepare(h->tab, h->L, S, &h->wave, h->stream);
-            if (e == cudaSuccess) e = wave_calibrate(h->tab, h->L, S, &h->wave, h->stream);
+            e = wave_prepare(h->tab, h->L, S, &h->wave, h->stream, plan_blocks);
+            if (e == cudaSuccess && plan_blocks <= 0)
+                e = wave_calibrate(h->tab, h->L, S, &h->wave, h->stream);
             if (e == cudaSuccess) e = launch_reset(h->storage, h->L, S, h->stream);
         }
     }
@@ -340,6 +348,8 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
     *out = h;
     return LBM_OK;
 }
+
+}  // namespace lbm
 
 extern "C" lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
     set_error("");

@@ -96,6 +96,13 @@ struct Units {
     double fx = 0.0, fy = 0.0;
 };
 
+// lbm_create with a choice of launch plan for the temporally blocked kernel:
+// plan_blocks <= 0 plans for the device's SMs and balances the plan by
+// measurement (lbm_create); plan_blocks > 0 plans that many blocks from the
+// cost model alone (the regions a batch schedules itself).
+lbm_status create_solver(const lbm_desc *desc, void *stream, void *workspace,
+                         uint64_t workspace_bytes, int plan_blocks, lbm_handle *out);
+
 // Thread-local error text for lbm_last_error().
 void set_error(const std::string &msg);
 
@@ -181,10 +188,11 @@ bool complex_boundary_node(const Tables &t, size_t g);
 // The blocks of one launch for a device with `sms` SMs: (X0, Y0, rows, has_boundary).
 std::vector<int4> wave_plan(const Tables &t, int sms);
 // Builds the node words from the class and boundary tables, the TMA
-// descriptors and the block table; S.nw (8 bytes per node of the pitched
-// plane) and S.wave_tab must be allocated.
+// descriptors and the block table (planned for the device's SMs, or for
+// plan_blocks blocks if it is positive); S.nw (8 bytes per node of the
+// pitched plane) and S.wave_tab must be allocated.
 cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, WaveMaps *m,
-                         cudaStream_t s);
+                         cudaStream_t s, int plan_blocks = 0);
 // Balances the blocks of a launch by measurement: blocked launches from
 // buffer 0 record each block's SM cycles, the modelled cost of every row is
 // scaled by its block's measured/modelled ratio and the strips are cut again
@@ -197,6 +205,28 @@ cudaError_t wave_calibrate(const Tables &t, const Lattice &L, const DevState &S,
 // kWaveK steps from buffer `cur` into buffer cur ^ 1; the first of them is
 // step `toff` after *S.time.  With `cycles`, block b stores its SM cycles in
 // cycles[b].
+// Device record of one instance of a batch stepped by the blocked kernel:
+// its tensor maps (input populations from buffer 0 or 1, node words,
+// displacement records), buffers, tables and lattice parameters.
+struct WaveInst {
+    CUtensorMap tf[2];
+    CUtensorMap tnw, tu;
+    float *f[2];
+    float4 *uc;
+    const BLink *blinks;
+    const BCDev *bcs;
+    const int64_t *time;
+    uint32_t *status;
+    Lattice L;
+};
+// One blocked launch over the regions of many instances: kWaveK steps of
+// every region; region r = (X0, Y0, rows, has_boundary) of instance
+// region_inst[r], read from buffer `cur` into cur ^ 1, its first step `toff`
+// after the instance's *time.  The blocks take regions in table order from
+// *counter, which must be 0 at the launch.
+cudaError_t launch_wave_batch(const WaveInst *insts, const int4 *regions, const int32_t *region_inst,
+                              int nregions, int32_t *counter, int cur, int toff, int sms,
+                              cudaStream_t s);
 cudaError_t launch_wave(const Lattice &L, const DevState &S, const WaveMaps &m, int cur, int toff,
                         cudaStream_t s, long long *cycles = nullptr);
 

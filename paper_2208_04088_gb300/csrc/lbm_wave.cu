@@ -85,6 +85,10 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
@@ -250,22 +254,23 @@ __device__ __forceinline__ void store_pair(float *out, int64_t stride, const F2 
     }
 }
 
-// One launch: kWaveK steps of every material node.  Block b handles the
-// region tab[b] = (X0, Y0, rows, has_boundary): core columns [X0, X0 +
-// kWaveW), core rows [Y0, Y0 + rows); has_boundary says whether a boundary
-// node lies in the region or its halo.  Each warp computes one level of one
-// 64-column half of the ring, two columns per lane, c and c + 32 (ring column c
-// is lattice column X0 - kWaveK + c): their collisions run as one stream of
-// paired (f32x2) operations, and every shared-memory access of a warp stays on
-// consecutive words.
-__global__ void __launch_bounds__(kThreads, 1)
-    k_wave(const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tnw,
-           const __grid_constant__ CUtensorMap tu, float *__restrict__ dst,
-           float4 *__restrict__ uc, const BLink *__restrict__ blinks,
-           const BCDev *__restrict__ bcs, Lattice L, const int64_t *__restrict__ time, int toff,
-           const int4 *__restrict__ tab, uint32_t *__restrict__ status,
-           long long *__restrict__ cycles) {
-    extern __shared__ __align__(1024) unsigned char sm[];
+// One region of a blocked launch: kWaveK steps of every material node of the
+// region (X0, Y0, rows, has_boundary): core columns [X0, X0 + kWaveW), core
+// rows [Y0, Y0 + rows); has_boundary says whether a boundary node lies in the
+// region or its halo.  Each warp computes one level of one 64-column half of
+// the ring, two columns per lane, c and c + 32 (ring column c is lattice
+// column X0 - kWaveK + c): their collisions run as one stream of paired
+// (f32x2) operations, and every shared-memory access of a warp stays on
+// consecutive words.  tf, tnw and tu are the tensor maps of the input
+// populations, the node words and the displacement records; `sm` is the
+// block's dynamic shared memory.  The block's earlier use of `sm` must be over
+// (a barrier) before the call.  *cycle_out, if given, receives the region's SM
+// cycles.
+__device__ __forceinline__ void wave_region(
+    const CUtensorMap *tf, const CUtensorMap *tnw, const CUtensorMap *tu, float *__restrict__ dst,
+    float4 *__restrict__ uc, const BLink *__restrict__ blinks, const BCDev *__restrict__ bcs,
+    const Lattice &L, const int64_t *__restrict__ time, int toff, const int4 region,
+    uint32_t *__restrict__ status, long long *cycle_out, unsigned char *sm) {
     const long long t_start = clock64();
     float *in = reinterpret_cast<float *>(sm + kOffIn);
     float *lev = reinterpret_cast<float *>(sm + kOffLev);
@@ -284,7 +289,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int lv = (warp >> 1) + 1;  // time level of this thread (warp-uniform)
     const int half = (warp ^ (warp >> 2)) & 1;
     const int c = (half << 6) | lane;  // the lane's columns c, c + 32
-    const int4 region = tab[blockIdx.x];
     const int X0 = region.x, Y0 = region.y, Hs = region.z;
     const int xin = X0 - kK;     // lattice column of ring column 0
     const int y_in0 = Y0 - kK;   // lattice row of input row index 0
@@ -298,9 +302,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t bar = bar0 + 8u * (uint32_t)(j & (kNI - 1));
         const int y = y_in0 + j;
         mbar_expect_tx(bar, kTxBytes);
-        tma_load_3d(smem_addr(in + (size_t)(j & (kNI - 1)) * kRowF), &tf, xin, y, 0, bar);
-        tma_load_2d(smem_addr(sm + kOffNw + (size_t)(j % kNU) * kNwRowBytes), &tnw, xin, y, bar);
-        tma_load_3d(smem_addr(sm + kOffU + (size_t)(j % kNU) * kURowBytes), &tu, 0, X0, y, bar);
+        tma_load_3d(smem_addr(in + (size_t)(j & (kNI - 1)) * kRowF), tf, xin, y, 0, bar);
+        tma_load_2d(smem_addr(sm + kOffNw + (size_t)(j % kNU) * kNwRowBytes), tnw, xin, y, bar);
+        tma_load_3d(smem_addr(sm + kOffU + (size_t)(j % kNU) * kURowBytes), tu, 0, X0, y, bar);
     };
     auto wait_row = [&](int j, int64_t limit) {
         return mbar_wait(bar0 + 8u * (uint32_t)(j & (kNI - 1)), (uint32_t)((j / kNI) & 1), limit);
@@ -327,8 +331,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
 
-    const bool live_a = c >= lv && c < kC - lv;
-    const bool live_b = c + 32 >= lv && c + 32 < kC - lv;
+    // a lane's node counts only inside the level's live columns and inside the
+    // lattice: every global store of the block then goes to a node of its
+    // region, whatever its shared-memory rows hold (after a wait has run out
+    // the sweep reads rows that never landed)
+    const bool live_a = c >= lv && c < kC - lv && (unsigned)(xin + c) < (unsigned)L.nx;
+    const bool live_b =
+        c + 32 >= lv && c + 32 < kC - lv && (unsigned)(xin + c + 32) < (unsigned)L.nx;
     const int lo = Y0 - (kK - lv), hi = Y0 + Hs - 1 + (kK - lv);
     const float *prev_base = lv == 1 ? in : lev + (size_t)(lv - 2) * 4 * kRowF;
     const int pmask = lv == 1 ? kNI - 1 : 3;
@@ -540,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     else
         sweep(std::false_type{});
     if (!isfinite(nonfinite)) flag_nonfinite(status, nonfinite, 0.0f, 0.0f);
-    if (cycles && tid == 0) cycles[blockIdx.x] = clock64() - t_start;
+    if (cycle_out && tid == 0) *cycle_out = clock64() - t_start;
     if (tid == 0 && !ok) {
         // a copy did not land within the limit (the rest of the sweep ran on
         // stale rows; thread 0 issued no copy after that): flag it, then wait
@@ -550,6 +559,49 @@ __global__ void __launch_bounds__(kThreads, 1)
         atomicOr(status, 2u);
         for (int j = last_waited + 1; j <= j_issued; ++j) wait_row(j, kDefaultWaitNs);
     }
+    // every copy has been waited for: the barriers are released, so that the
+    // block can initialise them again for its next region
+    if (tid == 0)
+        for (int q = 0; q < kNI; ++q) mbar_inval(bar0 + 8u * q);
+}
+
+// One launch over the regions of many lattices (a batch): a persistent grid
+// whose blocks take regions from an atomic counter; each region's instance
+// record supplies its tensor maps and buffers, and its lattice parameters are
+// staged in shared memory.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_wave_batch(const WaveInst *__restrict__ insts, const int4 *__restrict__ regions,
+                 const int32_t *__restrict__ region_inst, int nregions,
+                 int32_t *__restrict__ counter, int cur, int toff) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ int s_r;
+    __shared__ __align__(16) Lattice s_L;
+    for (;;) {
+        if (threadIdx.x == 0) s_r = atomicAdd(counter, 1);
+        __syncthreads();
+        const int r = s_r;
+        if (r >= nregions) break;
+        const WaveInst *I = insts + region_inst[r];
+        if (threadIdx.x == 0) s_L = I->L;
+        __syncthreads();
+        wave_region(&I->tf[cur], &I->tnw, &I->tu, I->f[cur ^ 1], I->uc, I->blinks, I->bcs, s_L,
+                    I->time, toff, regions[r], I->status, nullptr, sm);
+        __syncthreads();  // the next region reuses the shared memory
+    }
+}
+
+// One launch: kWaveK steps of every material node of one lattice; block b
+// handles the region tab[b].
+__global__ void __launch_bounds__(kThreads, 1)
+    k_wave(const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tnw,
+           const __grid_constant__ CUtensorMap tu, float *__restrict__ dst,
+           float4 *__restrict__ uc, const BLink *__restrict__ blinks,
+           const BCDev *__restrict__ bcs, Lattice L, const int64_t *__restrict__ time, int toff,
+           const int4 *__restrict__ tab, uint32_t *__restrict__ status,
+           long long *__restrict__ cycles) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    wave_region(&tf, &tnw, &tu, dst, uc, blinks, bcs, L, time, toff, tab[blockIdx.x], status,
+                cycles ? cycles + blockIdx.x : nullptr, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -682,7 +734,10 @@ __global__ void __launch_bounds__(kGradThreads, 1)
 
     // collision columns shrink by two per level, density columns by one less
     const int m0 = density_warp ? 2 * lv - 1 : 2 * lv;
-    const bool live_a = c >= m0 && c < kC - m0, live_b = c + 32 >= m0 && c + 32 < kC - m0;
+    // inside the live columns and the lattice (see k_wave)
+    const bool live_a = c >= m0 && c < kC - m0 && (unsigned)(xin + c) < (unsigned)L.nx;
+    const bool live_b =
+        c + 32 >= m0 && c + 32 < kC - m0 && (unsigned)(xin + c + 32) < (unsigned)L.nx;
     const bool core_a = c >= 2 * kGradK && c < kC - 2 * kGradK;
     const bool core_b = c + 32 >= 2 * kGradK && c + 32 < kC - 2 * kGradK;
     const int lo = Y0 - 2 * (kGradK - lv), hi = Y0 + Hs - 1 + 2 * (kGradK - lv);
@@ -1028,7 +1083,7 @@ bool wave_supported(const Lattice &L) {
 }
 
 cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, WaveMaps *m,
-                         cudaStream_t s) {
+                         cudaStream_t s, int plan_blocks) {
     const int64_t n = L.plane;
     k_nw_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S.cls, S.nw, n);
     if (L.nb > 0)
@@ -1056,12 +1111,24 @@ cudaError_t wave_prepare(const Tables &t, const Lattice &L, const DevState &S, W
                : cudaFuncSetAttribute(k_wave, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kSmem);
     if (e != cudaSuccess) return e;
-    const std::vector<int4> plan = wave_plan(t, device_sms());
+    const std::vector<int4> plan = wave_plan(t, plan_blocks > 0 ? plan_blocks : device_sms());
     m->nblocks = (int)plan.size();
     if (plan.empty() || plan.size() > wave_table_entries(t.nx, t.ny)) return cudaErrorInvalidValue;
     // pageable source: the copy is staged before the call returns
     return cudaMemcpyAsync(S.wave_tab, plan.data(), plan.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t launch_wave_batch(const WaveInst *insts, const int4 *regions, const int32_t *region_inst,
+                              int nregions, int32_t *counter, int cur, int toff, int sms,
+                              cudaStream_t s) {
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_wave_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (attr != cudaSuccess) return attr;
+    if (nregions <= 0) return cudaSuccess;
+    k_wave_batch<<<(unsigned)std::min(sms, nregions), kThreads, kSmem, s>>>(
+        insts, regions, region_inst, nregions, counter, cur, toff);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_wave(const Lattice &L, const DevState &S, const WaveMaps &m, int cur, int toff,

@@ -44,6 +44,30 @@ def test_batch_matches_instances_alone(storage):
     b.close()
 
 
+def test_blocked_batch_across_buffer_parities():
+    """Instances of at least 128 columns in FP32 take the temporally blocked
+    batch kernel.  Calls of 37, 16 and 27 steps replay chunks that start in
+    either population buffer (a chunk after an odd remainder) and finish with
+    the instances' own blocked and one-step launches; every instance stays
+    bit-identical to itself stepped alone, at every call boundary."""
+    from paper_2208_04088_gb300 import _native as N
+    wls = [W.hole_plate(300, 140, 23.5, 0), W.edge_crack(256, 64, 0, ny=96),
+           W.square_plate(128, 0), W.hole_plate(128, 64, 8.0, 0), W.hole_plate(96, 64, 9.0, 0)]
+    b = N.Batch([N.desc_from_workload(w) for w in wls])
+    assert b.info()["blocked_instances"] == 4
+    t = 0
+    for n in (37, 16, 27):
+        b.step(n)
+        t += n
+        for k, w in enumerate(wls):
+            assert _same(b.fields_host(k), _alone(w, t)), (t, w.name)
+    b.reset()
+    b.step(16)
+    for k, w in enumerate(wls):
+        assert _same(b.fields_host(k), _alone(w, 16)), ("after reset", w.name)
+    b.close()
+
+
 def test_every_launch_shape_and_the_tuner_give_identical_fields():
     from paper_2208_04088_gb300 import _native as N
     wls = _mix()
