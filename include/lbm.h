@@ -366,11 +366,16 @@ lbm_status lbm_batch_destroy(lbm_batch b);
 
 /* Continuous-batching server.  Requests (a descriptor and a step count) are
  * queued by lbm_server_submit; each lbm_server_tick admits queued requests in
- * arrival order while their workspaces fit in the device budget, advances
- * every admitted instance together by up to max_steps (never past the nearest
- * completion), and retires the instances that reached their step count:
- * their fields are copied to host memory and their device memory returns to
- * the budget.  Requests that arrive while others run join at the next tick. */
+ * arrival order while their workspaces fit in the device budget, queues the
+ * steps that advance every admitted instance together by up to max_steps
+ * (never past the nearest completion), and starts retiring the instances that
+ * reach their step count: their fields are copied to pinned host memory
+ * behind those steps, and once a later tick finds the copy complete the
+ * result is delivered and the device memory returns to the budget.  A tick
+ * does not wait for the device except to keep at most two ticks queued on it
+ * (and, when no instance is left to step, for the results in flight), so the
+ * host admits and classifies new requests while the device runs earlier
+ * ones.  Requests that arrive while others run join at the next tick. */
 typedef struct {
     int32_t active, queued;   /* after the tick */
     int32_t admitted, finished; /* during the tick */
@@ -382,7 +387,14 @@ typedef struct {
 
 lbm_status lbm_server_create(uint64_t hbm_budget_bytes, int32_t storage, void *stream,
                              lbm_server *out);
-/* Queue a request; the descriptor's host arrays are copied. */
+/* Queue a request; the descriptor's host arrays are copied.  Validation and
+ * classification of the tables then run on a host worker thread while
+ * earlier requests run, so the tick that admits the request finds them ready.
+ * Returns LBM_ERR_NOMEM at once if one population buffer and the displacement
+ * records of the lattice alone exceed the budget; any other problem with the
+ * request (bad tables, lambda != mu, another storage, a workspace larger than
+ * the budget) makes it fail at admission: lbm_server_result then returns
+ * LBM_ERR_ARG with the reason. */
 lbm_status lbm_server_submit(lbm_server s, const lbm_desc *desc, int64_t nsteps, int64_t *id);
 lbm_status lbm_server_tick(lbm_server s, int32_t max_steps, lbm_server_stats *stats);
 /* *state: 0 queued, 1 running, 2 done (fields copied to the host arrays, any

@@ -17,8 +17,10 @@
 // all of them, longest first, each block taking the next region from a
 // counter.  Its per-node arithmetic is that of the one-step kernels too.
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cstring>
+#include <future>
 #include <map>
 #include <memory>
 #include <string>
@@ -298,6 +300,16 @@ struct Instance {
     int64_t nodes = 0;
 };
 
+// A server request's tables, validated and classified on a worker thread
+// from the moment it is submitted.
+struct Prepared {
+    lbm_status st = LBM_OK;
+    std::string err;
+    lbm_desc d;
+    Tables t;
+    Units u;
+};
+
 struct Request {
     int64_t id;
     std::unique_ptr<DescCopy> desc;
@@ -306,6 +318,17 @@ struct Request {
     bool unstable = false;      // done, but a non-finite moment was produced
     std::vector<float> result;  // u(2N), v(2N), sigma(3N) when done
     std::string error;
+    std::shared_ptr<Prepared> prep;
+    std::future<void> ready;    // the worker that fills prep (destroyed first)
+};
+
+// A finished server instance whose fields are on their way to the host: its
+// workspace stays reserved until the copy has completed.
+struct Retiring {
+    Instance I;
+    cudaEvent_t done = nullptr;
+    float *buf = nullptr;  // pinned: u(2N), v(2N), sigma(3N), then the status word
+    size_t cap = 0;        // floats
 };
 
 }  // namespace
@@ -341,6 +364,17 @@ struct lbm_engine {
     int32_t *d_region_inst = nullptr, *d_wcounter = nullptr;
     int cap_winst = 0, cap_regions = 0, nregions = 0, nblocked = 0;
     int wcur = 0;  // the buffer that holds their populations
+    // pinned staging of the table uploads (reused once the last upload is done)
+    char *h_stage = nullptr;
+    size_t h_stage_cap = 0;
+    cudaEvent_t stage_done = nullptr;
+    bool stage_pending = false;
+    // server: finishing instances, pinned result buffers, queued ticks
+    std::vector<Retiring> retiring;
+    std::vector<std::pair<float *, size_t>> pinned;  // free result buffers (floats)
+    std::vector<cudaEvent_t> spare_events;
+    cudaEvent_t tick_done[2] = {nullptr, nullptr};
+    int64_t ticks = 0;
     int n_in_place = 0;           // instances with in-place streaming
     int64_t launches = 0;
     int64_t step_count = 0;  // steps run by the engine
@@ -393,6 +427,9 @@ lbm_status ensure_capacity(lbm_engine *E, int ninst, int64_t ntiles, int64_t nbn
 // swept), longest first, so that the blocks that take them from the counter
 // end close together.
 lbm_status rebuild_wave_tables(lbm_engine *E) {
+    bool any = E->nblocked > 0;
+    for (const Instance &I : E->inst) any = any || I.blocked;
+    if (!any) return LBM_OK;
     std::vector<WaveInst> wi;
     std::vector<std::pair<int, int4>> reg;  // (record, region)
     for (size_t i = 0; i < E->inst.size(); ++i) {
@@ -508,21 +545,42 @@ lbm_status rebuild_tables(lbm_engine *E) {
     c.ntiles = (int32_t)tiles.size();
     c.nbnodes = (int32_t)bmap.size();
     c.ninst = (int32_t)hi.size();
+    // the uploads go through pinned staging, queued on the stream behind the
+    // steps already queued (which still read the old tables); the staging is
+    // written again only once the previous upload has been done
+    const size_t b_inst = sizeof(InstDev) * hi.size(), b_tiles = sizeof(int2) * tiles.size();
+    const size_t b_bmap = sizeof(int2) * bmap.size(), need = b_inst + b_tiles + b_bmap + sizeof c;
     cudaError_t e = cudaSuccess;
-    if (!hi.empty())
-        e = cudaMemcpyAsync(E->d_inst, hi.data(), sizeof(InstDev) * hi.size(),
-                            cudaMemcpyHostToDevice, E->stream);
-    if (e == cudaSuccess && !tiles.empty())
-        e = cudaMemcpyAsync(E->d_tiles, tiles.data(), sizeof(int2) * tiles.size(),
-                            cudaMemcpyHostToDevice, E->stream);
-    if (e == cudaSuccess && !bmap.empty())
-        e = cudaMemcpyAsync(E->d_bmap, bmap.data(), sizeof(int2) * bmap.size(),
-                            cudaMemcpyHostToDevice, E->stream);
+    if (E->stage_pending) {
+        e = cudaEventSynchronize(E->stage_done);
+        E->stage_pending = false;
+    }
+    if (e == cudaSuccess && need > E->h_stage_cap) {
+        if (E->h_stage) cudaFreeHost(E->h_stage);
+        E->h_stage = nullptr;
+        E->h_stage_cap = std::max(need, 2 * E->h_stage_cap);
+        e = cudaMallocHost(&E->h_stage, E->h_stage_cap);
+    }
+    if (e == cudaSuccess && !E->stage_done)
+        e = cudaEventCreateWithFlags(&E->stage_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail_cuda(e, "batch: table staging");
+    char *p = E->h_stage;
+    std::memcpy(p, hi.data(), b_inst);
+    std::memcpy(p + b_inst, tiles.data(), b_tiles);
+    std::memcpy(p + b_inst + b_tiles, bmap.data(), b_bmap);
+    std::memcpy(p + b_inst + b_tiles + b_bmap, &c, sizeof c);
+    if (b_inst) e = cudaMemcpyAsync(E->d_inst, p, b_inst, cudaMemcpyHostToDevice, E->stream);
+    if (e == cudaSuccess && b_tiles)
+        e = cudaMemcpyAsync(E->d_tiles, p + b_inst, b_tiles, cudaMemcpyHostToDevice, E->stream);
+    if (e == cudaSuccess && b_bmap)
+        e = cudaMemcpyAsync(E->d_bmap, p + b_inst + b_tiles, b_bmap, cudaMemcpyHostToDevice,
+                            E->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(E->d_counts, &c, sizeof c, cudaMemcpyHostToDevice, E->stream);
-    // the host vectors die here: wait for the copies
-    if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+        e = cudaMemcpyAsync(E->d_counts, p + b_inst + b_tiles + b_bmap, sizeof c,
+                            cudaMemcpyHostToDevice, E->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(E->stage_done, E->stream);
     if (e != cudaSuccess) return fail_cuda(e, "batch: table upload");
+    E->stage_pending = true;
     E->tables_dirty = false;
     return LBM_OK;
 }
@@ -769,26 +827,29 @@ lbm_desc instance_desc(const lbm_engine *E, const lbm_desc &d_in) {
     return o;
 }
 
-// Admit one instance into the arena; LBM_ERR_NOMEM if it does not fit now.
-lbm_status admit(lbm_engine *E, const lbm_desc &d_in, int64_t id, int64_t steps) {
-    const lbm_desc d = instance_desc(E, d_in);
-    uint64_t bytes = 0;
-    lbm_status st = lbm_workspace_size(&d, &bytes);
-    if (st != LBM_OK) return st;
-    {
-        // the batched kernels implement the lambda = mu path (no density pass)
-        Units u;
-        if (make_units(d, &u) != LBM_OK) return LBM_ERR_ARG;
-        if (u.lam != u.mu) {
-            set_error("batch/server: instances must have lambda = mu (the density pass of the "
-                      "lambda != mu source is single-solver only)");
-            return LBM_ERR_ARG;
-        }
-        if (d.storage != E->storage) {
-            set_error("batch/server: every instance must use the engine's storage");
-            return LBM_ERR_ARG;
-        }
+// Admit one instance, from tables already validated and classified (d is the
+// instance's descriptor, instance_desc()), into the arena; LBM_ERR_NOMEM if it
+// does not fit now, and the tables are then left as they were.  Server
+// instances are created deferred: their uploads are queued behind the steps
+// already queued, with no wait on the host.
+lbm_status admit_prepared(lbm_engine *E, const lbm_desc &d, Tables &t, const Units &u, int64_t id,
+                          int64_t steps) {
+    // the batched kernels implement the lambda = mu path (no density pass)
+    if (u.lam != u.mu) {
+        set_error("batch/server: instances must have lambda = mu (the density pass of the "
+                  "lambda != mu source is single-solver only)");
+        return LBM_ERR_ARG;
     }
+    if (d.storage != E->storage) {
+        set_error("batch/server: every instance must use the engine's storage");
+        return LBM_ERR_ARG;
+    }
+    const uint64_t bytes = workspace_bytes_for(d, t, u);
+    if (bytes == 0) {
+        set_error("batch/server: the instance's stepping form is not supported");
+        return LBM_ERR_ARG;
+    }
+    lbm_status st = LBM_OK;
     const uint64_t off = E->arena.alloc(bytes);
     if (off == UINT64_MAX) {
         set_error("batch/server: not enough room in the device budget");
@@ -801,7 +862,10 @@ lbm_status admit(lbm_engine *E, const lbm_desc &d_in, int64_t id, int64_t steps)
         const int segments = std::max(1, (d.ny + kBatchSegmentRows / 2) / kBatchSegmentRows);
         plan_blocks = strips * segments;
     }
-    st = create_solver(&d, E->stream, E->arena.base() + off, bytes, plan_blocks, &h);
+    CreateOptions opt;
+    opt.plan_blocks = plan_blocks;
+    opt.deferred = E->server;
+    st = create_prepared(&d, std::move(t), u, E->stream, E->arena.base() + off, bytes, opt, &h);
     if (st != LBM_OK) {
         E->arena.release(off, bytes);
         return st;
@@ -820,12 +884,117 @@ lbm_status admit(lbm_engine *E, const lbm_desc &d_in, int64_t id, int64_t steps)
     return LBM_OK;
 }
 
-void retire(lbm_engine *E, size_t k) {
-    Instance &I = E->inst[k];
-    lbm_destroy(I.h);
-    E->arena.release(I.off, I.bytes);
+// Admit one instance from its descriptor (the lockstep batch).
+lbm_status admit(lbm_engine *E, const lbm_desc &d_in, int64_t id, int64_t steps) {
+    const lbm_desc d = instance_desc(E, d_in);
+    Tables t;
+    Units u;
+    lbm_status st = prepare(&d, &t, &u);
+    if (st != LBM_OK) return st;
+    return admit_prepared(E, d, t, u, id, steps);
+}
+
+// A pinned result buffer of at least n floats from the pool.
+float *take_pinned(lbm_engine *E, size_t n, size_t *cap) {
+    size_t best = SIZE_MAX;
+    for (size_t k = 0; k < E->pinned.size(); ++k)
+        if (E->pinned[k].second >= n && (best == SIZE_MAX || E->pinned[k].second < E->pinned[best].second))
+            best = k;
+    if (best != SIZE_MAX) {
+        float *p = E->pinned[best].first;
+        *cap = E->pinned[best].second;
+        E->pinned.erase(E->pinned.begin() + (long)best);
+        return p;
+    }
+    float *p = nullptr;
+    if (cudaMallocHost(&p, n * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    *cap = n;
+    return p;
+}
+
+cudaEvent_t take_event(lbm_engine *E) {
+    if (!E->spare_events.empty()) {
+        cudaEvent_t ev = E->spare_events.back();
+        E->spare_events.pop_back();
+        return ev;
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return ev;
+}
+
+// Server: instance k has reached its step count.  Its fields and status word
+// are queued for the host (fields kernels into the workspace's staging, then
+// copies into a pinned buffer); it leaves the tables now and its workspace is
+// released once the copies have completed (finish_retired).
+lbm_status start_retire(lbm_engine *E, size_t k) {
+    Retiring R;
+    R.I = E->inst[k];
+    lbm_solver *h = R.I.h;
+    const size_t N = (size_t)h->L.nx * h->L.ny;
+    R.buf = take_pinned(E, 7 * N + 1, &R.cap);
+    R.done = take_event(E);
+    if (!R.buf || !R.done) {
+        set_error("server: pinned result buffer or event allocation failed");
+        return LBM_ERR_NOMEM;
+    }
+    cudaError_t e = launch_fields(h->storage, h->L, h->S, h->cur, nullptr, nullptr, nullptr, E->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(R.buf, h->S.stage, 7 * N * sizeof(float), cudaMemcpyDeviceToHost,
+                            E->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(R.buf + 7 * N, h->S.status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                            E->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(R.done, E->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "server: retire");
+    E->launches += kernels_per_fields(h->L);
+    E->retiring.push_back(R);
     E->inst.erase(E->inst.begin() + (long)k);
     E->tables_dirty = true;
+    return LBM_OK;
+}
+
+// Server: the retiring instances whose copies have completed deliver their
+// results and give back their workspace; returns how many did.
+int finish_retired(lbm_engine *E) {
+    int n = 0;
+    for (size_t k = 0; k < E->retiring.size();) {
+        Retiring &R = E->retiring[k];
+        const cudaError_t q = cudaEventQuery(R.done);
+        if (q == cudaErrorNotReady) {
+            cudaGetLastError();
+            ++k;
+            continue;
+        }
+        Request &r = E->requests.at(R.I.id);
+        lbm_solver *h = R.I.h;
+        const size_t N = (size_t)h->L.nx * h->L.ny;
+        if (q == cudaSuccess) {
+            uint32_t status = 0;
+            std::memcpy(&status, R.buf + 7 * N, sizeof status);
+            r.result.assign(R.buf, R.buf + 7 * N);
+            r.unstable = (status & 1u) != 0;
+            r.state = (status & 2u) ? 3 : 2;
+            if (status & 2u) r.error = "a bounded wait for a tile copy expired on the device";
+        } else {
+            r.state = 3;
+            r.error = std::string("server: ") + cudaGetErrorString(q);
+        }
+        r.desc.reset();
+        destroy_deferred(h);
+        E->arena.release(R.I.off, R.I.bytes);
+        E->pinned.emplace_back(R.buf, R.cap);
+        E->spare_events.push_back(R.done);
+        E->retiring.erase(E->retiring.begin() + (long)k);
+        ++n;
+    }
+    return n;
 }
 
 }  // namespace
@@ -834,6 +1003,19 @@ lbm_engine::~lbm_engine() {
     if (stream) cudaStreamSynchronize(stream);
     for (auto &I : inst) lbm_destroy(I.h);
     inst.clear();
+    for (auto &R : retiring) {
+        destroy_deferred(R.I.h);
+        if (R.buf) cudaFreeHost(R.buf);
+        if (R.done) cudaEventDestroy(R.done);
+    }
+    retiring.clear();
+    for (auto &p : pinned) cudaFreeHost(p.first);
+    for (auto ev : spare_events) cudaEventDestroy(ev);
+    for (auto ev : tick_done)
+        if (ev) cudaEventDestroy(ev);
+    if (stage_done) cudaEventDestroy(stage_done);
+    if (h_stage) cudaFreeHost(h_stage);
+    requests.clear();  // waits for the workers of requests never admitted
     for (auto &g : graph)
         if (g) cudaGraphExecDestroy(g);
     if (d_winst) cudaFree(d_winst);
@@ -1047,12 +1229,11 @@ extern "C" lbm_status lbm_server_submit(lbm_server s, const lbm_desc *desc, int6
         set_error("lbm_server_submit: bad arguments");
         return LBM_ERR_ARG;
     }
-    // validate now, so a bad request fails at submission
-    uint64_t bytes = 0;
-    const lbm_desc d1 = one_step(*desc);
-    lbm_status st = lbm_workspace_size(&d1, &bytes);
-    if (st != LBM_OK) return st;
-    if (bytes > s->arena.capacity()) {
+    // a request that can never fit is refused now: one population buffer and
+    // the displacement records alone exceed the budget
+    const uint64_t esz = desc->storage == LBM_F32 ? 4 : 2;
+    const uint64_t nodes = (uint64_t)std::max(desc->nx, 0) * (uint64_t)std::max(desc->ny, 0);
+    if (nodes * (9 * esz + 16) > s->arena.capacity()) {
         set_error("lbm_server_submit: the request alone exceeds the device budget");
         return LBM_ERR_NOMEM;
     }
@@ -1060,6 +1241,16 @@ extern "C" lbm_status lbm_server_submit(lbm_server s, const lbm_desc *desc, int6
     r.id = s->next_id++;
     r.desc.reset(new DescCopy(*desc));
     r.steps = nsteps;
+    // validation and classification run on a worker thread from now on; a
+    // request that fails them fails at admission
+    auto prep = std::make_shared<Prepared>();
+    const DescCopy *dc = r.desc.get();
+    r.prep = prep;
+    r.ready = std::async(std::launch::async, [prep, dc]() {
+        prep->d = one_step(dc->d);
+        prep->st = prepare(&prep->d, &prep->t, &prep->u);
+        if (prep->st != LBM_OK) prep->err = lbm_last_error();
+    });
     *id = r.id;
     s->queue.push_back(r.id);
     s->requests.emplace(r.id, std::move(r));
@@ -1072,51 +1263,74 @@ extern "C" lbm_status lbm_server_tick(lbm_server s, int32_t max_steps, lbm_serve
         set_error("lbm_server_tick: bad arguments");
         return LBM_ERR_ARG;
     }
-    int32_t admitted = 0, finished = 0;
-    // admit queued requests in arrival order while they fit
+    int32_t admitted = 0;
+    // results whose copies have landed
+    int32_t finished = finish_retired(s);
+    // admit queued requests in arrival order while they are classified and fit
     while (!s->queue.empty()) {
         Request &r = s->requests.at(s->queue.front());
-        lbm_status st = admit(s, r.desc->d, r.id, r.steps);
-        if (st == LBM_ERR_NOMEM) break;
+        if (r.ready.valid()) {
+            // with instances running, an unclassified request waits for a
+            // later tick; with none, there is nothing else to do than wait
+            if (!s->inst.empty() &&
+                r.ready.wait_for(std::chrono::seconds(0)) != std::future_status::ready)
+                break;
+            r.ready.get();
+        }
+        Prepared &P = *r.prep;
+        lbm_status st = P.st;
+        std::string err = P.err;
+        if (st == LBM_OK && workspace_bytes_for(P.d, P.t, P.u) > s->arena.capacity()) {
+            st = LBM_ERR_NOMEM;
+            err = "the request alone exceeds the device budget";
+        } else if (st == LBM_OK) {
+            st = admit_prepared(s, P.d, P.t, P.u, r.id, r.steps);
+            if (st == LBM_ERR_NOMEM) break;  // room frees up as requests finish
+            if (st != LBM_OK) err = lbm_last_error();
+        }
         s->queue.erase(s->queue.begin());
+        r.prep.reset();
         if (st != LBM_OK) {
             r.state = 3;
-            r.error = lbm_last_error();
+            r.error = err;
             continue;
         }
         r.state = 1;
         ++admitted;
     }
-    // advance: at most max_steps, and no further than the nearest completion
+    // advance: at most max_steps, and no further than the nearest completion.
+    // At most two ticks are queued on the device: the host prepares the next
+    // while the device runs the previous one.
     int64_t adv = max_steps;
     for (auto &I : s->inst) adv = std::min(adv, I.steps - I.done);
     if (!s->inst.empty()) {
         if (adv < 1) adv = 1;
+        cudaEvent_t &slot = s->tick_done[s->ticks & 1];
+        if (!slot && cudaEventCreateWithFlags(&slot, cudaEventDisableTiming) != cudaSuccess)
+            return fail_cuda(cudaGetLastError(), "server: tick event");
+        if (s->ticks >= 2) {
+            const cudaError_t e = cudaEventSynchronize(slot);
+            if (e != cudaSuccess) return fail_cuda(e, "server: tick wait");
+        }
         lbm_status st = engine_steps(s, adv);
         if (st != LBM_OK) return st;
-    }
-    // retire finished instances: fields to host, free their memory
-    for (size_t k = 0; k < s->inst.size();) {
-        Instance &I = s->inst[k];
-        if (I.done < I.steps) {
-            ++k;
-            continue;
+        // instances that reach their step count in this tick start retiring
+        for (size_t k = 0; k < s->inst.size();) {
+            if (s->inst[k].done < s->inst[k].steps) {
+                ++k;
+                continue;
+            }
+            st = start_retire(s, k);
+            if (st != LBM_OK) return st;
         }
-        Request &r = s->requests.at(I.id);
-        const int64_t N = (int64_t)I.h->L.nx * I.h->L.ny;
-        r.result.assign(7 * N, 0.0f);
-        lbm_status st = lbm_get_fields(I.h, r.result.data(), r.result.data() + 2 * N,
-                                       r.result.data() + 4 * N, 0);
-        if (st == LBM_OK) st = lbm_sync(I.h);
-        if (st == LBM_ERR_UNSTABLE) {
-            r.unstable = true;
-            st = LBM_OK;
-        }
-        r.state = st == LBM_OK ? 2 : 3;
-        if (st != LBM_OK) r.error = lbm_last_error();
-        r.desc.reset();
-        retire(s, k);
-        ++finished;
+        const cudaError_t e = cudaEventRecord(slot, s->stream);
+        if (e != cudaSuccess) return fail_cuda(e, "server: tick event");
+        ++s->ticks;
+    } else if (!s->retiring.empty()) {
+        // nothing to step: wait for the results in flight instead of spinning
+        const cudaError_t e = cudaEventSynchronize(s->retiring.front().done);
+        if (e != cudaSuccess) return fail_cuda(e, "server: result wait");
+        finished += finish_retired(s);
     }
     if (stats) {
         std::memset(stats, 0, sizeof *stats);
@@ -1124,7 +1338,7 @@ extern "C" lbm_status lbm_server_tick(lbm_server s, int32_t max_steps, lbm_serve
         stats->queued = (int32_t)s->queue.size();
         stats->admitted = admitted;
         stats->finished = finished;
-        stats->steps = adv;
+        stats->steps = s->inst.empty() ? 0 : adv;
         for (auto &I : s->inst) stats->active_nodes += I.nodes;
         stats->device_bytes = s->arena.used();
         stats->kernel_launches = s->launches;

@@ -134,7 +134,9 @@ Lattice make_lattice(const Tables &t, const Units &u, int storage) {
     return L;
 }
 
-lbm_status prepare(const lbm_desc *desc, Tables *t, Units *u) {
+}  // namespace
+
+lbm_status lbm::prepare(const lbm_desc *desc, Tables *t, Units *u) {
     if (!desc) {
         set_error("NULL descriptor");
         return LBM_ERR_ARG;
@@ -143,6 +145,8 @@ lbm_status prepare(const lbm_desc *desc, Tables *t, Units *u) {
     if (st != LBM_OK) return st;
     return classify(*desc, *u, t);
 }
+
+namespace {
 
 void destroy_graphs(lbm_solver *h) {
     for (auto &g : h->graph)
@@ -215,6 +219,26 @@ extern "C" lbm_status lbm_create(const lbm_desc *desc, void *stream, void *works
 
 namespace lbm {
 
+// Pinned host staging of the probes and the status word, allocated on first
+// use for handles created without them.
+cudaError_t host_buffers(lbm_solver *h) {
+    cudaError_t e = cudaSuccess;
+    if (!h->h_probe_idx) e = cudaMallocHost(&h->h_probe_idx, kMaxProbe * sizeof(int32_t));
+    if (e == cudaSuccess && !h->h_probe_out)
+        e = cudaMallocHost(&h->h_probe_out, 7 * kMaxProbe * sizeof(float));
+    if (e == cudaSuccess && !h->h_status) {
+        e = cudaMallocHost(&h->h_status, sizeof(uint32_t));
+        if (e == cudaSuccess) *h->h_status = 0;
+    }
+    return e;
+}
+
+uint64_t workspace_bytes_for(const lbm_desc &d, const Tables &t, const Units &u) {
+    const int block = steps_per_launch(d, t, u);
+    if (block == 0) return 0;
+    return layout(t, d.storage, u.lam != u.mu, block, d.streaming == LBM_STREAM_IN_PLACE).total;
+}
+
 lbm_status create_solver(const lbm_desc *desc, void *stream, void *workspace,
                          uint64_t workspace_bytes, int plan_blocks, lbm_handle *out) {
     set_error("");
@@ -223,12 +247,25 @@ lbm_status create_solver(const lbm_desc *desc, void *stream, void *workspace,
         return LBM_ERR_ARG;
     }
     *out = nullptr;
+    Tables t;
+    Units u;
+    lbm_status st = prepare(desc, &t, &u);
+    if (st != LBM_OK) return st;
+    CreateOptions opt;
+    opt.plan_blocks = plan_blocks;
+    return create_prepared(desc, std::move(t), u, stream, workspace, workspace_bytes, opt, out);
+}
+
+lbm_status create_prepared(const lbm_desc *desc, Tables &&tab, const Units &units, void *stream,
+                           void *workspace, uint64_t workspace_bytes, const CreateOptions &opt,
+                           lbm_handle *out) {
+    set_error("");
+    *out = nullptr;
+    const int plan_blocks = opt.plan_blocks;
     lbm_solver *h = new lbm_solver();
-    lbm_status st = prepare(desc, &h->tab, &h->units);
-    if (st != LBM_OK) {
-        delete h;
-        return st;
-    }
+    h->tab = std::move(tab);
+    h->units = units;
+    h->deferred = opt.deferred;
     h->storage = desc->storage;
     h->stream = static_cast<cudaStream_t>(stream);
     h->L = make_lattice(h->tab, h->units, h->storage);
@@ -331,7 +368,9 @@ lbm_status create_solver(const lbm_desc *desc, void *stream, void *workspace,
             if (e == cudaSuccess) e = launch_reset(h->storage, h->L, S, h->stream);
         }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    // the host tables stay in the handle, so the uploads need not be waited
+    // for when the creator orders its own work after them (deferred)
+    if (e == cudaSuccess && !opt.deferred) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail(e, "lbm_create: upload");
     e = cudaStreamCreateWithFlags(&h->cap_main, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_side, cudaStreamNonBlocking);
@@ -339,11 +378,8 @@ lbm_status create_solver(const lbm_desc *desc, void *stream, void *workspace,
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gfork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gjoin, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_probe_idx, kMaxProbe * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_probe_out, 7 * kMaxProbe * sizeof(float));
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_status, sizeof(uint32_t));
+    if (e == cudaSuccess && !opt.deferred) e = host_buffers(h);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->status_ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) *h->h_status = 0;
     if (e != cudaSuccess) return fail(e, "lbm_create: streams/events");
     *out = h;
     return LBM_OK;
@@ -376,7 +412,8 @@ extern "C" lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
             return cuda_fail(q, "lbm_step: status query");
         }
     }
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = host_buffers(h);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_step: host buffers");
     int64_t done = 0;
     const int per_step = kernels_per_step(h->L);
     if (h->timing) {
@@ -536,7 +573,8 @@ extern "C" lbm_status lbm_reset(lbm_handle h) {
         set_error("lbm_reset: NULL handle");
         return LBM_ERR_ARG;
     }
-    cudaError_t e = launch_reset(h->storage, h->L, h->S, h->stream);
+    cudaError_t e = host_buffers(h);
+    if (e == cudaSuccess) e = launch_reset(h->storage, h->L, h->S, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "lbm_reset");
     h->cur = 0;
     h->time = 0;
@@ -642,6 +680,23 @@ extern "C" lbm_status lbm_get_timing(lbm_handle h, lbm_timing *out) {
     h->ev_used = 0;
     return LBM_OK;
 }
+
+namespace lbm {
+
+void destroy_deferred(lbm_handle h) {
+    if (!h) return;
+    destroy_graphs(h);
+    if (h->cap_main) cudaStreamDestroy(h->cap_main);
+    if (h->cap_side) cudaStreamDestroy(h->cap_side);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
+    if (h->gfork) cudaEventDestroy(h->gfork);
+    if (h->gjoin) cudaEventDestroy(h->gjoin);
+    if (h->status_ready) cudaEventDestroy(h->status_ready);
+    delete h;
+}
+
+}  // namespace lbm
 
 extern "C" lbm_status lbm_destroy(lbm_handle h) {
     if (!h) return LBM_OK;

@@ -103,6 +103,24 @@ struct Units {
 lbm_status create_solver(const lbm_desc *desc, void *stream, void *workspace,
                          uint64_t workspace_bytes, int plan_blocks, lbm_handle *out);
 
+// Creation from tables already validated and classified (prepare()).
+// deferred: the uploads are queued on the stream and not waited for (the
+// creator orders its later work on the same stream), and the pinned host
+// staging of probes and status is allocated on first use.
+struct CreateOptions {
+    int plan_blocks = 0;
+    bool deferred = false;
+};
+lbm_status prepare(const lbm_desc *desc, Tables *t, Units *u);
+uint64_t workspace_bytes_for(const lbm_desc &d, const Tables &t, const Units &u);
+lbm_status create_prepared(const lbm_desc *desc, Tables &&t, const Units &u, void *stream,
+                           void *workspace, uint64_t workspace_bytes, const CreateOptions &opt,
+                           lbm_handle *out);
+// Releases a handle's host-side resources without synchronising: only for a
+// handle none of whose device work is still pending or will be queued again
+// (its workspace belongs to its creator).
+void destroy_deferred(lbm_handle h);
+
 // Thread-local error text for lbm_last_error().
 void set_error(const std::string &msg);
 
@@ -255,6 +273,7 @@ struct lbm_solver {
     cudaEvent_t status_ready = nullptr;
     bool status_pending = false;
     int64_t launches = 0;            // kernels launched by this handle
+    bool deferred = false;           // created with CreateOptions::deferred
     // timing mode: events around every interior and boundary kernel
     bool timing = false;
     std::vector<lbm::StepEvents> ev_pool;
