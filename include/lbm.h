@@ -56,7 +56,11 @@ typedef enum {
 } lbm_status;
 
 /* Storage of the distribution functions.  All arithmetic is FP32; the 16-bit
- * forms store f - f_rest scaled by a power of two and round to nearest. */
+ * forms store f - f_rest scaled by a power of two and round to nearest.  The
+ * scale starts where the largest boundary value maps to about 8.  BF16 has the
+ * exponent range of FP32 and keeps it; FP16 ends at 65504, so its scale halves
+ * from one step to the next whenever a step stored a value above 8192 (a run
+ * that grows keeps finite values as long as FP32 would). */
 typedef enum { LBM_F32 = 0, LBM_F16_DEV = 1, LBM_BF16_DEV = 2 } lbm_storage;
 
 /* Where the Neumann rules take the wall density rho^bd and the wall stress
@@ -174,7 +178,10 @@ typedef struct {
     int64_t boundary_nodes; /* nodes with at least one cut link */
     int64_t interior_nodes; /* material nodes without cut links */
     uint64_t workspace_bytes;
-    float storage_scale;    /* power-of-two scale of the 16-bit forms, 1 for FP32 */
+    float storage_scale;    /* power-of-two scale of the 16-bit forms, 1 for FP32.
+                               FP16 rescales itself: this is the scale the last
+                               step stored with (lbm_get_info then waits for
+                               the handle's stream) */
     float bytes_per_update; /* algorithmic HBM bytes per interior lattice update */
     int64_t kernel_launches; /* kernels this handle has launched so far */
     int32_t time_block;      /* steps per launch in use: 1, LBM_TIME_BLOCK, or 4

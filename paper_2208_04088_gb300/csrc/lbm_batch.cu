@@ -102,6 +102,16 @@ __global__ void __launch_bounds__(TX *TY, 2048 / (TX * TY)) k_batch_interior(con
         __syncthreads();
         const InstDev &I = *reinterpret_cast<const InstDev *>(s_inst);
         const int64_t time = s_time;
+        if constexpr (std::is_same<T, __half>::value) {
+            // the instance's scales of this step (FP16); the tile of local
+            // index 0 publishes them
+            if (tid == 0 && time < I.target) {
+                InstDev &W = *reinterpret_cast<InstDev *>(s_inst);
+                step_scales<T>(W.L, time);
+                if (s_local == 0) publish_scale<T>(W.L, time);
+            }
+            __syncthreads();
+        }
         if (time < I.target) {
             const int local = s_local;
             const int tx = local % I.tiles_x, ty = local / I.tiles_x;
@@ -144,19 +154,21 @@ __global__ void __launch_bounds__(kB8) k_batch_boundary(const InstDev *__restric
         const int64_t time = *I.time;
         const bool live = in_list && time < I.target;
         const int cur = (int)(time & 1);
+        Lattice L = I.L;
+        step_scales<T>(L, time);
         if (I.L.in_place) {
             // stage: the instance's populations are stored by k_batch_scatter
             // once every boundary node has read its inputs
             T *f = static_cast<T *>(I.f[0]);
             if (cur)
-                boundary8_node<T, kAAOdd>(f, f, I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, I.L, m.y,
+                boundary8_node<T, kAAOdd>(f, f, I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, L, m.y,
                                           live, j, (float)(time - 1), I.status, I.stage);
             else
-                boundary8_node<T, kAAEven>(f, f, I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, I.L, m.y,
+                boundary8_node<T, kAAEven>(f, f, I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, L, m.y,
                                            live, j, (float)(time - 1), I.status, I.stage);
         } else {
             boundary8_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]),
-                              I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, I.L, m.y, live, j,
+                              I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, L, m.y, live, j,
                               (float)(time - 1), I.status);
         }
     }
@@ -176,6 +188,8 @@ __global__ void __launch_bounds__(256) k_batch_scatter(const InstDev *__restrict
         if (!I.L.in_place) continue;
         const int64_t time = *I.time;
         if (time >= I.target) continue;
+        Lattice L = I.L;
+        step_scales<T>(L, time);
         const BNode b = I.bn[m.y];
         const int64_t kn = (int64_t)b.y * I.L.pitch + b.x;
         int64_t o = 0;
@@ -189,7 +203,9 @@ __global__ void __launch_bounds__(256) k_batch_scatter(const InstDev *__restrict
             LBM_OUT(8)
 #undef LBM_OUT
         }
-        Store<T>::st(static_cast<T *>(I.f[0]) + o, I.stage[(int64_t)m.y * 9 + d], I.L.scale);
+        const float v = I.stage[(int64_t)m.y * 9 + d];
+        Store<T>::st(static_cast<T *>(I.f[0]) + o, v, L.scale);
+        note_range<T>(L, fabsf(v));
     }
 }
 

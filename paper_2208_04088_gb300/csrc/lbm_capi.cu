@@ -25,8 +25,8 @@ lbm_status cuda_fail(cudaError_t e, const char *where) {
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct Layout {
-    size_t f0, f1, ucomp, cls, bnodes, blinks, bcs, rho, status, time, stage, probe, probe_idx,
-        nw, wave_tab, total;
+    size_t f0, f1, ucomp, cls, bnodes, blinks, bcs, rho, status, time, scale, stage, probe,
+        probe_idx, nw, wave_tab, total;
 };
 
 // Steps per launch for a description: the temporally blocked kernel needs FP32
@@ -85,6 +85,7 @@ Layout layout(const Tables &t, int storage, bool grad, int block, bool in_place)
     l.rho = grad ? take(plane * sizeof(float)) : 0;
     l.status = take(sizeof(uint32_t));
     l.time = take(sizeof(int64_t));
+    l.scale = take(sizeof(ScaleState));
     // field staging; in place it also holds the boundary nodes' populations
     // between their update and their store (9 per boundary node)
     l.stage = take(std::max(7 * N, in_place ? 9 * t.bnodes.size() : 0) * sizeof(float));
@@ -327,6 +328,8 @@ lbm_status create_prepared(const lbm_desc *desc, Tables &&tab, const Units &unit
     S.rho = h->L.grad ? reinterpret_cast<float *>(b + lay.rho) : nullptr;
     S.status = reinterpret_cast<uint32_t *>(b + lay.status);
     S.time = reinterpret_cast<int64_t *>(b + lay.time);
+    // FP16 storage rescales itself (ScaleState); the other forms keep L.scale
+    h->L.sc = h->storage == LBM_F16_DEV ? reinterpret_cast<ScaleState *>(b + lay.scale) : nullptr;
     S.stage = reinterpret_cast<float *>(b + lay.stage);
     S.probe = reinterpret_cast<float *>(b + lay.probe);
     S.probe_idx = reinterpret_cast<int32_t *>(b + lay.probe_idx);
@@ -622,6 +625,14 @@ extern "C" lbm_status lbm_get_info(lbm_handle h, lbm_info *info) {
     info->interior_nodes = h->tab.interior;
     info->workspace_bytes = h->bytes;
     info->storage_scale = h->L.scale;
+    if (h->L.sc) {
+        // FP16: the scale the last step stored with (waits for the stream)
+        ScaleState sc;
+        cudaError_t e = cudaMemcpyAsync(&sc, h->L.sc, sizeof sc, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_get_info: scale");
+        info->storage_scale = sc.s[(h->time + 2) % 3];
+    }
     const float esz = h->storage == LBM_F32 ? 4.0f : 2.0f;
     info->bytes_per_update = 2.0f * 9.0f * esz + 32.0f;  // f read + write, u and compensation R+W
     info->kernel_launches = h->launches;

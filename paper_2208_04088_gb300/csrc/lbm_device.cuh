@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -45,6 +46,44 @@ struct Store<__nv_bfloat16> {
         *p = __float2bfloat16_rn(v * scale);
     }
 };
+
+// The scales of step t with FP16 storage: L.inv_scale for the values the step
+// reads (stored by step t - 1) and L.scale for the values it stores (the
+// scale of step t - 1, halved if one of its values passed kScaleOver).  Other
+// storage forms keep their fixed scale.  Every kernel of a step computes the
+// same pair from the solver's scale record.
+template <class T> __device__ __forceinline__ void step_scales(Lattice &L, int64_t t) {
+    if constexpr (std::is_same<T, __half>::value) {
+        if (L.sc) {
+            const int p = (int)((t + 2) % 3);
+            const float prev = L.sc->s[p];
+            L.inv_scale = __fdiv_rn(1.0f, prev);  // a power of two: exact
+            L.scale = L.sc->over[p] ? fmaxf(__fmul_rn(prev, 0.5f), kScaleMin) : prev;
+            L.over = L.sc->over + t % 3;
+        }
+    }
+}
+
+// Step t's scale into the record, and the flag of step t + 1 cleared (it
+// holds step t - 2's, which no kernel of step t reads).  One thread per step.
+template <class T> __device__ __forceinline__ void publish_scale(const Lattice &L, int64_t t) {
+    if constexpr (std::is_same<T, __half>::value) {
+        if (L.sc) {
+            L.sc->s[t % 3] = L.scale;
+            L.sc->over[(t + 1) % 3] = 0u;
+        }
+    }
+}
+
+// Flags the step (L as step_scales left it) when a value it stores, scaled,
+// passes kScaleOver.
+template <class T> __device__ __forceinline__ void note_range(const Lattice &L, float v) {
+    if constexpr (std::is_same<T, __half>::value) {
+        if (L.over && fabsf(__fmul_rn(v, L.scale)) > kScaleOver &&
+            !*reinterpret_cast<volatile uint32_t *>(L.over))
+            atomicExch(L.over, 1u);
+    }
+}
 
 // D2Q9 velocity components and opposite directions as constant expressions.
 __host__ __device__ constexpr int c_cx(int i) {
@@ -784,6 +823,12 @@ __device__ __forceinline__ void interior_node(const T *src, T *dst, float4 *__re
     collide(f, sx, sy, L, dr, jx, jy);
 #pragma unroll
     for (int i = 0; i < 9; ++i) Store<T>::st(dst + out_at<LAY>(k, i, L), f[i], L.scale);
+    if constexpr (std::is_same<T, __half>::value) {
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) m = fmaxf(m, fabsf(f[i]));
+        note_range<T>(L, m);
+    }
     integrate_u_value(w, jx, jy, L.rho0 + dr);
     uc[k] = w;
     flag_nonfinite(status, dr, jx, jy);
@@ -825,6 +870,7 @@ __device__ __forceinline__ void boundary8_node(const T *src, T *dst, float4 *__r
     } else {
         Store<T>::st(dst + out_at<LAY>(kn, kdir, L), mine, L.scale);
         if (lane0) Store<T>::st(dst + out_at<LAY>(kn, 0, L), fr, L.scale);
+        note_range<T>(L, fmaxf(fabsf(mine), lane0 ? fabsf(fr) : 0.0f));
     }
     if (lane0) {
         integrate_u(uc + kn, jx, jy, L.rho0 + m00);

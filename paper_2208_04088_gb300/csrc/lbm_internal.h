@@ -52,6 +52,18 @@ struct BCDev {
 };
 static_assert(sizeof(BCDev) == 24, "BCDev layout");
 
+// FP16 storage: the power-of-two scale of the populations stored by each of
+// the last three steps (step t in entry t mod 3) and whether a value stored by
+// that step exceeded kScaleOver.  Step t loads with the scale of step t - 1
+// and stores with it, halved if that step's flag is set (FP16 ends at 65504,
+// so a value can grow eightfold in one step before it overflows).
+struct ScaleState {
+    float s[3];
+    uint32_t over[3];
+};
+constexpr float kScaleOver = 8192.0f;
+constexpr float kScaleMin = 1.0e-30f;
+
 // Scalar parameters of one lattice, passed by value to every kernel.
 struct Lattice {
     int32_t nx, ny, pitch, nb;  // nb: number of boundary nodes
@@ -71,6 +83,8 @@ struct Lattice {
     int32_t in_place;           // one population buffer, AA pattern (lbm_desc.streaming)
     int32_t nbcs;               // entries of the boundary-condition table
     int64_t wait_ns;            // limit of a kernel's wait for a tile copy (lbm_set_wait_limit)
+    ScaleState *sc;             // FP16 storage: the adaptive scale (null otherwise)
+    uint32_t *over;             // FP16: this step's flag in *sc (set per step by step_scales)
 };
 
 // Default of Lattice::wait_ns, and the limit of the waits that drain the

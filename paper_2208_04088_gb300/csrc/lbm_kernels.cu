@@ -33,14 +33,30 @@ constexpr int kBB = 64;  // threads per block of the boundary-list kernels
 // Every load of a node -- the nine pulled populations and the displacement
 // record -- is issued before any arithmetic, so all of them are in flight
 // together.
+// With FP16 storage the kernel takes its step's scales from the solver's
+// record (step t = *time + toff), and its first thread publishes them.
+template <class T>
+__device__ __forceinline__ int64_t scales_of_step(Lattice &L, const int64_t *time, int toff,
+                                                  bool publisher) {
+    int64_t t = 0;
+    if constexpr (std::is_same<T, __half>::value) {
+        t = *time + toff;
+        step_scales<T>(L, t);
+        if (publisher) publish_scale<T>(L, t);
+    }
+    return t;
+}
+
 template <class T, int NR, int LAY = kPull>
 __global__ void __launch_bounds__(kBX *kBY, 8) k_interior(const T *src, T *dst,
                                                        float4 *__restrict__ uc,
                                                        const uint8_t *__restrict__ cls,
                                                        const float *__restrict__ rho, Lattice L,
-                                                       uint32_t *__restrict__ status) {
+                                                       uint32_t *__restrict__ status,
+                                                       const int64_t *__restrict__ time, int toff) {
     const int x = blockIdx.x * kBX + threadIdx.x;
     const int y0 = blockIdx.y * (kBY * NR) + threadIdx.y;
+    scales_of_step<T>(L, time, toff, x == 0 && y0 == 0);
     if (x >= L.nx) return;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
@@ -64,10 +80,13 @@ __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict_
                                                             const uint8_t *__restrict__ cls,
                                                             const float *__restrict__ rho,
                                                             Lattice L,
-                                                            uint32_t *__restrict__ status) {
+                                                            uint32_t *__restrict__ status,
+                                                            const int64_t *__restrict__ time,
+                                                            int toff) {
     __shared__ float rs[kGY + 2][kBX + 2];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kGY;
+    scales_of_step<T>(L, time, toff, x0 + tx == 0 && y0 + ty == 0);
     const int x = x0 + tx, y = y0 + ty;
     // the ring: top and bottom rows (kBX + 2 each), left and right columns (kGY each)
     const int tid = ty * kBX + tx;
@@ -129,37 +148,16 @@ __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict_
     collide(f, sx, sy, L, dr, jx, jy);
 #pragma unroll
     for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.fplane + k, f[i], L.scale);
+    if constexpr (std::is_same<T, __half>::value) {
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) m = fmaxf(m, fabsf(f[i]));
+        note_range<T>(L, m);
+    }
     integrate_u_value(w, jx, jy, L.rho0 + dr);
     uc[k] = w;
     flag_nonfinite(status, dr, jx, jy);
 }
-
-template <class T>
-__global__ void __launch_bounds__(kBB) k_boundary(const T *__restrict__ src, T *__restrict__ dst,
-                                                  float4 *__restrict__ uc,
-                                                  const BNode *__restrict__ bnodes,
-                                                  const BLink *__restrict__ blinks,
-                                                  const BCDev *__restrict__ bcs,
-                                                  const float *__restrict__ rho, Lattice L,
-                                                  const int64_t *__restrict__ time, int toff,
-                                                  uint32_t *__restrict__ status) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= L.nb) return;
-    const BNode b = bnodes[m];
-    const float tb = (float)(*time + toff - 1);  // boundary data at the time of f^col
-    float f[9];
-    pull_boundary(src, b, blinks + (int64_t)m * 8, bcs, tb, L, f);
-    const int64_t k = (int64_t)b.y * L.pitch + b.x;
-    float sx = L.fx, sy = L.fy;
-    if (L.grad) source_boundary(rho, b, k, rho[k], L, sx, sy);
-    float dr, jx, jy;
-    collide(f, sx, sy, L, dr, jx, jy);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.fplane + k, f[i], L.scale);
-    integrate_u(uc + k, jx, jy, L.rho0 + dr);
-    flag_nonfinite(status, dr, jx, jy);
-}
-
 
 template <class T, int LAY = kPull>
 __global__ void __launch_bounds__(kB8) k_boundary8(const T *src, T *dst, float4 *__restrict__ uc,
@@ -173,6 +171,7 @@ __global__ void __launch_bounds__(kB8) k_boundary8(const T *src, T *dst, float4 
                                                    float *__restrict__ stage) {
     const int g = (blockIdx.x * kB8 + threadIdx.x) >> 3;  // boundary node of this lane group
     const float tb = (float)(*time + toff - 1);           // boundary data at the time of f^col
+    scales_of_step<T>(L, time, toff, false);
     // groups past the end of the list work on node 0 and store nothing
     const bool live = g < L.nb;
     boundary8_node<T, LAY>(src, dst, uc, bnodes, blinks, bcs, cls, rho, L, live ? g : 0, live,
@@ -185,7 +184,10 @@ template <class T, int LAY>
 __global__ void __launch_bounds__(kBB) k_boundary_scatter(const float *__restrict__ stage,
                                                           T *dst,
                                                           const BNode *__restrict__ bnodes,
-                                                          Lattice L) {
+                                                          Lattice L,
+                                                          const int64_t *__restrict__ time,
+                                                          int toff) {
+    scales_of_step<T>(L, time, toff, false);
     const int64_t e = (int64_t)blockIdx.x * kBB + threadIdx.x;
     if (e >= (int64_t)L.nb * 9) return;
     const int g = (int)(e / 9), m = (int)(e % 9);
@@ -201,6 +203,7 @@ __global__ void __launch_bounds__(kBB) k_boundary_scatter(const float *__restric
 #undef LBM_OUT
     }
     Store<T>::st(dst + o, stage[e], L.scale);
+    note_range<T>(L, fabsf(stage[e]));
 }
 
 // Density at time t of every material node (lambda != mu): pull, with the
@@ -209,7 +212,9 @@ __global__ void __launch_bounds__(kBB) k_boundary_scatter(const float *__restric
 template <class T>
 __global__ void __launch_bounds__(kBX *kBY) k_density_interior(const T *__restrict__ src,
                                                                const uint8_t *__restrict__ cls,
-                                                               float *__restrict__ rho, Lattice L) {
+                                                               float *__restrict__ rho, Lattice L,
+                                                               const int64_t *__restrict__ time) {
+    scales_of_step<T>(L, time, 0, false);
     const int x = blockIdx.x * kBX + threadIdx.x;
     const int y = blockIdx.y * kBY + threadIdx.y;
     if (x >= L.nx || y >= L.ny) return;
@@ -228,6 +233,7 @@ __global__ void __launch_bounds__(kBB) k_density_boundary(const T *__restrict__ 
                                                           float *__restrict__ rho, Lattice L,
                                                           const int64_t *__restrict__ time,
                                                           int toff) {
+    scales_of_step<T>(L, time, toff, false);
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= L.nb) return;
     const BNode b = bnodes[m];
@@ -259,7 +265,9 @@ __global__ void __launch_bounds__(kBX *kBY) k_fields_interior(const T *__restric
                                                               const float4 *__restrict__ uc,
                                                               const uint8_t *__restrict__ cls,
                                                               const float *__restrict__ rho,
-                                                              Lattice L, float *__restrict__ out) {
+                                                              Lattice L, float *__restrict__ out,
+                                                              const int64_t *__restrict__ time) {
+    scales_of_step<T>(L, time, 0, false);  // the populations stored by the last step
     const int x = blockIdx.x * kBX + threadIdx.x;
     const int y = blockIdx.y * kBY + threadIdx.y;
     if (x >= L.nx || y >= L.ny) return;
@@ -288,6 +296,7 @@ __global__ void __launch_bounds__(kBB) k_fields_boundary(const T *__restrict__ s
                                                          const float *__restrict__ rho, Lattice L,
                                                          const int64_t *__restrict__ time,
                                                          float *__restrict__ out) {
+    scales_of_step<T>(L, time, 0, false);  // the populations stored by the last step
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= L.nb) return;
     const BNode b = bnodes[m];
@@ -302,6 +311,15 @@ __global__ void __launch_bounds__(kBB) k_fields_boundary(const T *__restrict__ s
 }
 
 __global__ void k_advance(int64_t *time, int64_t n) { *time += n; }
+
+// The scale record at rest: every step so far stored with the initial scale
+// and no value passed the threshold.
+__global__ void k_scale_reset(ScaleState *sc, float scale) {
+    for (int i = 0; i < 3; ++i) {
+        sc->s[i] = scale;
+        sc->over[i] = 0u;
+    }
+}
 
 __global__ void k_gather_probe(const float *__restrict__ stage, const int32_t *__restrict__ idx,
                                int count, int64_t N, float *__restrict__ out) {
@@ -351,18 +369,20 @@ static cudaError_t launch_boundary(const T *src, T *dst, const DevState &S, cons
 }
 
 template <class T>
-static void launch_interior(const T *src, T *dst, const DevState &S, const Lattice &L,
+static void launch_interior(const T *src, T *dst, const DevState &S, const Lattice &L, int toff,
                             cudaStream_t s) {
     if (L.grad) {
         const dim3 blk(kBX, kGY), grd((L.nx + kBX - 1) / kBX, (L.ny + kGY - 1) / kGY);
-        k_interior_grad<T><<<grd, blk, 0, s>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status);
+        k_interior_grad<T><<<grd, blk, 0, s>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status,
+                                                S.time, toff);
         return;
     }
     // one row per thread measured fastest for every storage (2 and 4 rows cost
     // occupancy: 58+ registers)
     constexpr int NR = 1;
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY * NR - 1) / (kBY * NR));
-    k_interior<T, NR><<<grd, blk, 0, s>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status);
+    k_interior<T, NR><<<grd, blk, 0, s>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status, S.time,
+                                          toff);
 }
 
 // In-place step of parity LAY: every boundary node reads its inputs and
@@ -386,17 +406,18 @@ static cudaError_t step_in_place(const Lattice &L, const DevState &S, int toff,
     if (split) {
         cudaEventRecord(fork, s_main);
         cudaStreamWaitEvent(s_side, fork, 0);
-        k_boundary_scatter<T, LAY><<<nsc, kBB, 0, s_side>>>(S.stage, f, S.bnodes, L);
+        k_boundary_scatter<T, LAY><<<nsc, kBB, 0, s_side>>>(S.stage, f, S.bnodes, L, S.time, toff);
         cudaEventRecord(join, s_side);
     }
     if (ev) cudaEventRecord(ev->before_interior, s_main);
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
-    k_interior<T, 1, LAY><<<grd, blk, 0, s_main>>>(f, f, S.ucomp, S.cls, S.rho, L, S.status);
+    k_interior<T, 1, LAY><<<grd, blk, 0, s_main>>>(f, f, S.ucomp, S.cls, S.rho, L, S.status, S.time,
+                                                   toff);
     if (ev) cudaEventRecord(ev->after_interior, s_main);
     if (split)
         cudaStreamWaitEvent(s_main, join, 0);
     else if (L.nb > 0)
-        k_boundary_scatter<T, LAY><<<nsc, kBB, 0, s_main>>>(S.stage, f, S.bnodes, L);
+        k_boundary_scatter<T, LAY><<<nsc, kBB, 0, s_main>>>(S.stage, f, S.bnodes, L, S.time, toff);
     return cudaGetLastError();
 }
 
@@ -427,7 +448,7 @@ static cudaError_t step_t(const Lattice &L, const DevState &S, int cur, int toff
         cudaEventRecord(join, s_side);
     }
     if (ev) cudaEventRecord(ev->before_interior, s_main);
-    launch_interior<T>(src, dst, S, L, s_main);
+    launch_interior<T>(src, dst, S, L, toff, s_main);
     if (ev) cudaEventRecord(ev->after_interior, s_main);
     if (split) {
         cudaStreamWaitEvent(s_main, join, 0);
@@ -466,7 +487,7 @@ template <class T, int LAY>
 static void fields_in_place(const Lattice &L, const DevState &S, cudaStream_t s) {
     const T *src = static_cast<const T *>(S.f[0]);
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
-    k_fields_interior<T, LAY><<<grd, blk, 0, s>>>(src, S.ucomp, S.cls, S.rho, L, S.stage);
+    k_fields_interior<T, LAY><<<grd, blk, 0, s>>>(src, S.ucomp, S.cls, S.rho, L, S.stage, S.time);
     if (L.nb > 0)
         k_fields_boundary<T, LAY><<<(L.nb + kBB - 1) / kBB, kBB, 0, s>>>(
             src, S.ucomp, S.bnodes, S.blinks, S.bcs, S.rho, L, S.time, S.stage);
@@ -485,12 +506,12 @@ static cudaError_t fields_t(const Lattice &L, const DevState &S, int cur, cudaSt
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
     const int nbb = (L.nb + kBB - 1) / kBB;
     if (L.grad) {
-        k_density_interior<T><<<grd, blk, 0, s>>>(src, S.cls, S.rho, L);
+        k_density_interior<T><<<grd, blk, 0, s>>>(src, S.cls, S.rho, L, S.time);
         if (L.nb > 0)
             k_density_boundary<T><<<nbb, kBB, 0, s>>>(src, S.bnodes, S.blinks, S.bcs, S.rho, L,
                                                       S.time, 0);
     }
-    k_fields_interior<T><<<grd, blk, 0, s>>>(src, S.ucomp, S.cls, S.rho, L, S.stage);
+    k_fields_interior<T><<<grd, blk, 0, s>>>(src, S.ucomp, S.cls, S.rho, L, S.stage, S.time);
     if (L.nb > 0)
         k_fields_boundary<T><<<nbb, kBB, 0, s>>>(src, S.ucomp, S.bnodes, S.blinks, S.bcs, S.rho,
                                                  L, S.time, S.stage);
@@ -537,6 +558,10 @@ cudaError_t launch_reset(int storage, const Lattice &L, const DevState &S, cudaS
     if (e == cudaSuccess && S.rho) e = cudaMemsetAsync(S.rho, 0, (size_t)L.plane * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.status, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.time, 0, sizeof(int64_t), s);
+    if (e == cudaSuccess && L.sc) {
+        k_scale_reset<<<1, 1, 0, s>>>(L.sc, L.scale);
+        e = cudaGetLastError();
+    }
     return e;
 }
 
