@@ -366,6 +366,57 @@ def _variant_record(wl, args, dev, stream, storage, wall_node, time_block, solve
             "unstable": unstable, "roofline": roof}
 
 
+def _batch_record(dev, stream, storage, wall_node, count, steps, loop):
+    """Config 4 (seeded plates with holes, `count` instances, `steps` steps):
+    one batched solve timed with CUDA events after a warm-up solve, and, if
+    `loop`, the same instances solved one after another through lbm_step in
+    FP32 (the per-instance loop)."""
+    import torch
+
+    from paper_2208_04088_gb300 import _native as N
+    from paper_2208_04088_gb300 import workloads as W
+    wls = W.batched_instances(count, seed=4, steps=steps)
+    b = N.Batch([N.desc_from_workload(w, storage=storage, wall_node=wall_node) for w in wls],
+                stream=stream)
+    shape = b.tune(steps_per_trial=20)
+    info = b.info()
+    nodes = info["nodes"]
+    b.reset()
+    b.step(steps)
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    b.reset()
+    b.step(steps)
+    stop.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = start.elapsed_time(stop)
+    info = b.info()
+    b.close()
+    rec = {"value": nodes * steps / (ms * 1e-3) / 1e9, "unit": "GLUPS", "storage": storage,
+           "instances": count, "material_nodes": nodes, "time_steps": steps,
+           "blocked_instances": info["blocked_instances"], "unstable_instances": info["unstable"],
+           "tuned_shape": shape, "ms_per_solve": ms}
+    if loop:
+        solvers = [N.Solver(N.desc_from_workload(w, wall_node=wall_node), stream=stream)
+                   for w in wls]
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for sv in solvers:
+            sv.step(steps)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        lms = start.elapsed_time(stop)
+        for sv in solvers:
+            sv.close()
+        rec["per_instance_loop"] = {"value": nodes * steps / (lms * 1e-3) / 1e9, "unit": "GLUPS",
+                                    "storage": "f32",
+                                    "how": "lbm_step per instance, one after another"}
+        rec["speedup_over_loop"] = rec["value"] / rec["per_instance_loop"]["value"]
+    return rec
+
+
 def _k_apparent(sigma_yy, length, y):
     """Apparent stress intensity ahead of the tip (tip at x = length - 1/2):
     the largest sigma_yy sqrt(2 pi r) over r = 1.5 .. 10.5, sigma_yy averaged
@@ -837,6 +888,12 @@ def run_gpu(args):
         from paper_2208_04088_gb300 import workloads as W
         trace = W.serving_trace(args.sub_requests, seed=5, rate=args.sub_rate,
                                 max_side=args.sub_max_side, max_steps=args.sub_max_steps)
+        extras["batch"] = {
+            "workload": f"batched_{args.batch_count}_hole_plates_seed4, {args.batch_steps} steps",
+            "f32": _batch_record(dev, stream, "f32", wall_node, args.batch_count,
+                                 args.batch_steps, loop=True),
+            "f16": _batch_record(dev, stream, "f16", wall_node, args.batch_count,
+                                 args.batch_steps, loop=False)}
         extras["serving"] = {
             "trace": (f"seed 5, {args.sub_requests} requests, Poisson {args.sub_rate:g}/s, "
                       f"sides 64..{args.sub_max_side}, steps 1000..{args.sub_max_steps}; "

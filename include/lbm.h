@@ -345,7 +345,7 @@ typedef struct {
  * every one with lambda = mu and the same storage), all at rest at t = 0.
  * FP32 instances with two population buffers and nx >= 128 are stepped by the
  * temporally blocked kernel: one persistent launch per LBM_TIME_BLOCK steps
- * over the strip segments of all of them (segments of about 384 rows, the
+ * over the strip segments of all of them (segments of about 768 rows, the
  * longest first, taken by the blocks from a counter).  The other instances
  * are stepped one step per launch by the batched interior and boundary
  * kernels.  time_block of the descriptors is not used; each instance keeps

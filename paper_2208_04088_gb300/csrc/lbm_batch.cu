@@ -439,15 +439,16 @@ lbm_status ensure_capacity(lbm_engine *E, int ninst, int64_t ntiles, int64_t nbn
 }
 
 // Regions of the blocked instances: per instance, the strip segments of a
-// plan for plan_blocks blocks; all of them ordered by modelled cost (rows
-// swept), longest first, so that the blocks that take them from the counter
-// end close together.
+// plan for plan_blocks blocks; all of them ordered by the planner's modelled
+// cost (row sweeps, boundary updates included), the most expensive first, so
+// that the blocks that take them from the counter end close together.
 lbm_status rebuild_wave_tables(lbm_engine *E) {
     bool any = E->nblocked > 0;
     for (const Instance &I : E->inst) any = any || I.blocked;
     if (!any) return LBM_OK;
     std::vector<WaveInst> wi;
     std::vector<std::pair<int, int4>> reg;  // (record, region)
+    std::vector<double> cost;
     for (size_t i = 0; i < E->inst.size(); ++i) {
         const Instance &I = E->inst[i];
         if (!I.blocked) continue;
@@ -466,19 +467,23 @@ lbm_status rebuild_wave_tables(lbm_engine *E) {
         w.time = h->S.time;
         w.status = h->S.status;
         w.L = h->L;
-        for (const int4 &r : wave_plan(h->tab, I.plan_blocks))
-            reg.emplace_back((int)wi.size(), r);
+        const std::vector<int4> plan = wave_plan(h->tab, I.plan_blocks);
+        const std::vector<double> c = wave_plan_costs(h->tab, plan);
+        for (size_t r = 0; r < plan.size(); ++r) {
+            reg.emplace_back((int)wi.size(), plan[r]);
+            cost.push_back(c[r]);
+        }
         wi.push_back(w);
     }
-    std::stable_sort(reg.begin(), reg.end(),
-                     [](const std::pair<int, int4> &a, const std::pair<int, int4> &b) {
-                         return a.second.z > b.second.z;
-                     });
+    std::vector<size_t> order(reg.size());
+    for (size_t r = 0; r < order.size(); ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(),
+                     [&cost](size_t a, size_t b) { return cost[a] > cost[b]; });
     std::vector<int4> regions(reg.size());
     std::vector<int32_t> rinst(reg.size());
     for (size_t r = 0; r < reg.size(); ++r) {
-        regions[r] = reg[r].second;
-        rinst[r] = reg[r].first;
+        regions[r] = reg[order[r]].second;
+        rinst[r] = reg[order[r]].first;
     }
     cudaError_t e = cudaSuccess;
     if ((int)wi.size() > E->cap_winst) {
@@ -826,7 +831,7 @@ lbm_desc one_step(const lbm_desc &d) {
 // enough that the 3 kWaveK - 3 rows of a segment's pipeline fill and drain
 // stay a small part of it, short enough that a batch holds many more segments
 // than the device has SMs.
-constexpr int kBatchSegmentRows = 384;
+constexpr int kBatchSegmentRows = 768;
 
 // Whether an instance of the lockstep batch takes the temporally blocked
 // kernel: FP32 storage, two population buffers and at least kWaveC columns.

@@ -219,6 +219,8 @@ size_t wave_table_entries(int nx, int ny);
 bool complex_boundary_node(const Tables &t, size_t g);
 // The blocks of one launch for a device with `sms` SMs: (X0, Y0, rows, has_boundary).
 std::vector<int4> wave_plan(const Tables &t, int sms);
+// The modelled cost (in row sweeps) of each block of a plan of this lattice.
+std::vector<double> wave_plan_costs(const Tables &t, const std::vector<int4> &plan);
 // Builds the node words from the class and boundary tables, the TMA
 // descriptors and the block table (planned for the device's SMs, or for
 // plan_blocks blocks if it is positive); S.nw (8 bytes per node of the

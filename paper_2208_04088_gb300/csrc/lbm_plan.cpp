@@ -193,6 +193,21 @@ std::vector<int4> wave_plan(const Tables &t, int sms) {
     return cut_strips(br, nstrips, ny, std::max(sms, nstrips), cost);
 }
 
+std::vector<double> wave_plan_costs(const Tables &t, const std::vector<int4> &plan) {
+    const int nstrips = (t.nx + kPW - 1) / kPW;
+    const StripRows br = strip_rows(t, nstrips);
+    std::vector<double> out;
+    out.reserve(plan.size());
+    for (const int4 &b : plan) {
+        const int sx = b.x / kPW, a = b.y, e = b.y + b.z;
+        const auto &r = br.row[sx];
+        const size_t lo = std::lower_bound(r.begin(), r.end(), a - kPK) - r.begin();
+        const size_t hi = std::lower_bound(r.begin(), r.end(), e + kPK) - r.begin();
+        out.push_back((double)(e - a + 3 * kPK - 3) + kBlockCost + (br.pre[sx][hi] - br.pre[sx][lo]));
+    }
+    return out;
+}
+
 namespace {
 
 // Measured plans of this process, by lattice: a lattice created again (same
