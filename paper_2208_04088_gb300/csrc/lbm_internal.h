@@ -62,7 +62,10 @@ struct ScaleState {
     uint32_t over[3];
 };
 constexpr float kScaleOver = 8192.0f;
-constexpr float kScaleMin = 1.0e-30f;
+// The smallest scale, 2^-126 (the smallest normal FP32 number; its inverse,
+// 2^126, is finite): scaled FP16 values then reach 65504 * 2^126, beyond the
+// FP32 range, so FP16 storage never overflows before an FP32 solve would.
+constexpr float kScaleMin = 1.17549435e-38f;
 
 // Scalar parameters of one lattice, passed by value to every kernel.
 struct Lattice {
@@ -82,6 +85,9 @@ struct Lattice {
                                 // in-place streaming pitch * (ny + 2) (a ring of one node)
     int32_t in_place;           // one population buffer, AA pattern (lbm_desc.streaming)
     int32_t nbcs;               // entries of the boundary-condition table
+    int32_t nbx;                // boundary nodes [0, nbx) take the eight-lane update; the
+                                // rest are simple ones, one lane each (two buffers, lambda = mu)
+    int32_t pad0;
     int64_t wait_ns;            // limit of a kernel's wait for a tile copy (lbm_set_wait_limit)
     ScaleState *sc;             // FP16 storage: the adaptive scale (null otherwise)
     uint32_t *over;             // FP16: this step's flag in *sc (set per step by step_scales)
@@ -98,6 +104,7 @@ struct Tables {
     std::vector<BNode> bnodes;   // canonical order (row-major)
     std::vector<BLink> blinks;   // [nb][8]
     std::vector<BCDev> bcs;
+    int64_t nbx = 0;             // boundary nodes before the simple ones (see partition_boundary)
     int64_t interior = 0;
     float max_load = 0.0f;       // largest boundary-value magnitude (lattice units)
 };
@@ -217,6 +224,9 @@ size_t wave_table_entries(int nx, int ny);
 // walls, corners, crack mouth) rather than the one-lane update of a mid-link
 // wall with one BC and one axis-aligned normal.
 bool complex_boundary_node(const Tables &t, size_t g);
+// Reorders the boundary list (nodes and their link records) so that the nodes
+// that are not simple come first, each part in its original order; sets t.nbx.
+void partition_boundary(Tables &t);
 // The blocks of one launch for a device with `sms` SMs: (X0, Y0, rows, has_boundary).
 std::vector<int4> wave_plan(const Tables &t, int sms);
 // The modelled cost (in row sweeps) of each block of a plan of this lattice.
