@@ -52,7 +52,8 @@ struct InstDev {
 
 // Sizes of the work tables and the dynamic-schedule counters (device memory).
 struct BatchCounts {
-    int32_t ntiles, nbnodes, ninst, pad;
+    int32_t ntiles, nbnodes, ninst;
+    int32_t nbx;  // entries [0, nbx) of the boundary map take the eight-lane update, the rest one lane
     int32_t tile_counter, pad2[3];
 };
 
@@ -142,7 +143,7 @@ template <class T>
 __global__ void __launch_bounds__(kB8) k_batch_boundary(const InstDev *__restrict__ insts,
                                                         const int2 *__restrict__ bmap,
                                                         const BatchCounts *__restrict__ counts) {
-    const int nb = counts->nbnodes;
+    const int nb = counts->nbx;  // map entries [0, nbx): eight lanes to a node
     constexpr int kGroups = kB8 / 8;
     const int j = threadIdx.x & 7;
     // the loop bound is uniform over the block, so all lanes reach the shuffles
@@ -171,6 +172,27 @@ __global__ void __launch_bounds__(kB8) k_batch_boundary(const InstDev *__restric
                               I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, L, m.y, live, j,
                               (float)(time - 1), I.status);
         }
+    }
+}
+
+// Map entries [nbx, nbnodes): the simple boundary nodes of two-buffer
+// instances (box edges, crack faces), one lane each, bit-identical to the
+// eight-lane update.
+template <class T>
+__global__ void __launch_bounds__(128) k_batch_simple(const InstDev *__restrict__ insts,
+                                                      const int2 *__restrict__ bmap,
+                                                      const BatchCounts *__restrict__ counts) {
+    for (int g = counts->nbx + blockIdx.x * 128 + threadIdx.x; g < counts->nbnodes;
+         g += gridDim.x * 128) {
+        const int2 m = bmap[g];
+        const InstDev &I = insts[m.x];
+        const int64_t time = *I.time;
+        if (time >= I.target) continue;
+        const int cur = (int)(time & 1);
+        Lattice L = I.L;
+        step_scales<T>(L, time);
+        simple_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]), I.uc,
+                       I.bn, I.bl, I.bcs, L, m.y, (float)(time - 1), I.status);
     }
 }
 
@@ -526,7 +548,7 @@ lbm_status rebuild_wave_tables(lbm_engine *E) {
 lbm_status rebuild_tables(lbm_engine *E) {
     const int TX = E->shape.tile_x, TY = E->shape.tile_y;
     std::vector<InstDev> hi(E->inst.size());
-    std::vector<int2> tiles, bmap;
+    std::vector<int2> tiles, bmap, simple;
     for (size_t i = 0; i < E->inst.size(); ++i) {
         const lbm_solver *h = E->inst[i].h;
         InstDev &d = hi[i];
@@ -548,8 +570,14 @@ lbm_status rebuild_tables(lbm_engine *E) {
         if (d.blocked) continue;  // not in the one-step tables
         const int tiles_y = (h->L.ny + TY - 1) / TY;
         for (int t = 0; t < d.tiles_x * tiles_y; ++t) tiles.push_back(make_int2((int)i, t));
-        for (int b = 0; b < h->L.nb; ++b) bmap.push_back(make_int2((int)i, b));
+        // the simple boundary nodes (after the others in the list) of a two-buffer
+        // instance take one lane each; in place, every node takes eight
+        const int nbx = h->L.in_place ? h->L.nb : (int)h->tab.nbx;
+        for (int b = 0; b < nbx; ++b) bmap.push_back(make_int2((int)i, b));
+        for (int b = nbx; b < h->L.nb; ++b) simple.push_back(make_int2((int)i, b));
     }
+    const int32_t nbx = (int32_t)bmap.size();
+    bmap.insert(bmap.end(), simple.begin(), simple.end());
     lbm_status st = ensure_capacity(E, (int)hi.size(), (int64_t)tiles.size(), (int64_t)bmap.size());
     if (st != LBM_OK) return st;
     E->n_in_place = 0;
@@ -565,6 +593,7 @@ lbm_status rebuild_tables(lbm_engine *E) {
     std::memset(&c, 0, sizeof c);
     c.ntiles = (int32_t)tiles.size();
     c.nbnodes = (int32_t)bmap.size();
+    c.nbx = nbx;
     c.ninst = (int32_t)hi.size();
     // the uploads go through pinned staging, queued on the stream behind the
     // steps already queued (which still read the old tables); the staging is
@@ -663,6 +692,13 @@ cudaError_t launch_batch_step_t(lbm_engine *E, cudaStream_t s_main, cudaStream_t
         k_batch_scatter<T><<<2 * E->sms, 256, 0, s_side>>>(
             (const InstDev *)E->d_inst, (const int2 *)E->d_bmap, (const BatchCounts *)E->d_counts);
     }
+    // the simple boundary nodes of the two-buffer instances, beside the interior tiles
+    cfg.gridDim = dim3(2 * E->sms);
+    cfg.blockDim = dim3(128);
+    cfg.stream = s_side;
+    e = cudaLaunchKernelEx(&cfg, k_batch_simple<T>, (const InstDev *)E->d_inst,
+                           (const int2 *)E->d_bmap, (const BatchCounts *)E->d_counts);
+    if (e != cudaSuccess) return e;
     cudaEventRecord(E->join, s_side);
     const int TX = E->shape.tile_x, TY = E->shape.tile_y;
     if (TX == 32 && TY == 8)
@@ -749,7 +785,8 @@ lbm_status engine_steps(lbm_engine *E, int64_t nsteps) {
     if (E->inst.empty() || nsteps <= 0) return LBM_OK;
     cudaError_t e = cudaSuccess;
     int64_t done = 0;
-    const int per_step = one_step_instances(E) > 0 ? (E->n_in_place > 0 ? 4 : 3) : 0;
+    // boundary, simple boundary nodes, interior, advance (+ scatter with in-place instances)
+    const int per_step = one_step_instances(E) > 0 ? (E->n_in_place > 0 ? 5 : 4) : 0;
     if (nsteps >= kChunk) {
         if (!E->graph[E->wcur]) {
             lbm_status st = build_batch_graph(E);

@@ -144,7 +144,9 @@ lbm_status lbm::prepare(const lbm_desc *desc, Tables *t, Units *u) {
     }
     lbm_status st = make_units(*desc, u);
     if (st != LBM_OK) return st;
-    return classify(*desc, *u, t);
+    st = classify(*desc, *u, t);
+    if (st == LBM_OK) partition_boundary(*t);
+    return st;
 }
 
 namespace {

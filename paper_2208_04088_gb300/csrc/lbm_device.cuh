@@ -878,4 +878,119 @@ __device__ __forceinline__ void boundary8_node(const T *src, T *dst, float4 *__r
     }
 }
 
+// Incoming populations f(x, t) of a "simple" boundary node (every cut link a
+// mid-link wall, kappa = 0 and 1 + kappa = 1, of one BC and one axis-aligned
+// normal: box edges and crack faces), one lane per node.  ld(i, dx, dy) is
+// f_i^col(x + (dx, dy), t - 1); masks have bit i for direction i (cut: link i
+// crosses the wall; dirich: it takes the bounce-back rule; miss: its upstream
+// node x - c_i is unusable); sl is the link record shared by the cut links.
+// The wall data that do not depend on the link are formed once; every value is
+// computed by the same explicitly rounded functions as in cut_link_value, so
+// the result is that of the cooperative form bit for bit.  With kGuard no
+// population is read across a cut link (ld may only address the lattice);
+// without it those reads are issued unconditionally and their values replaced
+// (ld addresses rows with halo columns).
+template <bool kGuard, class Ld>
+__device__ __forceinline__ void simple_pull(const Ld &ld, uint32_t cut, uint32_t dirich,
+                                            uint32_t miss, const BLink &sl,
+                                            const BCDev *__restrict__ bcs, float tb,
+                                            const Lattice &L, float f[9]) {
+    float g[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) g[m] = ld(m, 0, 0);
+    f[0] = g[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k)  // intact links (the cut ones are replaced below)
+        f[k] = kGuard && ((cut >> opp(k)) & 1u) ? 0.0f : ld(k, -c_cx(k), -c_cy(k));
+    const Mom mx = moments(g);
+    float kap, fac;
+    link_kappa(0.5f, kap, fac);
+    if (dirich) {
+        float jsx, jsy;
+        dirichlet_momentum(sl, bcs, tb, L, jsx, jsy);
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+            const int i = opp(k);
+            const uint32_t bit = 1u << i;
+            if (!(cut & bit)) continue;
+            const float gy_i = (miss & bit) ? 0.0f : ld(i, c_cx(k), c_cy(k));
+            f[k] = bounce_back(k, kap, fac, g[k], g[i], gy_i, jsx, jsy);
+        }
+        return;
+    }
+    const WallFrame wf = wall_frame(sl, bcs, tb);
+    // wall values at the node: the wall-node option, or no usable upstream node
+    const WallState st0 = wall_state(false, 0.5f, mx.dr, mx.pxx, mx.pyy, mx.pxy, 0.0f, 0.0f, 0.0f,
+                                     0.0f, L);
+    float sxx, syy, sxy;
+    wall_sigma(wf, st0, sxx, syy, sxy);
+    const WallMoments wm0 = wall_moments(st0.drb, sxx, syy, sxy, L);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+        const int i = opp(k);
+        const uint32_t bit = 1u << i;
+        if (!(cut & bit)) continue;
+        const int cxk = c_cx(k), cyk = c_cy(k);
+        const bool ms = (miss & bit) != 0;
+        const float gy_i = ms ? 0.0f : ld(i, cxk, cyk);
+        WallMoments wm = wm0;
+        if (!ms && !L.wall_node) {
+            // extrapolation along the link from the upstream node x - c_i
+            float gy[9];
+#pragma unroll
+            for (int m = 0; m < 9; ++m) gy[m] = ld(m, cxk, cyk);
+            const Mom my = moments(gy);
+            const WallState st = wall_state(true, 0.5f, mx.dr, mx.pxx, mx.pyy, mx.pxy, my.dr,
+                                            my.pxx, my.pyy, my.pxy, L);
+            float ax, ay, axy;
+            wall_sigma(wf, st, ax, ay, axy);
+            wm = wall_moments(st.drb, ax, ay, axy, L);
+        }
+        f[k] = anti_bounce_back(kap, fac, g[k], g[i], gy_i, wall_equilibrium(k, wm));
+    }
+}
+
+// Populations f^col(x + (dx, dy), t - 1) of a two-buffer lattice in device memory.
+template <class T>
+struct GlobalRows {
+    const T *src;
+    int64_t k, pitch, fplane;
+    float inv_scale;
+    __device__ __forceinline__ float operator()(int i, int dx, int dy) const {
+        return Store<T>::ld(src + i * fplane + k + dy * pitch + dx, inv_scale);
+    }
+};
+
+// One simple boundary node g of the list (two buffers, lambda = mu), one lane:
+// the update of boundary8_node, bit for bit.
+template <class T>
+__device__ __forceinline__ void simple_node(const T *src, T *dst, float4 *__restrict__ uc,
+                                            const BNode *__restrict__ bnodes,
+                                            const BLink *__restrict__ blinks,
+                                            const BCDev *__restrict__ bcs, const Lattice &L, int g,
+                                            float tb, uint32_t *__restrict__ status) {
+    const BNode b = bnodes[g];
+    const int64_t k = (int64_t)b.y * L.pitch + b.x;
+    const uint32_t cut = b.cut;
+    const int d0 = __ffs((int)(cut >> 1));  // first cut direction, 1..8
+    const BLink sl = blinks[(int64_t)g * 8 + (d0 > 0 ? d0 - 1 : 0)];
+    float f[9];
+    simple_pull<true>(GlobalRows<T>{src, k, L.pitch, L.fplane, L.inv_scale}, cut, b.dirich,
+                      b.miss, sl, bcs, tb, L, f);
+    float4 w = uc[k];
+    float dr, jx, jy;
+    collide(f, L.fx, L.fy, L, dr, jx, jy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::st(dst + i * L.fplane + k, f[i], L.scale);
+    if constexpr (std::is_same<T, __half>::value) {
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) m = fmaxf(m, fabsf(f[i]));
+        note_range<T>(L, m);
+    }
+    integrate_u_value(w, jx, jy, L.rho0 + dr);
+    uc[k] = w;
+    flag_nonfinite(status, dr, jx, jy);
+}
+
 }  // namespace lbm

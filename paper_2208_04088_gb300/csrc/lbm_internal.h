@@ -85,9 +85,6 @@ struct Lattice {
                                 // in-place streaming pitch * (ny + 2) (a ring of one node)
     int32_t in_place;           // one population buffer, AA pattern (lbm_desc.streaming)
     int32_t nbcs;               // entries of the boundary-condition table
-    int32_t nbx;                // boundary nodes [0, nbx) take the eight-lane update; the
-                                // rest are simple ones, one lane each (two buffers, lambda = mu)
-    int32_t pad0;
     int64_t wait_ns;            // limit of a kernel's wait for a tile copy (lbm_set_wait_limit)
     ScaleState *sc;             // FP16 storage: the adaptive scale (null otherwise)
     uint32_t *over;             // FP16: this step's flag in *sc (set per step by step_scales)
@@ -101,10 +98,10 @@ constexpr int64_t kDefaultWaitNs = 1000000000;
 struct Tables {
     int32_t nx = 0, ny = 0, pitch = 0;
     std::vector<uint8_t> cls;    // [ny][pitch]
-    std::vector<BNode> bnodes;   // canonical order (row-major)
+    std::vector<BNode> bnodes;   // row-major; partition_boundary puts the simple ones last
     std::vector<BLink> blinks;   // [nb][8]
     std::vector<BCDev> bcs;
-    int64_t nbx = 0;             // boundary nodes before the simple ones (see partition_boundary)
+    int64_t nbx = 0;             // boundary nodes before the simple ones (partition_boundary)
     int64_t interior = 0;
     float max_load = 0.0f;       // largest boundary-value magnitude (lattice units)
 };

@@ -70,6 +70,24 @@ bool complex_boundary_node(const Tables &t, size_t g) {
     return bc < 0;
 }
 
+void partition_boundary(Tables &t) {
+    const size_t nb = t.bnodes.size();
+    std::vector<BNode> bn;
+    std::vector<BLink> bl;
+    bn.reserve(nb);
+    bl.reserve(nb * 8);
+    for (int pass = 0; pass < 2; ++pass)
+        for (size_t g = 0; g < nb; ++g)
+            if (complex_boundary_node(t, g) == (pass == 0)) {
+                bn.push_back(t.bnodes[g]);
+                bl.insert(bl.end(), t.blinks.begin() + g * 8, t.blinks.begin() + g * 8 + 8);
+            }
+    t.nbx = 0;
+    for (size_t g = 0; g < nb; ++g) t.nbx += complex_boundary_node(t, g) ? 1 : 0;
+    t.bnodes.swap(bn);
+    t.blinks.swap(bl);
+}
+
 namespace {
 
 // Modelled extra cost (row sweeps) of each row of every strip: the boundary

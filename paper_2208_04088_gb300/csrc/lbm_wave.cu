@@ -176,71 +176,6 @@ struct Rows {
     }
 };
 
-// Incoming populations f(x, t) of a "simple" boundary node (every cut link a
-// mid-link wall, kappa = 0 and 1 + kappa = 1, of one BC and one axis-aligned
-// normal: box edges and crack faces), one lane per node.  The wall data that
-// do not depend on the link are formed once; every value is computed by the
-// same explicitly rounded functions as in cut_link_value, so the result is
-// that of the cooperative form bit for bit.
-__device__ __forceinline__ void simple_pull(const Rows &ld, uint64_t nw,
-                                            const BCDev *__restrict__ bcs, float tb,
-                                            const Lattice &L, float f[9]) {
-    const uint32_t cut = nw_mask(nw, 2), dirich = nw_mask(nw, 10), miss = nw_mask(nw, 26);
-    const BLink sl = simple_link((uint32_t)(nw >> 35), L);
-    float g[9];
-#pragma unroll
-    for (int m = 0; m < 9; ++m) g[m] = ld(m, 0, 0);
-    f[0] = g[0];
-#pragma unroll
-    for (int k = 1; k < 9; ++k) f[k] = ld(k, -c_cx(k), -c_cy(k));  // intact links (cut ones replaced)
-    const Mom mx = moments(g);
-    float kap, fac;
-    link_kappa(0.5f, kap, fac);
-    if (dirich) {
-        float jsx, jsy;
-        dirichlet_momentum(sl, bcs, tb, L, jsx, jsy);
-#pragma unroll
-        for (int k = 1; k < 9; ++k) {
-            const int i = opp(k);
-            const uint32_t bit = 1u << i;
-            if (!(cut & bit)) continue;
-            const float gy_i = (miss & bit) ? 0.0f : ld(i, c_cx(k), c_cy(k));
-            f[k] = bounce_back(k, kap, fac, g[k], g[i], gy_i, jsx, jsy);
-        }
-        return;
-    }
-    const WallFrame wf = wall_frame(sl, bcs, tb);
-    // wall values at the node: the wall-node option, or no usable upstream node
-    const WallState st0 = wall_state(false, 0.5f, mx.dr, mx.pxx, mx.pyy, mx.pxy, 0.0f, 0.0f, 0.0f,
-                                     0.0f, L);
-    float sxx, syy, sxy;
-    wall_sigma(wf, st0, sxx, syy, sxy);
-    const WallMoments wm0 = wall_moments(st0.drb, sxx, syy, sxy, L);
-#pragma unroll
-    for (int k = 1; k < 9; ++k) {
-        const int i = opp(k);
-        const uint32_t bit = 1u << i;
-        if (!(cut & bit)) continue;
-        const int cxk = c_cx(k), cyk = c_cy(k);
-        const bool ms = (miss & bit) != 0;
-        const float gy_i = ms ? 0.0f : ld(i, cxk, cyk);
-        WallMoments wm = wm0;
-        if (!ms && !L.wall_node) {
-            // extrapolation along the link from the upstream node x - c_i
-            float gy[9];
-#pragma unroll
-            for (int m = 0; m < 9; ++m) gy[m] = ld(m, cxk, cyk);
-            const Mom my = moments(gy);
-            const WallState st = wall_state(true, 0.5f, mx.dr, mx.pxx, mx.pyy, mx.pxy, my.dr,
-                                            my.pxx, my.pyy, my.pxy, L);
-            float ax, ay, axy;
-            wall_sigma(wf, st, ax, ay, axy);
-            wm = wall_moments(st.drb, ax, ay, axy, L);
-        }
-        f[k] = anti_bounce_back(kap, fac, g[k], g[i], gy_i, wall_equilibrium(k, wm));
-    }
-}
-
 // Stores the post-collision populations of a lane's two nodes (columns c and
 // c + 32; plane stride `stride`), those that were updated.
 __device__ __forceinline__ void store_pair(float *out, int64_t stride, const F2 f[9], bool a,
@@ -478,8 +413,11 @@ __device__ __forceinline__ void wave_region(
                                 float g[9];
                                 const int dc = h << 5;
                                 if (h ? sim_b : sim_a) {
-                                    simple_pull(Rows{rm - c, r0 - c, rp - c, c + dc}, h ? nwb : nwa,
-                                                bcs, tb, L, g);
+                                    const uint64_t wn = h ? nwb : nwa;
+                                    simple_pull<false>(
+                                        Rows{rm - c, r0 - c, rp - c, c + dc}, nw_mask(wn, 2),
+                                        nw_mask(wn, 10), nw_mask(wn, 26),
+                                        simple_link((uint32_t)(wn >> 35), L), bcs, tb, L, g);
                                 } else {
                                     g[0] = r0[dc];
                                     g[1] = r0[kC + dc - 1];
@@ -772,10 +710,14 @@ __global__ void __launch_bounds__(kGradThreads, 1)
             for (int h = 0; h < 2; ++h) {
                 float g[9];
                 const int dc = h << 5;
-                if (h ? sim_b : sim_a)
-                    simple_pull(Rows{rm - c, r0 - c, rp - c, c + dc}, h ? nwb : nwa, bcs, tb, L, g);
-                else
+                if (h ? sim_b : sim_a) {
+                    const uint64_t wn = h ? nwb : nwa;
+                    simple_pull<false>(Rows{rm - c, r0 - c, rp - c, c + dc}, nw_mask(wn, 2),
+                                       nw_mask(wn, 10), nw_mask(wn, 26),
+                                       simple_link((uint32_t)(wn >> 35), L), bcs, tb, L, g);
+                } else {
                     pull_rows(rm, r0, rp, dc, g);
+                }
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     float va, vb;
