@@ -60,7 +60,10 @@ typedef enum {
  * scale starts where the largest boundary value maps to about 8.  BF16 has the
  * exponent range of FP32 and keeps it; FP16 ends at 65504, so its scale halves
  * from one step to the next whenever a step stored a value above 8192 (a run
- * that grows keeps finite values as long as FP32 would). */
+ * that grows keeps finite values as long as FP32 would).  The displacement u
+ * is accumulated in FP32: with FP32 storage with Kahan compensation (16 bytes
+ * per node), with 16-bit storage without it (8 bytes per node; the populations'
+ * own rounding is far larger than what compensation recovers). */
 typedef enum { LBM_F32 = 0, LBM_F16_DEV = 1, LBM_BF16_DEV = 2 } lbm_storage;
 
 /* Where the Neumann rules take the wall density rho^bd and the wall stress

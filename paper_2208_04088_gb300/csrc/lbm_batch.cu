@@ -38,7 +38,7 @@ struct InstDev {
     Lattice L;
     void *f[2];      // two buffers, or f[0] alone with in-place streaming (L.in_place)
     float *stage;    // in place: the boundary nodes' staged populations
-    float4 *uc;
+    void *uc;        // displacement records (URec of the storage type)
     const uint8_t *cls;
     const BNode *bn;
     const BLink *bl;
@@ -123,12 +123,12 @@ __global__ void __launch_bounds__(TX *TY, 2048 / (TX * TY)) k_batch_interior(con
                 if (kMixed && I.L.in_place) {  // one buffer: the AA step of the instance's parity
                     T *f = static_cast<T *>(I.f[0]);
                     if (cur)
-                        interior_node<T, kAAOdd>(f, f, I.uc, I.cls, nullptr, I.L, k, I.status);
+                        interior_node<T, kAAOdd>(f, f, static_cast<URec<T> *>(I.uc), I.cls, nullptr, I.L, k, I.status);
                     else
-                        interior_node<T, kAAEven>(f, f, I.uc, I.cls, nullptr, I.L, k, I.status);
+                        interior_node<T, kAAEven>(f, f, static_cast<URec<T> *>(I.uc), I.cls, nullptr, I.L, k, I.status);
                 } else {
                     interior_node<T>(static_cast<const T *>(I.f[cur]),
-                                     static_cast<T *>(I.f[cur ^ 1]), I.uc, I.cls, nullptr, I.L, k,
+                                     static_cast<T *>(I.f[cur ^ 1]), static_cast<URec<T> *>(I.uc), I.cls, nullptr, I.L, k,
                                      I.status);
                 }
             }
@@ -162,14 +162,14 @@ __global__ void __launch_bounds__(kB8) k_batch_boundary(const InstDev *__restric
             // once every boundary node has read its inputs
             T *f = static_cast<T *>(I.f[0]);
             if (cur)
-                boundary8_node<T, kAAOdd>(f, f, I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, L, m.y,
+                boundary8_node<T, kAAOdd>(f, f, static_cast<URec<T> *>(I.uc), I.bn, I.bl, I.bcs, I.cls, nullptr, L, m.y,
                                           live, j, (float)(time - 1), I.status, I.stage);
             else
-                boundary8_node<T, kAAEven>(f, f, I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, L, m.y,
+                boundary8_node<T, kAAEven>(f, f, static_cast<URec<T> *>(I.uc), I.bn, I.bl, I.bcs, I.cls, nullptr, L, m.y,
                                            live, j, (float)(time - 1), I.status, I.stage);
         } else {
             boundary8_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]),
-                              I.uc, I.bn, I.bl, I.bcs, I.cls, nullptr, L, m.y, live, j,
+                              static_cast<URec<T> *>(I.uc), I.bn, I.bl, I.bcs, I.cls, nullptr, L, m.y, live, j,
                               (float)(time - 1), I.status);
         }
     }
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(128) k_batch_simple(const InstDev *__restrict_
         const int cur = (int)(time & 1);
         Lattice L = I.L;
         step_scales<T>(L, time);
-        simple_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]), I.uc,
+        simple_node<T>(static_cast<const T *>(I.f[cur]), static_cast<T *>(I.f[cur ^ 1]), static_cast<URec<T> *>(I.uc),
                        I.bn, I.bl, I.bcs, L, m.y, (float)(time - 1), I.status);
     }
 }
@@ -483,7 +483,7 @@ lbm_status rebuild_wave_tables(lbm_engine *E) {
         w.tu = h->wave.u;
         w.f[0] = static_cast<float *>(h->S.f[0]);
         w.f[1] = static_cast<float *>(h->S.f[1]);
-        w.uc = h->S.ucomp;
+        w.uc = static_cast<float4 *>(h->S.ucomp);
         w.blinks = h->S.blinks;
         w.bcs = h->S.bcs;
         w.time = h->S.time;

@@ -77,7 +77,7 @@ Layout layout(const Tables &t, int storage, bool grad, int block, bool in_place)
     };
     l.f0 = take(9 * fplane * esz);
     l.f1 = in_place ? 0 : take(9 * fplane * esz);
-    l.ucomp = take(plane * sizeof(float4));
+    l.ucomp = take(plane * urec_bytes(storage));
     l.cls = take(plane);
     l.bnodes = take(std::max<size_t>(1, t.bnodes.size()) * sizeof(BNode));
     l.blinks = take(std::max<size_t>(1, t.blinks.size()) * sizeof(BLink));
@@ -322,7 +322,7 @@ lbm_status create_prepared(const lbm_desc *desc, Tables &&tab, const Units &unit
     // in place: node (0, 0) sits one row and one column into the padded planes
     S.f[0] = b + lay.f0 + (in_place ? (size_t)(h->tab.pitch + 1) * esz : 0);
     S.f[1] = in_place ? nullptr : b + lay.f1;
-    S.ucomp = reinterpret_cast<float4 *>(b + lay.ucomp);
+    S.ucomp = b + lay.ucomp;
     S.cls = reinterpret_cast<uint8_t *>(b + lay.cls);
     S.bnodes = reinterpret_cast<BNode *>(b + lay.bnodes);
     S.blinks = reinterpret_cast<BLink *>(b + lay.blinks);
@@ -636,7 +636,8 @@ extern "C" lbm_status lbm_get_info(lbm_handle h, lbm_info *info) {
         info->storage_scale = sc.s[(h->time + 2) % 3];
     }
     const float esz = h->storage == LBM_F32 ? 4.0f : 2.0f;
-    info->bytes_per_update = 2.0f * 9.0f * esz + 32.0f;  // f read + write, u and compensation R+W
+    // f read and written, the displacement record read and written
+    info->bytes_per_update = 2.0f * 9.0f * esz + 2.0f * (float)urec_bytes(h->storage);
     info->kernel_launches = h->launches;
     info->time_block = h->block;
     info->streaming = h->L.in_place ? LBM_STREAM_IN_PLACE : LBM_STREAM_TWO_BUFFERS;

@@ -270,8 +270,31 @@ __device__ __forceinline__ void integrate_u_value(float4 &w, float jx, float jy,
     w.y = t;
 }
 
-__device__ __forceinline__ void integrate_u(float4 *uc, float jx, float jy, float rho) {
-    float4 w = *uc;
+// 16-bit storage: u(t+1) = u(t) + j/rho without compensation; w holds
+// (u_x, u_y).  The populations' own rounding (FP16: 2^-11 of their size, each
+// step) is far larger than what the compensation recovers, and the record is
+// half as many bytes in the bandwidth-bound step.
+__device__ __forceinline__ void integrate_u_value(float2 &w, float jx, float jy, float rho) {
+    const float ir = __fdividef(1.0f, rho);
+    w.x = radd(w.x, rmul(jx, ir));
+    w.y = radd(w.y, rmul(jy, ir));
+}
+
+// The displacement record of a storage type: FP32 populations keep the
+// compensated float4, 16-bit populations a float2.
+template <class T> struct URecOf { using type = float2; };
+template <> struct URecOf<float> { using type = float4; };
+template <class T> using URec = typename URecOf<T>::type;
+
+// u of a record (the compensated sum without its compensation).
+__device__ __forceinline__ float2 u_of(const float4 &w) {
+    return make_float2(w.x - w.z, w.y - w.w);
+}
+__device__ __forceinline__ float2 u_of(const float2 &w) { return w; }
+
+template <class W>
+__device__ __forceinline__ void integrate_u(W *uc, float jx, float jy, float rho) {
+    W w = *uc;
     integrate_u_value(w, jx, jy, rho);
     *uc = w;
 }
@@ -809,14 +832,14 @@ __device__ __forceinline__ void source_boundary8(const T *__restrict__ src,
 // With kAA src and dst are the same buffer: the node reads all nine of its
 // locations before it writes any.
 template <class T, int LAY = kPull>
-__device__ __forceinline__ void interior_node(const T *src, T *dst, float4 *__restrict__ uc,
+__device__ __forceinline__ void interior_node(const T *src, T *dst, URec<T> *__restrict__ uc,
                                               const uint8_t *__restrict__ cls,
                                               const float *__restrict__ rho, const Lattice &L,
                                               int64_t k, uint32_t *__restrict__ status) {
     if (__ldg(cls + k) != kInterior) return;
     float f[9];
     pull_interior_at<LAY>(src, k, L, f);
-    float4 w = uc[k];
+    URec<T> w = uc[k];
     float sx = L.fx, sy = L.fy;
     if (L.grad) source_interior(rho, k, L.pitch, rho[k], L, sx, sy);
     float dr, jx, jy;
@@ -843,7 +866,7 @@ constexpr int kB8 = 128;  // threads per block of the cooperative boundary kerne
 // stage[9 g + m] (FP32) instead of the buffer: the in-place form stores them
 // only after every boundary node has read its inputs.
 template <class T, int LAY = kPull>
-__device__ __forceinline__ void boundary8_node(const T *src, T *dst, float4 *__restrict__ uc,
+__device__ __forceinline__ void boundary8_node(const T *src, T *dst, URec<T> *__restrict__ uc,
                                                const BNode *__restrict__ bnodes,
                                                const BLink *__restrict__ blinks,
                                                const BCDev *__restrict__ bcs,
@@ -964,7 +987,7 @@ struct GlobalRows {
 // One simple boundary node g of the list (two buffers, lambda = mu), one lane:
 // the update of boundary8_node, bit for bit.
 template <class T>
-__device__ __forceinline__ void simple_node(const T *src, T *dst, float4 *__restrict__ uc,
+__device__ __forceinline__ void simple_node(const T *src, T *dst, URec<T> *__restrict__ uc,
                                             const BNode *__restrict__ bnodes,
                                             const BLink *__restrict__ blinks,
                                             const BCDev *__restrict__ bcs, const Lattice &L, int g,
@@ -977,7 +1000,7 @@ __device__ __forceinline__ void simple_node(const T *src, T *dst, float4 *__rest
     float f[9];
     simple_pull<true>(GlobalRows<T>{src, k, L.pitch, L.fplane, L.inv_scale}, cut, b.dirich,
                       b.miss, sl, bcs, tb, L, f);
-    float4 w = uc[k];
+    URec<T> w = uc[k];
     float dr, jx, jy;
     collide(f, L.fx, L.fy, L, dr, jx, jy);
 #pragma unroll

@@ -90,6 +90,10 @@ struct Lattice {
     uint32_t *over;             // FP16: this step's flag in *sc (set per step by step_scales)
 };
 
+// Bytes of one node's displacement record: the compensated (u, kahan) float4
+// with FP32 storage, (u_x, u_y) with 16-bit storage.
+inline size_t urec_bytes(int storage) { return storage == LBM_F32 ? 16 : 8; }
+
 // Default of Lattice::wait_ns, and the limit of the waits that drain the
 // copies still in flight after a wait has run out: 1 s.
 constexpr int64_t kDefaultWaitNs = 1000000000;
@@ -154,7 +158,8 @@ struct DevState {
     void *f[2] = {nullptr, nullptr};  // two distribution buffers (9 planes each); with
                                       // in-place streaming f[0] only, at node (0, 0) of
                                       // its padded planes
-    float4 *ucomp = nullptr;          // (u_x, u_y, kahan_x, kahan_y) per node
+    void *ucomp = nullptr;            // per node: FP32 storage (u_x, u_y, kahan_x, kahan_y)
+                                      // float4; 16-bit storage (u_x, u_y) float2
     uint8_t *cls = nullptr;
     BNode *bnodes = nullptr;
     BLink *blinks = nullptr;

@@ -49,7 +49,7 @@ __device__ __forceinline__ int64_t scales_of_step(Lattice &L, const int64_t *tim
 
 template <class T, int NR, int LAY = kPull>
 __global__ void __launch_bounds__(kBX *kBY, 8) k_interior(const T *src, T *dst,
-                                                       float4 *__restrict__ uc,
+                                                       URec<T> *__restrict__ uc,
                                                        const uint8_t *__restrict__ cls,
                                                        const float *__restrict__ rho, Lattice L,
                                                        uint32_t *__restrict__ status,
@@ -76,7 +76,7 @@ constexpr int kGY = 8;  // rows of the lambda != mu tile (16 measured slower)
 template <class T>
 __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict__ src,
                                                             T *__restrict__ dst,
-                                                            float4 *__restrict__ uc,
+                                                            URec<T> *__restrict__ uc,
                                                             const uint8_t *__restrict__ cls,
                                                             const float *__restrict__ rho,
                                                             Lattice L,
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict_
     // density is summed, so a ring thread waits for one memory round trip
     bool live = false, ring_int = false;
     float f[9], g[9];
-    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    URec<T> w{};
     int64_t k = 0;
     float own = 0.0f, v = 0.0f;
     uint8_t c = kVoid, cr = kVoid;
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kBX *kGY) k_interior_grad(const T *__restrict_
 }
 
 template <class T, int LAY = kPull>
-__global__ void __launch_bounds__(kB8) k_boundary8(const T *src, T *dst, float4 *__restrict__ uc,
+__global__ void __launch_bounds__(kB8) k_boundary8(const T *src, T *dst, URec<T> *__restrict__ uc,
                                                    const BNode *__restrict__ bnodes,
                                                    const BLink *__restrict__ blinks,
                                                    const BCDev *__restrict__ bcs,
@@ -244,15 +244,17 @@ __global__ void __launch_bounds__(kBB) k_density_boundary(const T *__restrict__ 
 }
 
 // Fields at the current time t (Eqs. moments, poissonstress, approxdiv).
+template <class W>
 __device__ __forceinline__ void write_fields(float *__restrict__ out, int64_t N, int64_t o,
-                                             const float f[9], float sx, float sy, float4 w,
+                                             const float f[9], float sx, float sy, const W &w,
                                              const Lattice &L) {
     const Mom m = moments(f);
     const float jx = m.mx + 0.5f * sx, jy = m.my + 0.5f * sy;
     const float rho = L.rho0 + m.dr;
     const float dv = -L.lam_m_mu_r0 * m.dr;
-    out[o] = (w.x - w.z) * L.out_u;
-    out[N + o] = (w.y - w.w) * L.out_u;
+    const float2 u = u_of(w);
+    out[o] = u.x * L.out_u;
+    out[N + o] = u.y * L.out_u;
     out[2 * N + o] = jx / rho * L.out_v;
     out[3 * N + o] = jy / rho * L.out_v;
     out[4 * N + o] = (-m.pxx + dv) * L.out_s;
@@ -262,7 +264,7 @@ __device__ __forceinline__ void write_fields(float *__restrict__ out, int64_t N,
 
 template <class T, int LAY = kPull>
 __global__ void __launch_bounds__(kBX *kBY) k_fields_interior(const T *__restrict__ src,
-                                                              const float4 *__restrict__ uc,
+                                                              const URec<T> *__restrict__ uc,
                                                               const uint8_t *__restrict__ cls,
                                                               const float *__restrict__ rho,
                                                               Lattice L, float *__restrict__ out,
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(kBX *kBY) k_fields_interior(const T *__restric
 
 template <class T, int LAY = kPull>
 __global__ void __launch_bounds__(kBB) k_fields_boundary(const T *__restrict__ src,
-                                                         const float4 *__restrict__ uc,
+                                                         const URec<T> *__restrict__ uc,
                                                          const BNode *__restrict__ bnodes,
                                                          const BLink *__restrict__ blinks,
                                                          const BCDev *__restrict__ bcs,
@@ -362,7 +364,7 @@ static cudaError_t launch_boundary(const T *src, T *dst, const DevState &S, cons
     attr[0].val.priority = high_priority();
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_boundary8<T, LAY>, src, dst, S.ucomp,
+    return cudaLaunchKernelEx(&cfg, k_boundary8<T, LAY>, src, dst, static_cast<URec<T> *>(S.ucomp),
                               (const BNode *)S.bnodes, (const BLink *)S.blinks,
                               (const BCDev *)S.bcs, (const uint8_t *)S.cls, (const float *)S.rho, L,
                               (const int64_t *)S.time, toff, S.status, stage);
@@ -373,7 +375,8 @@ static void launch_interior(const T *src, T *dst, const DevState &S, const Latti
                             cudaStream_t s) {
     if (L.grad) {
         const dim3 blk(kBX, kGY), grd((L.nx + kBX - 1) / kBX, (L.ny + kGY - 1) / kGY);
-        k_interior_grad<T><<<grd, blk, 0, s>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status,
+        k_interior_grad<T><<<grd, blk, 0, s>>>(src, dst, static_cast<URec<T> *>(S.ucomp), S.cls,
+                                                S.rho, L, S.status,
                                                 S.time, toff);
         return;
     }
@@ -381,7 +384,8 @@ static void launch_interior(const T *src, T *dst, const DevState &S, const Latti
     // occupancy: 58+ registers)
     constexpr int NR = 1;
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY * NR - 1) / (kBY * NR));
-    k_interior<T, NR><<<grd, blk, 0, s>>>(src, dst, S.ucomp, S.cls, S.rho, L, S.status, S.time,
+    k_interior<T, NR><<<grd, blk, 0, s>>>(src, dst, static_cast<URec<T> *>(S.ucomp), S.cls, S.rho,
+                                          L, S.status, S.time,
                                           toff);
 }
 
@@ -411,7 +415,8 @@ static cudaError_t step_in_place(const Lattice &L, const DevState &S, int toff,
     }
     if (ev) cudaEventRecord(ev->before_interior, s_main);
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
-    k_interior<T, 1, LAY><<<grd, blk, 0, s_main>>>(f, f, S.ucomp, S.cls, S.rho, L, S.status, S.time,
+    k_interior<T, 1, LAY><<<grd, blk, 0, s_main>>>(f, f, static_cast<URec<T> *>(S.ucomp), S.cls,
+                                                   S.rho, L, S.status, S.time,
                                                    toff);
     if (ev) cudaEventRecord(ev->after_interior, s_main);
     if (split)
@@ -487,10 +492,12 @@ template <class T, int LAY>
 static void fields_in_place(const Lattice &L, const DevState &S, cudaStream_t s) {
     const T *src = static_cast<const T *>(S.f[0]);
     const dim3 blk(kBX, kBY), grd((L.nx + kBX - 1) / kBX, (L.ny + kBY - 1) / kBY);
-    k_fields_interior<T, LAY><<<grd, blk, 0, s>>>(src, S.ucomp, S.cls, S.rho, L, S.stage, S.time);
+    k_fields_interior<T, LAY><<<grd, blk, 0, s>>>(src, static_cast<const URec<T> *>(S.ucomp), S.cls,
+                                                  S.rho, L, S.stage, S.time);
     if (L.nb > 0)
         k_fields_boundary<T, LAY><<<(L.nb + kBB - 1) / kBB, kBB, 0, s>>>(
-            src, S.ucomp, S.bnodes, S.blinks, S.bcs, S.rho, L, S.time, S.stage);
+            src, static_cast<const URec<T> *>(S.ucomp), S.bnodes, S.blinks, S.bcs, S.rho, L, S.time,
+            S.stage);
 }
 
 template <class T>
@@ -511,9 +518,11 @@ static cudaError_t fields_t(const Lattice &L, const DevState &S, int cur, cudaSt
             k_density_boundary<T><<<nbb, kBB, 0, s>>>(src, S.bnodes, S.blinks, S.bcs, S.rho, L,
                                                       S.time, 0);
     }
-    k_fields_interior<T><<<grd, blk, 0, s>>>(src, S.ucomp, S.cls, S.rho, L, S.stage, S.time);
+    k_fields_interior<T><<<grd, blk, 0, s>>>(src, static_cast<const URec<T> *>(S.ucomp), S.cls,
+                                             S.rho, L, S.stage, S.time);
     if (L.nb > 0)
-        k_fields_boundary<T><<<nbb, kBB, 0, s>>>(src, S.ucomp, S.bnodes, S.blinks, S.bcs, S.rho,
+        k_fields_boundary<T><<<nbb, kBB, 0, s>>>(src, static_cast<const URec<T> *>(S.ucomp),
+                                                 S.bnodes, S.blinks, S.bcs, S.rho,
                                                  L, S.time, S.stage);
     return cudaGetLastError();
 }
@@ -554,7 +563,7 @@ cudaError_t launch_reset(int storage, const Lattice &L, const DevState &S, cudaS
     char *f0 = static_cast<char *>(S.f[0]) - (L.in_place ? (size_t)(L.pitch + 1) * esz : 0);
     cudaError_t e = cudaMemsetAsync(f0, 0, fbytes, s);
     if (e == cudaSuccess && S.f[1]) e = cudaMemsetAsync(S.f[1], 0, fbytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S.ucomp, 0, (size_t)L.plane * sizeof(float4), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.ucomp, 0, (size_t)L.plane * urec_bytes(storage), s);
     if (e == cudaSuccess && S.rho) e = cudaMemsetAsync(S.rho, 0, (size_t)L.plane * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.status, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.time, 0, sizeof(int64_t), s);

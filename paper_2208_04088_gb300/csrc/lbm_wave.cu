@@ -1077,11 +1077,13 @@ cudaError_t launch_wave(const Lattice &L, const DevState &S, const WaveMaps &m, 
                         cudaStream_t s, long long *cycles) {
     if (L.grad)
         k_wave_grad<<<(unsigned)m.nblocks, kGradThreads, kGSmem, s>>>(
-            m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]), S.ucomp, S.blinks, S.bcs, L,
+            m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]),
+            static_cast<float4 *>(S.ucomp), S.blinks, S.bcs, L,
             S.time, toff, S.wave_tab, S.status, cycles);
     else
         k_wave<<<(unsigned)m.nblocks, kThreads, kSmem, s>>>(
-            m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]), S.ucomp, S.blinks, S.bcs, L,
+            m.f[cur], m.nw, m.u, static_cast<float *>(S.f[cur ^ 1]),
+            static_cast<float4 *>(S.ucomp), S.blinks, S.bcs, L,
             S.time, toff, S.wave_tab, S.status, cycles);
     return cudaGetLastError();
 }
