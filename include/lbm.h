@@ -315,10 +315,13 @@ const char *lbm_last_error(void);
  * Many instances, one launch per step.  The paper has one lattice per run;
  * these entry points advance many independent lattices (Poisson solids,
  * lambda = mu, one storage form) together.  A step is one persistent interior
- * kernel over a table of (instance, tile) pairs and one persistent boundary
- * kernel over a table of (instance, boundary node) pairs, running the same
- * per-node code as lbm_step, so every instance's fields are bit-identical to
- * the same instance stepped alone.  Steps replay a captured CUDA graph.
+ * kernel over a table of (instance, tile) pairs and persistent boundary
+ * kernels over a table of (instance, boundary node) pairs (eight lanes to a
+ * node; the simple nodes of box edges and crack faces one lane each), running
+ * the same per-node code as lbm_step, so every instance's fields are
+ * bit-identical to the same instance stepped alone.  FP32 instances of at
+ * least 128 columns are stepped instead by the temporally blocked kernel, 8
+ * steps per launch over all of them.  Steps replay a captured CUDA graph.
  * ------------------------------------------------------------------------ */
 typedef struct lbm_engine *lbm_batch;
 typedef struct lbm_engine *lbm_server;
