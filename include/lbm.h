@@ -330,7 +330,7 @@ typedef struct lbm_engine *lbm_server;
  * threads (one node each; 32x4, 32x8, 32x16 or 64x4) and a schedule
  * (`dynamic`): 0 a persistent grid of blocks_per_sm blocks per SM walking the
  * tiles with a grid stride, 1 the same grid taking tiles from an atomic
- * counter, 2 one block per tile. */
+ * counter, 2 one block per tile, 3 one block per 4 consecutive tiles. */
 typedef struct {
     int32_t tile_x, tile_y, blocks_per_sm, dynamic;
 } lbm_launch_shape;

@@ -62,13 +62,18 @@ namespace {
 constexpr int kChunk = 16;  // steps per replayed graph
 
 // Batched interior kernel.  The descriptor of the tile's instance is staged in
-// shared memory once per tile, so the per-node code reads its lattice
-// parameters from shared memory (as the single-solver kernel reads them from
-// the parameter bank).  Schedules: 0 persistent grid stride, 1 persistent with
-// tiles handed out by an atomic counter, 2 one tile per block.  kMixed: the
+// shared memory when a block turns to a tile of another instance, so the
+// per-node code reads its lattice parameters from shared memory (as the
+// single-solver kernel reads them from the parameter bank).  Schedules: 0
+// persistent grid stride, 1 persistent with tiles handed out by an atomic
+// counter, 2 one tile per block, 3 one block per kTileRun consecutive tiles
+// (an instance's tiles are consecutive in the table, so most runs stage the
+// descriptor once).  kMixed: the
 // batch holds in-place instances, so each tile branches on its instance's
 // streaming; without them the pull-only form is launched (the three inlined
 // node updates of the mixed form cost registers: 88 bytes of spills against 24).
+constexpr int kTileRun = 4;
+
 template <class T, int TX, int TY, bool kMixed>
 __global__ void __launch_bounds__(TX *TY, 2048 / (TX * TY)) k_batch_interior(const InstDev *__restrict__ insts,
                                                            const int2 *__restrict__ tiles,
@@ -81,7 +86,8 @@ __global__ void __launch_bounds__(TX *TY, 2048 / (TX * TY)) k_batch_interior(con
     __shared__ long long s_time;
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int ntiles = counts->ntiles;
-    int tile = schedule == 1 ? -1 : (int)blockIdx.x;
+    int tile = schedule == 1 ? -1 : (schedule == 3 ? (int)blockIdx.x * kTileRun : (int)blockIdx.x);
+    int staged = -1;  // instance whose descriptor is in s_inst
     for (;;) {
         if (tid == 0) {
             if (schedule == 1) tile = atomicAdd(&counts->tile_counter, 1);
@@ -90,28 +96,30 @@ __global__ void __launch_bounds__(TX *TY, 2048 / (TX * TY)) k_batch_interior(con
                 const int2 t = tiles[tile];
                 s_local = t.y;
                 s_time = (long long)*insts[t.x].time;
-                s_inst[0] = (uint32_t)t.x;  // placeholder, overwritten below
             }
         }
         __syncthreads();
         tile = s_tile;
         if (tile >= ntiles) break;
-        // copy the descriptor (a few hundred bytes) with the whole block
         const int inst = tiles[tile].x;
-        const uint32_t *src_words = reinterpret_cast<const uint32_t *>(insts + inst);
-        for (int w = tid; w < kWords; w += TX * TY) s_inst[w] = __ldg(src_words + w);
-        __syncthreads();
-        const InstDev &I = *reinterpret_cast<const InstDev *>(s_inst);
         const int64_t time = s_time;
-        if constexpr (std::is_same<T, __half>::value) {
-            // the instance's scales of this step (FP16); the tile of local
-            // index 0 publishes them
-            if (tid == 0 && time < I.target) {
-                InstDev &W = *reinterpret_cast<InstDev *>(s_inst);
-                step_scales<T>(W.L, time);
-                if (s_local == 0) publish_scale<T>(W.L, time);
-            }
+        if (inst != staged) {  // uniform over the block
+            // copy the descriptor (a few hundred bytes) with the whole block
+            const uint32_t *src_words = reinterpret_cast<const uint32_t *>(insts + inst);
+            for (int w = tid; w < kWords; w += TX * TY) s_inst[w] = __ldg(src_words + w);
             __syncthreads();
+            if constexpr (std::is_same<T, __half>::value) {
+                // the instance's scales of this step (FP16)
+                if (tid == 0 && time < reinterpret_cast<const InstDev *>(s_inst)->target)
+                    step_scales<T>(reinterpret_cast<InstDev *>(s_inst)->L, time);
+                __syncthreads();
+            }
+            staged = inst;
+        }
+        const InstDev &I = *reinterpret_cast<const InstDev *>(s_inst);
+        if constexpr (std::is_same<T, __half>::value) {
+            // the tile of local index 0 publishes the instance's scales
+            if (tid == 0 && time < I.target && s_local == 0) publish_scale<T>(I.L, time);
         }
         if (time < I.target) {
             const int local = s_local;
@@ -134,8 +142,12 @@ __global__ void __launch_bounds__(TX *TY, 2048 / (TX * TY)) k_batch_interior(con
             }
         }
         if (schedule == 2) break;
+        if (schedule == 3) {
+            if ((tile + 1) % kTileRun == 0) break;
+            tile += 1;
+        }
         if (schedule == 0) tile += gridDim.x;
-        __syncthreads();  // the next tile overwrites the staged descriptor
+        __syncthreads();  // the next tile may overwrite the staged descriptor and s_tile
     }
 }
 
@@ -583,7 +595,7 @@ lbm_status rebuild_tables(lbm_engine *E) {
     E->n_in_place = 0;
     for (const InstDev &d : hi) E->n_in_place += d.L.in_place ? 1 : 0;
     if (E->graph_in_place != (E->n_in_place > 0)) drop_graphs(E);  // the kernels' order changes
-    if (E->shape.dynamic == 2 && (int64_t)tiles.size() != E->ntiles) {
+    if (E->shape.dynamic >= 2 && (int64_t)tiles.size() != E->ntiles) {
         drop_graphs(E);  // one block per tile: the captured grid must match the table
     }
     lbm_status wst = rebuild_wave_tables(E);
@@ -647,8 +659,10 @@ int high_priority_value() {
 template <class T, int TX, int TY>
 cudaError_t launch_interior_shape(lbm_engine *E, cudaStream_t s) {
     const int sched = E->shape.dynamic;
-    const unsigned blocks = sched == 2 ? (unsigned)std::max<int64_t>(1, E->ntiles)
-                                       : (unsigned)(E->shape.blocks_per_sm * E->sms);
+    const unsigned blocks =
+        sched == 2   ? (unsigned)std::max<int64_t>(1, E->ntiles)
+        : sched == 3 ? (unsigned)std::max<int64_t>(1, (E->ntiles + kTileRun - 1) / kTileRun)
+                     : (unsigned)(E->shape.blocks_per_sm * E->sms);
     const dim3 blk(TX, TY), grd(blocks);
     if (E->n_in_place > 0)
         k_batch_interior<T, TX, TY, true><<<grd, blk, 0, s>>>(E->d_inst, E->d_tiles, E->d_counts, sched);
@@ -1155,7 +1169,7 @@ extern "C" lbm_status lbm_batch_set_shape(lbm_batch b, const lbm_launch_shape *s
                                                   shape->tile_y == 16)) ||
                          (shape->tile_x == 64 && shape->tile_y == 4);
     if (!ok_tile || shape->blocks_per_sm < 1 || shape->blocks_per_sm > 64 ||
-        shape->dynamic < 0 || shape->dynamic > 2) {
+        shape->dynamic < 0 || shape->dynamic > 3) {
         set_error("lbm_batch_set_shape: tiles 32x4, 32x8, 32x16 or 64x4; 1..64 blocks per SM; "
                   "schedule 0, 1 or 2");
         return LBM_ERR_ARG;
@@ -1204,7 +1218,8 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch b, int32_t steps_per_trial,
     const lbm_launch_shape cands[] = {
         {32, 8, 8, 2},  {32, 4, 16, 2}, {64, 4, 8, 2},  {32, 16, 4, 2}, {32, 8, 8, 0},
         {32, 8, 8, 1},  {32, 8, 4, 0},  {32, 4, 16, 0}, {32, 4, 16, 1}, {64, 4, 8, 0},
-        {64, 4, 8, 1},  {32, 16, 4, 0}, {32, 16, 4, 1}};
+        {64, 4, 8, 1},  {32, 16, 4, 0}, {32, 16, 4, 1}, {32, 4, 16, 3}, {32, 8, 8, 3},
+        {64, 4, 8, 3}};
     float best = 1e30f;
     lbm_launch_shape best_shape = b->shape;
     for (const auto &c : cands) {

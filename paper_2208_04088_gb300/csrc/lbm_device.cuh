@@ -52,14 +52,28 @@ struct Store<__nv_bfloat16> {
 // scale of step t - 1, halved if one of its values passed kScaleOver).  Other
 // storage forms keep their fixed scale.  Every kernel of a step computes the
 // same pair from the solver's scale record.
+//
+// t mod 3 for t >= 0 from the two 32-bit halves (2^32 = 1 mod 3), without a
+// 64-bit division.
+__host__ __device__ __forceinline__ int mod3(int64_t t) {
+    const uint32_t lo = (uint32_t)t, hi = (uint32_t)((uint64_t)t >> 32);
+    return (int)((lo % 3u + hi % 3u) % 3u);
+}
+
+// 1/s of a power of two s = 2^e, -127 <= e <= 126, exactly: the biased
+// exponent 127 + e becomes 127 - e (the scales lie in [2^-126, 2^60]).
+__device__ __forceinline__ float pow2_reciprocal(float s) {
+    return __int_as_float(0x7f000000 - __float_as_int(s));
+}
+
 template <class T> __device__ __forceinline__ void step_scales(Lattice &L, int64_t t) {
     if constexpr (std::is_same<T, __half>::value) {
         if (L.sc) {
-            const int p = (int)((t + 2) % 3);
+            const int p = mod3(t + 2);
             const float prev = L.sc->s[p];
-            L.inv_scale = __fdiv_rn(1.0f, prev);  // a power of two: exact
+            L.inv_scale = pow2_reciprocal(prev);
             L.scale = L.sc->over[p] ? fmaxf(__fmul_rn(prev, 0.5f), kScaleMin) : prev;
-            L.over = L.sc->over + t % 3;
+            L.over = L.sc->over + mod3(t);
         }
     }
 }
@@ -69,8 +83,8 @@ template <class T> __device__ __forceinline__ void step_scales(Lattice &L, int64
 template <class T> __device__ __forceinline__ void publish_scale(const Lattice &L, int64_t t) {
     if constexpr (std::is_same<T, __half>::value) {
         if (L.sc) {
-            L.sc->s[t % 3] = L.scale;
-            L.sc->over[(t + 1) % 3] = 0u;
+            L.sc->s[mod3(t)] = L.scale;
+            L.sc->over[mod3(t + 1)] = 0u;
         }
     }
 }

@@ -73,7 +73,8 @@ def test_every_launch_shape_and_the_tuner_give_identical_fields():
     wls = _mix()
     ref = [_alone(w, 40) for w in wls]
     b = N.Batch([N.desc_from_workload(w) for w in wls])
-    for shape in [(32, 8, 8, 0), (32, 8, 4, 1), (32, 4, 16, 0), (64, 4, 8, 1), (32, 16, 4, 0)]:
+    for shape in [(32, 8, 8, 0), (32, 8, 4, 1), (32, 4, 16, 0), (64, 4, 8, 1), (32, 16, 4, 0),
+                  (32, 4, 16, 3), (64, 4, 8, 3)]:
         b.reset()
         b.set_shape(*shape)
         b.step(40)
@@ -149,7 +150,7 @@ def test_batch_in_place_instances_match_alone(storage):
         b.sync()
         for k, w in enumerate(wls):
             assert _same(b.fields_host(k), ref[k]), (mixed, w.name)
-        for shape in [(32, 4, 16, 0), (64, 4, 8, 1)]:
+        for shape in [(32, 4, 16, 0), (64, 4, 8, 1), (32, 8, 8, 3)]:
             b.reset()
             b.set_shape(*shape)
             b.step(75)
