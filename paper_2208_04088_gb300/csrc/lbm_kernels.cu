@@ -103,8 +103,13 @@ template <> struct Pair16<__nv_bfloat16> {
     }
 };
 
+// Blocks per SM the register bound aims at: FP16 measured fastest at six (40
+// registers: 93.9 against 90.4 GLUPS at four on the 2048^2 crack), BF16 at four
+// (100.7 against 98.9 at six).
+template <class T> constexpr int kPairMinBlocks = std::is_same<T, __half>::value ? 6 : 4;
+
 template <class T>
-__global__ void __launch_bounds__(kBX *kBY, 4) k_interior_pair(const T *__restrict__ src,
+__global__ void __launch_bounds__(kBX *kBY, kPairMinBlocks<T>) k_interior_pair(const T *__restrict__ src,
                                                             T *__restrict__ dst,
                                                             float2 *__restrict__ uc,
                                                             const uint8_t *__restrict__ cls,
@@ -114,13 +119,19 @@ __global__ void __launch_bounds__(kBX *kBY, 4) k_interior_pair(const T *__restri
                                                             int toff) {
     const int x0 = 2 * (int)(blockIdx.x * kBX + threadIdx.x);
     const int y = blockIdx.y * kBY + threadIdx.y;
-    scales_of_step<T>(L, time, toff, x0 == 0 && y == 0);
+    // FP16: this step's scales.  The thread of node (0, 0), which is never
+    // interior, publishes them after its node classes have been read, so that
+    // no store sits between the loads of a thread and delays them.
+    const int64_t t = scales_of_step<T>(L, time, toff, false);
     if (x0 >= L.nx || y >= L.ny) return;
     const int64_t k = (int64_t)y * L.pitch + x0;
     const uint32_t cc = __ldg(reinterpret_cast<const uint16_t *>(cls + k));
     const bool a = (cc & 0xffu) == kInterior;
     const bool b = x0 + 1 < L.nx && (cc >> 8) == kInterior;
-    if (!a && !b) return;
+    if (!a && !b) {
+        if (x0 == 0 && y == 0) publish_scale<T>(L, t);
+        return;
+    }
     // word of plane i at (x0 + 2 dw, y + dy): nodes x0 + 2 dw and x0 + 2 dw + 1
     auto word = [&](int i, int dw, int dy) {
         return __ldg(reinterpret_cast<const unsigned int *>(src + i * L.fplane + k +
