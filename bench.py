@@ -45,7 +45,7 @@ FLOPS_PER_UPDATE = 91
 FLOPS_PER_UPDATE_GRAD = 109
 # the kernel sources each kernel's recorded DRAM traffic depends on
 KERNEL_SOURCES = {"k_interior": ("lbm_kernels.cu", "lbm_device.cuh"),
-                  "k_interior_pair": ("lbm_kernels.cu", "lbm_device.cuh"),
+                  "k_interior_pair": ("lbm_kernels.cu", "lbm_device.cuh", "lbm_pair.cuh"),
                   "k_interior_grad": ("lbm_kernels.cu", "lbm_device.cuh"),
                   "k_interior_aa": ("lbm_kernels.cu", "lbm_device.cuh"),
                   "k_wave": ("lbm_wave.cu", "lbm_device.cuh"),

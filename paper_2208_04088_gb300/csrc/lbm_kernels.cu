@@ -22,6 +22,7 @@
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_pair.cuh"
 
 namespace lbm {
 // ---------------------------------------------------------------------------
@@ -66,44 +67,8 @@ __global__ void __launch_bounds__(kBX *kBY, 8) k_interior(const T *src, T *dst,
     }
 }
 
-// 16-bit storage, two buffers, lambda = mu: two horizontally adjacent nodes
-// (x0, x0 + 1), x0 even, per thread.  Each population plane is read and
-// written as aligned 32-bit pairs (the row pitch is a multiple of 64): the
-// planes pulled straight up or down as one word, the others from two
-// neighbouring words recombined with one byte permutation.  The pair collides
-// with the f32x2 instructions.  Every value is the one interior_node forms for
-// its node (the conversions, the power-of-two scalings and the paired
-// arithmetic round each half as the scalar code does), and a node that is
-// not interior reads nothing beyond its pair's own words and stores nothing.
-template <class T> struct Pair16;
-template <> struct Pair16<__half> {
-    static __device__ __forceinline__ float2 to_f2(uint32_t w) {
-        __half2 h;
-        memcpy(&h, &w, 4);
-        return __half22float2(h);
-    }
-    static __device__ __forceinline__ uint32_t from(float lo, float hi) {
-        const __half2 h = __floats2half2_rn(lo, hi);
-        uint32_t w;
-        memcpy(&w, &h, 4);
-        return w;
-    }
-};
-template <> struct Pair16<__nv_bfloat16> {
-    static __device__ __forceinline__ float2 to_f2(uint32_t w) {
-        __nv_bfloat162 h;
-        memcpy(&h, &w, 4);
-        return __bfloat1622float2(h);
-    }
-    static __device__ __forceinline__ uint32_t from(float lo, float hi) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-        uint32_t w;
-        memcpy(&w, &h, 4);
-        return w;
-    }
-};
-
-// Blocks per SM the register bound aims at: FP16 measured fastest at six (40
+// 16-bit storage, two buffers, lambda = mu: two adjacent nodes per thread
+// (interior_pair).  Blocks per SM the register bound aims at: FP16 measured fastest at six (40
 // registers: 93.9 against 90.4 GLUPS at four on the 2048^2 crack), BF16 at four
 // (100.7 against 98.9 at six).
 template <class T> constexpr int kPairMinBlocks = std::is_same<T, __half>::value ? 6 : 4;
@@ -124,84 +89,8 @@ __global__ void __launch_bounds__(kBX *kBY, kPairMinBlocks<T>) k_interior_pair(c
     // no store sits between the loads of a thread and delays them.
     const int64_t t = scales_of_step<T>(L, time, toff, false);
     if (x0 >= L.nx || y >= L.ny) return;
-    const int64_t k = (int64_t)y * L.pitch + x0;
-    const uint32_t cc = __ldg(reinterpret_cast<const uint16_t *>(cls + k));
-    const bool a = (cc & 0xffu) == kInterior;
-    const bool b = x0 + 1 < L.nx && (cc >> 8) == kInterior;
-    if (!a && !b) {
-        if (x0 == 0 && y == 0) publish_scale<T>(L, t);
-        return;
-    }
-    // word of plane i at (x0 + 2 dw, y + dy): nodes x0 + 2 dw and x0 + 2 dw + 1
-    auto word = [&](int i, int dw, int dy) {
-        return __ldg(reinterpret_cast<const unsigned int *>(src + i * L.fplane + k +
-                                                             (int64_t)dy * L.pitch) + dw);
-    };
-    uint32_t w[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int cx = c_cx(i), dy = -c_cy(i);
-        const uint32_t w0 = word(i, 0, dy);
-        if (cx == 0) {
-            w[i] = w0;
-        } else if (cx > 0) {  // from x - 1: (x0 - 1, x0)
-            const uint32_t wm = a ? word(i, -1, dy) : 0u;
-            w[i] = __byte_perm(wm, w0, 0x5432);
-        } else {  // from x + 1: (x0 + 1, x0 + 2)
-            const uint32_t wp = b ? word(i, 1, dy) : 0u;
-            w[i] = __byte_perm(w0, wp, 0x5432);
-        }
-    }
-    const float4 u2 = *reinterpret_cast<const float4 *>(uc + k);
-    const F2 is2 = splat<F2>(L.inv_scale);
-    F2 f[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const float2 v = Pair16<T>::to_f2(w[i]);
-        f[i] = rmul(f2(v.x, v.y), is2);
-    }
-    F2 dr, jx, jy;
-    collide_v(f, f2(L.fx, L.fx), f2(L.fy, L.fy), splat<F2>(L.omega),
-              splat<F2>(rmul(L.src, 1.0f / 3.0f)), dr, jx, jy);
-    const F2 sc2 = splat<F2>(L.scale);
-    float m = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        float fa, fb;
-        f2_split(f[i], fa, fb);
-        if (a) m = fmaxf(m, fabsf(fa));
-        if (b) m = fmaxf(m, fabsf(fb));
-        float va, vb;
-        f2_split(rmul(f[i], sc2), va, vb);
-        T *o = dst + i * L.fplane + k;
-        if (a && b) {
-            *reinterpret_cast<uint32_t *>(o) = Pair16<T>::from(va, vb);
-        } else if (a) {
-            Store<T>::st(o, fa, L.scale);
-        } else {
-            Store<T>::st(o + 1, fb, L.scale);
-        }
-    }
-    note_range<T>(L, m);
-    float dra, drb, jxa, jxb, jya, jyb;
-    f2_split(dr, dra, drb);
-    f2_split(jx, jxa, jxb);
-    f2_split(jy, jya, jyb);
-    float2 ua = make_float2(u2.x, u2.y), ub = make_float2(u2.z, u2.w);
-    if (a) {
-        integrate_u_value(ua, jxa, jya, L.rho0 + dra);
-        flag_nonfinite(status, dra, jxa, jya);
-    }
-    if (b) {
-        integrate_u_value(ub, jxb, jyb, L.rho0 + drb);
-        flag_nonfinite(status, drb, jxb, jyb);
-    }
-    if (a && b)
-        *reinterpret_cast<float4 *>(uc + k) = make_float4(ua.x, ua.y, ub.x, ub.y);
-    else if (a)
-        uc[k] = ua;
-    else
-        uc[k + 1] = ub;
+    if (!interior_pair<T>(src, dst, uc, cls, L, x0, y, status) && x0 == 0 && y == 0)
+        publish_scale<T>(L, t);
 }
 
 // Interior kernel for lambda != mu: the density deviations of the tile and a
