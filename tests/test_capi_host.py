@@ -59,8 +59,11 @@ def test_workspace_size_accounts_for_storage():
     b32 = N.lbm_workspace_size(_desc(wl, storage="f32"))
     b16 = N.lbm_workspace_size(_desc(wl, storage="f16"))
     plane = 256 * 128
-    assert b32 - b16 >= 2 * 9 * plane * 2   # two buffers, 2 bytes less per value
+    # two buffers with 2 bytes less per value, and the displacement record:
+    # (u, compensation) float4 with FP32 storage, (u_x, u_y) float2 with 16-bit
+    assert b32 - b16 >= 2 * 9 * plane * 2 + 8 * plane
     assert b32 > 2 * 9 * plane * 4 + 16 * plane
+    assert b16 > 2 * 9 * plane * 2 + 8 * plane
 
 
 def test_validation_rejects_bad_tables():
